@@ -1,0 +1,421 @@
+#!/usr/bin/env python
+"""Benchmark of the whole GCR re-ranking pipeline on one GB300 (or N replicas).
+
+A step is one pass of the hot path over the cross-camera workload with the Market-1501
+shape (3,368 queries + 15,913 gallery, d = 2048, 6 cameras, k = 20, T = 2, alpha = 0.7):
+normalise, T x (similarity GEMM + streaming top-k, certified refinement, weights/degrees/
+operator, propagation), then the re-ranked distance GEMM and the per-query sort.
+The metric is re-ranked queries/s = queries / step time. The primary path is BF16 tensor
+cores + certified FP32/FP64 refinement; the plain FP32 path is timed beside it.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Prints one JSON line (rank 0). With --impl reference the FP64 CPU oracle is timed instead.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "re-ranked queries/s, BF16+refine vs plain FP32 at stated error; p50/p99 latency"
+UNIT = "queries/s"
+WORKLOAD = ("crosscam: 3,368 queries + 15,913 gallery (Market-1501 shape), d=2048, 751 identity "
+            "clusters + 20% distractors, ReLU features, 6 cameras; k=20, T=2, gamma=0.2, alpha=0.7, "
+            "symmetric operator, global + cross-camera graphs, full gallery ranking per query")
+L2_FLUSH_BYTES = 256 << 20
+FP32_LANES_PER_SM = 128
+N_SMS = 152
+
+
+def _args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--precision", choices=["auto", "bf16", "fp32"], default="auto")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except Exception:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0,
+                "sm_max_mhz": 2070.0}, "fallback"
+
+
+# ------------------------------------------------------------------------------------ clocks
+class ClockSampler:
+    FIELDS = ("timestamp,index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.path = tempfile.mktemp(prefix="gcr_clocks_", suffix=".csv")
+        self.proc = None
+        try:
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={gpu_index}", f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=self.fh, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        self.t0 = self.t1 = None
+
+    def mark_start(self):
+        self.t0 = time.time()
+
+    def mark_end(self):
+        self.t1 = time.time()
+
+    def result(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.fh.close()
+        rows = []
+        with open(self.path) as f:
+            for line in f:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) < 10:
+                    continue
+                try:
+                    ts = time.mktime(time.strptime(parts[0].split(".")[0], "%Y/%m/%d %H:%M:%S"))
+                except Exception:
+                    continue
+                rows.append((ts, parts))
+        os.unlink(self.path)
+        inwin = [p for ts, p in rows if self.t0 is None or (self.t0 - 1.0 <= ts <= self.t1 + 1.0)]
+        use = inwin or [p for _, p in rows]
+        sm = [float(p[2]) for p in use if p[2].replace(".", "").isdigit()]
+        mx = [float(p[3]) for p in use if p[3].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for p in use for i in range(4) if p[6 + i].lower().startswith("active")})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(use)}
+
+
+# ------------------------------------------------------------------------------------ oracle arm
+def oracle_sample_step(w, rows_knn=96, rows_q=96, rows_prop=2000, seed=0):
+    """Times the FP64 oracle on bounded row samples of the workload and scales each stage
+    linearly to the full workload. Returns (estimated seconds for one full step, detail)."""
+    import numpy as np
+    import oracle
+
+    rng = np.random.default_rng(seed)
+    X0 = oracle.l2_normalize(w.X)
+    n, nq = w.n, w.n_query
+    rows = rng.choice(n, rows_knn, replace=False)
+    t0 = time.perf_counter()
+    oracle.knn_rows(X0, rows, w.k)
+    oracle.knn_rows(X0, rows, w.k, w.cam, cross_camera=True)
+    t_knn = time.perf_counter() - t0
+    sub = np.arange(rows_prop)
+    Xs = X0[sub]
+    t0 = time.perf_counter()
+    g = oracle.build_graph(Xs, w.k, w.gamma, w.cam[sub], True, True, w.alpha)
+    oracle.propagate(Xs, g["M"])
+    t_sub = time.perf_counter() - t0
+    # the sub-problem also paid its own kNN search: remove it with the measured per-row rate
+    t_prop = max(0.0, t_sub - t_knn / rows_knn * rows_prop * (rows_prop / n))
+    q = rng.choice(nq, rows_q, replace=False)
+    t0 = time.perf_counter()
+    oracle.rerank(X0[q], X0[nq:])
+    t_rr = time.perf_counter() - t0
+    est = w.T * (t_knn * n / rows_knn + t_prop * n / rows_prop) + t_rr * nq / rows_q
+    return est, dict(t_knn=t_knn, t_prop=t_prop, t_rerank=t_rr)
+
+
+def cpu_sample_description(rows_knn=96, rows_q=96, rows_prop=2000):
+    return (f"FP64 oracle stages on row samples of the same workload, each scaled linearly to the full "
+            f"step: kNN (global + cross-camera) of {rows_knn} of 19,281 rows per layer, graph + propagation "
+            f"on the first {rows_prop} rows, re-ranking of {rows_q} of 3,368 queries")
+
+
+def run_reference(a):
+    import numpy as np  # noqa: F401
+    import workloads
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    w = workloads.crosscam()
+    for _ in range(a.warmup):
+        oracle_sample_step(w, rows_knn=32, rows_q=32, rows_prop=500)
+    ests = []
+    t_start = time.perf_counter()
+    for s in range(a.steps):
+        est, _ = oracle_sample_step(w, seed=s)
+        ests.append(est)
+    wall = time.perf_counter() - t_start
+    ms = statistics.mean(ests) * 1e3
+    v = w.n_query / (ms / 1e3)
+    cores = os.cpu_count()
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": a.gpus,
+            "steps": a.steps, "warmup": a.warmup, "ms_per_step": ms, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "l2": "n/a (CPU)", "parallelism": "single process"},
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": cpu_sample_description(), "wall_s": wall},
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ------------------------------------------------------------------------------------ our arm
+def _src_hash(files):
+    h = hashlib.sha256()
+    for f in files:
+        with open(os.path.join(ROOT, "paper_2306_08792_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def _traffic(kernel_key, files):
+    """DRAM bytes per launch from the committed ncu summary, if it matches the current source."""
+    try:
+        with open(os.path.join(ROOT, "profiles", "traffic.json")) as f:
+            t = json.load(f)
+        e = t.get(kernel_key)
+        if e and e.get("src_hash") == _src_hash(files):
+            return e.get("bytes_per_launch")
+    except Exception:
+        pass
+    return None
+
+
+def time_path(gcr, torch, w, X, cam, precision, steps, warmup, dist):
+    from paper_2306_08792_gb300 import _lib
+    p = gcr.default_params(k=w.k, T=w.T, cross_camera=1, alpha=w.alpha, gamma=w.gamma, precision=precision)
+    pl = gcr.Pipeline(w.n, w.n_query, w.d, p)
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device="cuda")
+    for _ in range(warmup):
+        pl(X, cam, keep_features=False)
+    torch.cuda.synchronize()
+    lib = _lib.load()
+    import ctypes
+    S = _lib.GCR_STAGES
+    ms_arr = (ctypes.c_double * S)()
+    la = (ctypes.c_int64 * S)()
+    ca = (ctypes.c_int64 * S)()
+    lib.gcr_profile_enable(1)
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    pl.stats.zero_()
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    for s in range(steps):
+        flush.zero_()                           # evict L2 between steps (outside the timed events)
+        evs[s][0].record(stream)
+        pl(X, cam, keep_features=False)
+        evs[s][1].record(stream)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    per = [a.elapsed_time(b) for a, b in evs]
+    lib.gcr_profile_read(ms_arr, la, ca, S)
+    lib.gcr_profile_enable(0)
+    stages = {name: {"ms": ms_arr[i] / steps, "launches": la[i] / steps, "calls": ca[i] / steps}
+              for i, name in enumerate(_lib.STAGE_NAMES)}
+    launches = sum(v["launches"] for v in stages.values()) * steps
+    return dict(ms=statistics.mean(per), ms_median=statistics.median(per), stages=stages, launches=launches,
+                stats=pl.stats_dict(), pipeline=pl, params=p)
+
+
+def time_e2e(gcr, torch, w, Xh, camh, pl, steps, warmup):
+    """Same pipeline through the C ABI with host buffers: H2D of the inputs and D2H of the
+    ranking inside the timed region, every step."""
+    stream = torch.cuda.current_stream()
+    Xd = torch.empty(w.n, w.d, dtype=torch.float32, device="cuda")
+    camd = torch.empty(w.n, dtype=torch.int32, device="cuda")
+    idx_h = torch.empty(pl.idx.shape, dtype=torch.int32).pin_memory()
+    dist_h = torch.empty(pl.dist.shape, dtype=torch.float32).pin_memory()
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device="cuda")
+
+    def one():
+        Xd.copy_(Xh, non_blocking=True)
+        camd.copy_(camh, non_blocking=True)
+        pl(Xd, camd, keep_features=False)
+        idx_h.copy_(pl.idx, non_blocking=True)
+        dist_h.copy_(pl.dist, non_blocking=True)
+
+    for _ in range(warmup):
+        one()
+    torch.cuda.synchronize()
+    per = []
+    for _ in range(steps):
+        flush.zero_()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        one()
+        b.record(stream)
+        b.synchronize()
+        per.append(a.elapsed_time(b))
+    h2d = Xh.numel() * 4 + camh.numel() * 4
+    d2h = idx_h.numel() * 4 + dist_h.numel() * 4
+    return statistics.mean(per), h2d, d2h
+
+
+def sampled_error(torch, pl, w, nsample=8):
+    """Max |returned distance - FP64 distance on the returned features| over sampled queries."""
+    import numpy as np
+    XT = pl.X_final.double().cpu().numpy()
+    q = np.random.default_rng(0).choice(w.n_query, nsample, replace=False)
+    idx = pl.idx.cpu().numpy()[q].astype(np.int64)
+    dist = pl.dist.cpu().numpy()[q].astype(np.float64)
+    G = XT[w.n_query:]
+    err = 0.0
+    for t, qi in enumerate(q):
+        diff = G[idx[t]] - XT[qi][None, :]
+        d = np.sum(diff * diff, axis=1)
+        err = max(err, float(np.max(np.abs(d - dist[t]))))
+    return err
+
+
+def run_ours(a):
+    import numpy as np
+    import torch
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    dist = None
+    if world > 1:
+        import torch.distributed as td
+        td.init_process_group("nccl")
+        torch.cuda.set_device(local)
+        dist = td
+    else:
+        torch.cuda.set_device(0)
+    from paper_2306_08792_gb300 import build
+    build.build()
+    import paper_2306_08792_gb300 as gcr
+    import workloads
+
+    if not gcr.device_supported(torch.cuda.current_device()):
+        raise SystemExit("libgcr needs an sm_103 GPU")
+    w = workloads.crosscam()
+    Xh = torch.from_numpy(w.X).pin_memory()
+    camh = torch.from_numpy(w.cam).pin_memory()
+    X = Xh.cuda()
+    cam = camh.cuda()
+
+    from paper_2306_08792_gb300 import _lib
+    prec_order = ["bf16", "fp32"] if a.precision == "auto" else [a.precision]
+    results = {}
+    sampler = ClockSampler(local)
+    sampler.mark_start()
+    for prec in prec_order:
+        try:
+            results[prec] = time_path(gcr, torch, w, X, cam, prec, a.steps, a.warmup, dist)
+        except gcr.GcrError as e:
+            if a.precision != "auto":
+                raise
+            results[prec] = {"error": str(e)}
+    sampler.mark_end()
+    clocks = sampler.result()
+    primary = next(p for p in prec_order if "ms" in results[p])
+    R = results[primary]
+    ms_local = R["ms"]
+    if dist:
+        t = torch.tensor([ms_local], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    else:
+        ms = ms_local
+    value = world * w.n_query / (ms / 1e3)
+
+    e2e_ms, h2d, d2h = time_e2e(gcr, torch, w, Xh, camh, R["pipeline"], max(3, a.steps // 2), 2)
+    if dist:
+        t = torch.tensor([e2e_ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_ms = float(t.item())
+    # one more untimed run that keeps the features, for the sampled error check
+    R["pipeline"](X, cam, keep_features=True)
+    torch.cuda.synchronize()
+    err = sampled_error(torch, R["pipeline"], w)
+
+    peaks, psrc = _peaks()
+    n, d = w.n, w.d
+    flops = 2.0 * n * n * d
+    sg = R["stages"]["sim_gemm"]
+    per_launch_ms = sg["ms"] / max(sg["calls"], 1)
+    achieved = flops / (per_launch_ms / 1e3) / 1e12
+    if primary == "bf16":
+        peak = peaks["bf16_tflops"]
+        roof = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                "frac": achieved / peak, "peak_source": f"bf16_tflops (burst) of {psrc}",
+                "kernel": "umma_pool_kernel (similarity GEMM + streaming top-k)",
+                "traffic": _traffic("umma_pool", ["umma.cu", "pool.cuh"])}
+    else:
+        peak = N_SMS * FP32_LANES_PER_SM * 2 * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
+        roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                "frac": achieved / peak, "peak_source": f"FP32 FMA: 152 SMs x 128 lanes x 2 x sm_max_mhz of {psrc}",
+                "kernel": "sgemm_pool_kernel (similarity GEMM + streaming top-k)",
+                "traffic": _traffic("sgemm_pool", ["sgemm.cu", "pool.cuh"])}
+    roof["flops_per_launch"] = flops
+    roof["ms_per_launch"] = per_launch_ms
+    roof["share_of_step"] = sg["ms"] / R["ms"]
+
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": a.steps,
+            "warmup": a.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": primary if primary == "bf16" else "f32", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "precision": primary,
+                       "l2": "flushed between steps (256 MB write outside the timed events); X is 158 MB > L2",
+                       "parallelism": "replicas" if world > 1 else "single GPU"},
+            "roofline": roof,
+            "e2e": {"value": world * w.n_query / (e2e_ms / 1e3), "unit": UNIT, "h2d_bytes_per_step": h2d,
+                    "d2h_bytes_per_step": d2h, "ms_per_step": e2e_ms},
+            "gpu_launches": int(R["launches"]), "clocks": clocks,
+            "stages_ms": {k: round(v["ms"], 4) for k, v in R["stages"].items()},
+            "knn_stats": R["stats"], "max_dist_err_fp64_sampled": err}
+    for prec in prec_order:
+        if prec != primary:
+            o = results[prec]
+            if "ms" in o:
+                line[f"{prec}_path"] = {"value": world * w.n_query / (o["ms"] / 1e3), "ms_per_step": o["ms"],
+                                        "stages_ms": {k: round(v["ms"], 4) for k, v in o["stages"].items()},
+                                        "knn_stats": o["stats"]}
+                line["speedup_vs_" + prec] = o["ms"] / R["ms"]
+            else:
+                line[f"{prec}_path"] = o
+    if rank == 0 and world == 1 and not a.no_cpu_baseline:
+        t0 = time.perf_counter()
+        est, det = oracle_sample_step(w)
+        line["cpu_baseline"] = {"value": w.n_query / est, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
+                                "sample": cpu_sample_description(), "wall_s": time.perf_counter() - t0,
+                                "stage_s": det}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+def main():
+    a = _args()
+    if a.impl == "reference":
+        run_reference(a)
+    else:
+        run_ours(a)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,200 @@
+/*
+ * gcr.h -- C ABI of the GB300 (sm_103a) implementation of Graph Convolution based
+ * Re-ranking (GCR) and its video extension (GCRV), arXiv 2306.08792.
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * - Pointers to feature matrices, graphs, outputs and workspaces are DEVICE pointers
+ *   (global memory of the current CUDA device) unless a comment says "host". The
+ *   caller owns every buffer; the library never allocates, frees or retains memory.
+ * - Feature matrices are row-major float32, one sample per row: X[i*d + c].
+ *   d must be a multiple of 4 (16-byte rows) and at most 4096; the BF16 tensor-core
+ *   path additionally needs d % 8 == 0.
+ * - Every call is asynchronous on the caller's stream (a cudaStream_t passed as
+ *   gcr_stream_t; NULL is the legacy default stream) and returns a gcr_status code.
+ *   Arguments are validated on the host before anything is launched; on a non-zero
+ *   status nothing has been launched. CUDA errors raised by earlier asynchronous work
+ *   surface as GCR_E_CUDA at a later call or at gcr_sync().
+ * - A call that needs scratch memory takes (void* ws, size_t ws_bytes); the needed
+ *   size comes from the matching *_workspace_size() query. Scratch contents need no
+ *   initialisation and are meaningless after the call. Distinct workspaces make calls
+ *   independent, so they may run concurrently on different streams.
+ * - Nothing in this file synchronises the device except gcr_sync().
+ *
+ * Notation follows the paper: X (features), N_i (the k nearest neighbours of sample i,
+ * i excluded), A~ (Eq. 4 affinity), D_r / D_c (Eq. 5 degrees), gamma (temperature),
+ * alpha (Eq. 9 mix), lambda (Eq. 17 regularisation), T (iterations, Eq. 3).
+ */
+#ifndef GCR_H
+#define GCR_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef void* gcr_stream_t; /* a cudaStream_t */
+
+typedef enum {
+  GCR_OK = 0,
+  GCR_E_INVALID = 1,     /* bad argument: null pointer, size or parameter out of range */
+  GCR_E_WORKSPACE = 2,   /* ws_bytes below the *_workspace_size() requirement */
+  GCR_E_CUDA = 3,        /* a CUDA runtime call or kernel launch failed */
+  GCR_E_TIMEOUT = 4,     /* a bounded device-side wait ran out (serving loop) */
+  GCR_E_UNSUPPORTED = 5  /* shape or mode not supported by this build or device */
+} gcr_status;
+
+typedef enum {
+  GCR_PREC_FP32 = 0, /* similarity GEMM on CUDA cores in FP32 (the reference path) */
+  GCR_PREC_BF16 = 1  /* similarity GEMM on tcgen05 tensor cores, BF16 x BF16 -> FP32,
+                        then boundary candidates re-scored in FP32 (FP64 for ties) */
+} gcr_precision;
+
+/* Hyper-parameters of one GCR run. gcr_default_params() fills the paper's defaults:
+ * k = 15, gamma = 0.2, T = 3 (Sec. IV-B), alpha = 0.7 (Sec. IV-D). */
+typedef struct {
+  int32_t k;            /* neighbours per sample, |N_i| (Eq. 4); 0 <= k < pool          */
+  float   gamma;        /* temperature of Eq. 4 / Eq. 8; > 0                             */
+  float   alpha;        /* weight of the global graph in Eq. 9; in [0, 1]; used only
+                           with cross_camera = 1                                          */
+  int32_t symmetric;    /* 1: A = (A~ + A~^T)/2 and D^{-1/2} A D^{-1/2} (Eq. 7, Eq. 2);
+                           0: D_r^{-1/2} A~ D_c^{-1/2} (Eq. 6)                            */
+  int32_t cross_camera; /* 1: add the cross-camera graph (Eq. 8) and mix by Eq. 9         */
+  int32_t precision;    /* gcr_precision                                                  */
+  int32_t pool;         /* per-row candidate pool of the streaming kNN search: 32 or 64;
+                           0 picks 32 for FP32 and 64 for BF16; must exceed k             */
+  int32_t topk_out;     /* gcr_rerank: results per query; 0 = the whole gallery           */
+  int32_t T;            /* iterations of Eq. 3, used by gcr_pipeline                      */
+} gcr_params;
+
+/* Counters written by gcr_build_graph (added to, never cleared by the library). */
+enum {
+  GCR_STAT_ROWS = 0,          /* (row, graph) pairs searched                               */
+  GCR_STAT_UNCERTIFIED = 1,   /* pairs whose candidate pool could not certify the k-th
+                                 neighbour and went through the threshold (band) rescan  */
+  GCR_STAT_BAND_FAILED = 2,   /* pairs whose band rescan overflowed; their sets are the
+                                 best available, not certified                            */
+  GCR_STAT_FP64_ROWS = 3,     /* pairs whose k-th / (k+1)-th boundary needed FP64          */
+  GCR_STAT_FP64_DOTS = 4,     /* FP64 dot products computed for those boundaries           */
+  GCR_STAT_CLAMPED = 5,       /* pairs with fewer than k eligible samples                  */
+  GCR_STAT_RESCORED = 6,      /* FP32 re-scored candidates                                 */
+  GCR_STATS_LEN = 8
+};
+
+/* The graph produced by gcr_build_graph and consumed by gcr_propagate. All arrays are
+ * device arrays owned by the caller and sized by gcr_graph_op_capacity() and n, k.
+ * Rows of nbr / nbr_cr list N_i (resp. N_i^cr) by ascending distance; a row with
+ * fewer than k eligible samples is padded with index -1 and distance +inf.
+ * The operator arrays hold, in CSR form, the matrix applied by one propagation layer:
+ *   symmetric:  alpha * D^{-1/2} A D^{-1/2} + (1 - alpha) * (same for the cross graph)
+ *   otherwise:  alpha * D_r^{-1/2} A~ D_c^{-1/2} + (1 - alpha) * (same for cross)
+ * (alpha = 1 when cross_camera = 0). Row i occupies op_col/op_val[op_rowptr[i] ..
+ * op_rowptr[i] + op_len[i]), sorted by column, one entry per column.              */
+typedef struct {
+  int32_t* nbr;       /* [n*k]  N_i (Eq. 4)                                        */
+  float*   nbr_d2;    /* [n*k]  ||x_i - x_j||^2 of those edges                      */
+  int32_t* nbr_cr;    /* [n*k]  N_i^cr (Eq. 8); may be NULL when cross_camera = 0   */
+  float*   nbr_cr_d2; /* [n*k]  may be NULL when cross_camera = 0                   */
+  float*   deg_r;     /* [n]    D_r of Eq. 5 (global graph)                         */
+  float*   deg_c;     /* [n]    D_c of Eq. 5 (global graph)                         */
+  float*   deg_r_cr;  /* [n]    D_r^cr (may be NULL when cross_camera = 0)          */
+  float*   deg_c_cr;  /* [n]    D_c^cr (may be NULL when cross_camera = 0)          */
+  int32_t* op_rowptr; /* [n+1]                                                      */
+  int32_t* op_len;    /* [n]                                                        */
+  int32_t* op_col;    /* [op_capacity]                                              */
+  float*   op_val;    /* [op_capacity]                                              */
+  int64_t* stats;     /* [GCR_STATS_LEN] device counters (may be NULL)              */
+} gcr_graph;
+
+/* ------------------------------------------------------------------ utilities */
+const char* gcr_status_string(int status);
+int gcr_version(void);
+/* Paper defaults (Sec. IV-B, IV-D): k=15, gamma=0.2, T=3, alpha=0.7, symmetric=1,
+ * cross_camera=0, precision=FP32, pool=0, topk_out=0. Host pointer. */
+void gcr_default_params(gcr_params* p);
+/* 1 if `device` is an sm_103 GPU this library was built for, else 0. */
+int gcr_device_supported(int device);
+/* cudaStreamSynchronize(stream) and report any pending CUDA error. */
+int gcr_sync(gcr_stream_t stream);
+
+/* ------------------------------------------------------------------ S0: normalise
+ * X_out[i] = X_in[i] / ||X_in[i]||_2 (zero rows stay zero). The method works on unit
+ * features: the profile derivation of Sec. III-D assumes ||x_i|| = 1, and each
+ * propagation layer ends with the same normalisation. X_in may equal X_out. */
+int gcr_normalize(const float* X_in, float* X_out, int64_t n, int32_t d, gcr_stream_t stream);
+
+/* ------------------------------------------------------------------ S1-S4: graph
+ * Builds, from the current features X (n x d, unit rows), the kNN graph of Eq. 4
+ * (and of Eq. 8 when cross_camera = 1, with cam[i] the camera of sample i), its
+ * degrees (Eq. 5) and the propagation operator (Eq. 6 or Eq. 7, mixed by Eq. 9).
+ * The all-pairs similarity is streamed tile by tile and never stored. kNN sets are
+ * exact: every candidate whose score lies within the certified error bound of the
+ * k-th is re-scored in FP32 and, where FP32 cannot separate two candidates, in FP64;
+ * exact FP64 ties go to the smaller index.
+ * cam: device int32[n], required when cross_camera = 1, else may be NULL.
+ * Errors: GCR_E_INVALID (n < 1, k out of range, gamma <= 0, alpha outside [0,1],
+ * pool <= k, missing arrays), GCR_E_UNSUPPORTED (d % 4, or d % 8 with BF16),
+ * GCR_E_WORKSPACE. */
+size_t gcr_graph_op_capacity(int64_t n, const gcr_params* p);
+size_t gcr_build_graph_workspace_size(int64_t n, int32_t d, const gcr_params* p);
+int gcr_build_graph(const float* X, int64_t n, int32_t d, const int32_t* cam,
+                    const gcr_params* p, gcr_graph* g, void* ws, size_t ws_bytes,
+                    gcr_stream_t stream);
+
+/* ------------------------------------------------------------------ S5: propagate
+ * One layer of Eq. 2 / Eq. 9 followed by the row L2 normalisation:
+ *   X_out[i] = normalise( sum_j M_ij X_in[j] ),  M = the operator stored in g.
+ * X_out must not alias X_in. No workspace. */
+int gcr_propagate(const gcr_graph* g, const float* X_in, float* X_out, int64_t n,
+                  int32_t d, gcr_stream_t stream);
+
+/* ------------------------------------------------------------------ S7: re-rank
+ * Re-ranked retrieval (Sec. III-A: retrieval uses the Euclidean distance of the
+ * updated features): for each query q, the gallery sorted by ascending
+ * ||x_q - x_g||^2, ties by gallery index. Writes idx_out[q*K + r] (gallery index of
+ * rank r) and dist_out[q*K + r], K = topk_out (or ng when topk_out = 0).
+ * precision = BF16 computes the distances on tensor cores (error ~1e-3 worst case).
+ * Errors: GCR_E_INVALID, GCR_E_UNSUPPORTED (K = ng above 16384), GCR_E_WORKSPACE. */
+size_t gcr_rerank_workspace_size(int64_t nq, int64_t ng, int32_t d, const gcr_params* p);
+int gcr_rerank(const float* Xq, int64_t nq, const float* Xg, int64_t ng, int32_t d,
+               const gcr_params* p, int32_t* idx_out, float* dist_out, void* ws,
+               size_t ws_bytes, gcr_stream_t stream);
+
+/* ------------------------------------------------------------------ S0-S7 in one call
+ * The whole offline re-ranking of Sec. III (Eq. 3 with T = p->T iterations):
+ * X_0 = normalise(X), X_t = normalise(M_t X_{t-1}) with the graph rebuilt from X_{t-1}
+ * each iteration, then gcr_rerank(X_T[0:nq], X_T[nq:n]). Queries are rows [0, nq).
+ * X_final (may be NULL) receives X_T. stats (may be NULL) receives the counters of
+ * every gcr_build_graph call. */
+size_t gcr_pipeline_workspace_size(int64_t n, int64_t nq, int32_t d, const gcr_params* p);
+int gcr_pipeline(const float* X, int64_t n, int64_t nq, int32_t d, const int32_t* cam,
+                 const gcr_params* p, float* X_final, int32_t* idx_out, float* dist_out,
+                 int64_t* stats, void* ws, size_t ws_bytes, gcr_stream_t stream);
+
+/* ------------------------------------------------------------------ stage profiler
+ * Process-wide, for measurement only (not thread-safe). While enabled, every entry point
+ * records a CUDA event pair on its stream around each stage below. gcr_profile_read()
+ * waits for the recorded events, writes per stage the summed milliseconds, kernel launches
+ * and timed calls (arrays of n_stages entries, host pointers) and clears the records.
+ * At most 4096 stage records are kept between reads. */
+enum {
+  GCR_STAGE_NORMALIZE = 0, /* S0 row normalisation                         */
+  GCR_STAGE_PREP = 1,      /* row norms, BF16 shadow, error bounds          */
+  GCR_STAGE_SIM_GEMM = 2,  /* S1+S2 similarity GEMM fused with the top-k    */
+  GCR_STAGE_REFINE = 3,    /* S3 certified refinement of the pools          */
+  GCR_STAGE_BAND = 4,      /* S3 threshold rescan of uncertified rows       */
+  GCR_STAGE_GRAPH = 5,     /* S4 weights, degrees, transpose, operator      */
+  GCR_STAGE_PROPAGATE = 6, /* S5 propagation + L2 normalisation             */
+  GCR_STAGE_DIST_GEMM = 7, /* S7 re-ranked distance GEMM                    */
+  GCR_STAGE_SORT = 8,      /* S7 segmented sort                             */
+  GCR_STAGES = 12
+};
+int gcr_profile_enable(int on);
+int gcr_profile_read(double* ms, int64_t* launches, int64_t* calls, int n_stages);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* GCR_H */

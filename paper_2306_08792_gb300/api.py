@@ -1,0 +1,206 @@
+"""Python binding of the C ABI: the same entry points, taking and returning torch tensors.
+
+Argument marshalling only: each function checks shapes and dtypes, takes device pointers
+from CUDA tensors, sizes and allocates the workspace with torch, and calls the library on
+torch's current stream. Every computation runs in the library's kernels; there is no CPU
+path and a missing library raises.
+"""
+from __future__ import annotations
+
+import ctypes
+from dataclasses import dataclass
+from typing import Optional
+
+import torch
+
+from . import _lib
+from ._lib import GCR_PREC_BF16, GCR_PREC_FP32, Graph, Params
+
+
+class GcrError(RuntimeError):
+    def __init__(self, status: int, where: str):
+        msg = _lib.load().gcr_status_string(status).decode()
+        super().__init__(f"{where}: {msg} (status {status})")
+        self.status = status
+
+
+def _check(status: int, where: str):
+    if status != 0:
+        raise GcrError(status, where)
+
+
+def _stream(stream=None):
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def _ptr(t: Optional[torch.Tensor]):
+    return ctypes.c_void_p(t.data_ptr()) if t is not None else ctypes.c_void_p(0)
+
+
+def _dev_f32(X: torch.Tensor, name: str) -> torch.Tensor:
+    if not (X.is_cuda and X.dtype == torch.float32 and X.dim() == 2 and X.is_contiguous()):
+        raise ValueError(f"{name} must be a contiguous float32 CUDA matrix")
+    return X
+
+
+def default_params(**kw) -> Params:
+    """The paper's defaults (k=15, gamma=0.2, T=3, alpha=0.7), overridden by keyword."""
+    p = Params()
+    _lib.load().gcr_default_params(ctypes.byref(p))
+    for k, v in kw.items():
+        if k == "precision" and isinstance(v, str):
+            v = {"fp32": GCR_PREC_FP32, "bf16": GCR_PREC_BF16}[v]
+        setattr(p, k, v)
+    return p
+
+
+def gcr_normalize(X: torch.Tensor, out: Optional[torch.Tensor] = None, stream=None) -> torch.Tensor:
+    X = _dev_f32(X, "X")
+    out = torch.empty_like(X) if out is None else out
+    _check(_lib.load().gcr_normalize(_ptr(X), _ptr(out), X.shape[0], X.shape[1], _stream(stream)), "gcr_normalize")
+    return out
+
+
+@dataclass
+class GraphTensors:
+    """Device arrays of one built graph (see gcr_graph in include/gcr.h)."""
+    nbr: torch.Tensor
+    nbr_d2: torch.Tensor
+    nbr_cr: Optional[torch.Tensor]
+    nbr_cr_d2: Optional[torch.Tensor]
+    deg_r: torch.Tensor
+    deg_c: torch.Tensor
+    deg_r_cr: Optional[torch.Tensor]
+    deg_c_cr: Optional[torch.Tensor]
+    op_rowptr: torch.Tensor
+    op_len: torch.Tensor
+    op_col: torch.Tensor
+    op_val: torch.Tensor
+    stats: torch.Tensor
+
+    def struct(self) -> Graph:
+        g = Graph()
+        for f, _t in Graph._fields_:
+            setattr(g, f, getattr(self, f).data_ptr() if getattr(self, f) is not None else None)
+        return g
+
+    def stats_dict(self):
+        v = self.stats.cpu().tolist()
+        return {name: int(v[i]) for i, name in enumerate(_lib.STAT_NAMES)}
+
+
+def alloc_graph(n: int, p: Params, device) -> GraphTensors:
+    lib = _lib.load()
+    cap = lib.gcr_graph_op_capacity(n, ctypes.byref(p))
+    cross = bool(p.cross_camera)
+    k = p.k
+    i32, f32 = torch.int32, torch.float32
+    e = lambda *s, dt: torch.empty(*s, dtype=dt, device=device)  # noqa: E731
+    return GraphTensors(
+        nbr=e(n, k, dt=i32), nbr_d2=e(n, k, dt=f32),
+        nbr_cr=e(n, k, dt=i32) if cross else None, nbr_cr_d2=e(n, k, dt=f32) if cross else None,
+        deg_r=e(n, dt=f32), deg_c=e(n, dt=f32),
+        deg_r_cr=e(n, dt=f32) if cross else None, deg_c_cr=e(n, dt=f32) if cross else None,
+        op_rowptr=e(n + 1, dt=i32), op_len=e(n, dt=i32), op_col=e(max(cap, 1), dt=i32),
+        op_val=e(max(cap, 1), dt=f32),
+        stats=torch.zeros(_lib.GCR_STATS_LEN, dtype=torch.int64, device=device))
+
+
+def gcr_build_graph(X: torch.Tensor, p: Params, cam: Optional[torch.Tensor] = None,
+                    graph: Optional[GraphTensors] = None, ws: Optional[torch.Tensor] = None,
+                    stream=None) -> GraphTensors:
+    """kNN graph(s), degrees and propagation operator of the current features X (unit rows)."""
+    X = _dev_f32(X, "X")
+    n, d = X.shape
+    lib = _lib.load()
+    if cam is not None:
+        if not (cam.is_cuda and cam.dtype == torch.int32 and cam.is_contiguous() and cam.numel() == n):
+            raise ValueError("cam must be a contiguous int32 CUDA vector of length n")
+    need = lib.gcr_build_graph_workspace_size(n, d, ctypes.byref(p))
+    if need == 0:
+        _check(lib.gcr_build_graph(_ptr(X), n, d, _ptr(cam), ctypes.byref(p), None, None, 0, _stream(stream)),
+               "gcr_build_graph")
+    if ws is None or ws.numel() < need:
+        ws = torch.empty(need, dtype=torch.uint8, device=X.device)
+    g = alloc_graph(n, p, X.device) if graph is None else graph
+    gs = g.struct()
+    _check(lib.gcr_build_graph(_ptr(X), n, d, _ptr(cam), ctypes.byref(p), ctypes.byref(gs), _ptr(ws),
+                               ws.numel(), _stream(stream)), "gcr_build_graph")
+    return g
+
+
+def gcr_propagate(graph: GraphTensors, X: torch.Tensor, out: Optional[torch.Tensor] = None,
+                  stream=None) -> torch.Tensor:
+    """One layer: out = normalise(M X) with M the operator held by `graph`."""
+    X = _dev_f32(X, "X")
+    out = torch.empty_like(X) if out is None else out
+    gs = graph.struct()
+    _check(_lib.load().gcr_propagate(ctypes.byref(gs), _ptr(X), _ptr(out), X.shape[0], X.shape[1],
+                                     _stream(stream)), "gcr_propagate")
+    return out
+
+
+def gcr_rerank(Xq: torch.Tensor, Xg: torch.Tensor, p: Params, stream=None):
+    """Per query: gallery indices by ascending squared distance (ties by index) and the distances."""
+    Xq = _dev_f32(Xq, "Xq")
+    Xg = _dev_f32(Xg, "Xg")
+    nq, d = Xq.shape
+    ng = Xg.shape[0]
+    lib = _lib.load()
+    K = min(p.topk_out, ng) if p.topk_out > 0 else ng
+    need = lib.gcr_rerank_workspace_size(nq, ng, d, ctypes.byref(p))
+    idx = torch.empty(nq, K, dtype=torch.int32, device=Xq.device)
+    dist = torch.empty(nq, K, dtype=torch.float32, device=Xq.device)
+    ws = torch.empty(max(need, 1), dtype=torch.uint8, device=Xq.device)
+    _check(lib.gcr_rerank(_ptr(Xq), nq, _ptr(Xg), ng, d, ctypes.byref(p), _ptr(idx), _ptr(dist), _ptr(ws),
+                          need, _stream(stream)), "gcr_rerank")
+    return idx, dist
+
+
+class Pipeline:
+    """Whole re-ranking (normalise, T x (graph, propagate), re-rank) with reusable buffers."""
+
+    def __init__(self, n: int, nq: int, d: int, p: Params, device="cuda"):
+        self.n, self.nq, self.d, self.p = n, nq, d, p
+        lib = _lib.load()
+        need = lib.gcr_pipeline_workspace_size(n, nq, d, ctypes.byref(p))
+        if need == 0:
+            raise GcrError(_lib.GCR_E_INVALID, "gcr_pipeline_workspace_size")
+        ng = n - nq
+        K = min(p.topk_out, ng) if p.topk_out > 0 else ng
+        self.ws = torch.empty(need, dtype=torch.uint8, device=device)
+        self.idx = torch.empty(nq, K, dtype=torch.int32, device=device)
+        self.dist = torch.empty(nq, K, dtype=torch.float32, device=device)
+        self.X_final = torch.empty(n, d, dtype=torch.float32, device=device)
+        self.stats = torch.zeros(_lib.GCR_STATS_LEN, dtype=torch.int64, device=device)
+
+    def __call__(self, X: torch.Tensor, cam: Optional[torch.Tensor] = None, keep_features: bool = True,
+                 stream=None):
+        X = _dev_f32(X, "X")
+        lib = _lib.load()
+        _check(lib.gcr_pipeline(_ptr(X), self.n, self.nq, self.d, _ptr(cam), ctypes.byref(self.p),
+                                _ptr(self.X_final) if keep_features else ctypes.c_void_p(0), _ptr(self.idx),
+                                _ptr(self.dist), _ptr(self.stats), _ptr(self.ws), self.ws.numel(),
+                                _stream(stream)), "gcr_pipeline")
+        return self.idx, self.dist
+
+    def stats_dict(self):
+        v = self.stats.cpu().tolist()
+        return {name: int(v[i]) for i, name in enumerate(_lib.STAT_NAMES)}
+
+
+def gcr_pipeline(X: torch.Tensor, nq: int, p: Params, cam: Optional[torch.Tensor] = None, stream=None):
+    """One-shot wrapper of :class:`Pipeline`; returns (idx, dist, X_T, stats)."""
+    n, d = X.shape
+    pl = Pipeline(n, nq, d, p, device=X.device)
+    idx, dist = pl(X, cam, stream=stream)
+    return idx, dist, pl.X_final, pl.stats_dict()
+
+
+def gcr_sync(stream=None):
+    _check(_lib.load().gcr_sync(_stream(stream)), "gcr_sync")
+
+
+def device_supported(device: int = 0) -> bool:
+    return bool(_lib.load().gcr_device_supported(device))

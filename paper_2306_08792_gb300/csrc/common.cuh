@@ -1,0 +1,102 @@
+// Shared device/host helpers of the GCR library (sm_103a).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <math_constants.h>
+
+#include "../../include/gcr.h"
+
+#define GCR_FULL 0xffffffffu
+
+namespace gcr {
+
+constexpr int kMaxK = 64;          // largest k supported by the kNN search
+constexpr int kQCap = 32;          // survivors queued per row before a merge
+
+__host__ __device__ inline size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+
+// Bump allocator over the caller's workspace (256-byte aligned slices).
+struct Carve {
+  char* base;
+  size_t off;
+  size_t cap;
+  __host__ Carve(void* b, size_t c) : base((char*)b), off(0), cap(c) {}
+  template <typename T>
+  __host__ T* take(size_t count) {
+    off = align_up(off, 256);
+    T* p = (T*)(base ? base + off : nullptr);
+    off += count * sizeof(T);
+    return p;
+  }
+};
+
+// Strict total order used by every top-k structure: larger value first, then smaller index.
+__device__ __forceinline__ bool better(float a, int ai, float b, int bi) {
+  return a > b || (a == b && ai < bi);
+}
+__device__ __forceinline__ bool better_d(double a, int ai, double b, int bi) {
+  return a > b || (a == b && ai < bi);
+}
+
+__device__ __forceinline__ float warp_sum(float v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(GCR_FULL, v, o);
+  return v;
+}
+__device__ __forceinline__ double warp_sum_d(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(GCR_FULL, v, o);
+  return v;
+}
+
+// Descending bitonic sort of 32 (value, index) pairs held one per lane.
+__device__ __forceinline__ void warp_sort32_desc(float& v, int& vi, int lane) {
+#pragma unroll
+  for (int size = 2; size <= 32; size <<= 1) {
+#pragma unroll
+    for (int stride = size >> 1; stride > 0; stride >>= 1) {
+      float ov = __shfl_xor_sync(GCR_FULL, v, stride);
+      int oi = __shfl_xor_sync(GCR_FULL, vi, stride);
+      bool desc = (lane & size) == 0 || size == 32;
+      bool lower = (lane & stride) == 0;
+      bool take = (lower == desc) ? better(ov, oi, v, vi) : better(v, vi, ov, oi);
+      if (take) { v = ov; vi = oi; }
+    }
+  }
+}
+
+// Descending bitonic merge of a bitonic sequence of 32 pairs held one per lane.
+__device__ __forceinline__ void warp_merge32_desc(float& v, int& vi, int lane) {
+#pragma unroll
+  for (int stride = 16; stride > 0; stride >>= 1) {
+    float ov = __shfl_xor_sync(GCR_FULL, v, stride);
+    int oi = __shfl_xor_sync(GCR_FULL, vi, stride);
+    bool lower = (lane & stride) == 0;
+    bool take = lower ? better(ov, oi, v, vi) : better(v, vi, ov, oi);
+    if (take) { v = ov; vi = oi; }
+  }
+}
+
+// float -> uint32 whose unsigned order equals the float order (ascending).
+__device__ __forceinline__ uint32_t float_to_ordered(float f) {
+  uint32_t u = __float_as_uint(f);
+  return (u & 0x80000000u) ? ~u : (u | 0x80000000u);
+}
+__device__ __forceinline__ float ordered_to_float(uint32_t u) {
+  return __uint_as_float((u & 0x80000000u) ? (u & 0x7fffffffu) : ~u);
+}
+
+}  // namespace gcr
+
+#define GCR_CUDA_TRY(expr)                         \
+  do {                                             \
+    cudaError_t _e = (expr);                       \
+    if (_e != cudaSuccess) return GCR_E_CUDA;      \
+  } while (0)
+
+#define GCR_LAUNCH_CHECK()                         \
+  do {                                             \
+    cudaError_t _e = cudaGetLastError();           \
+    if (_e != cudaSuccess) return GCR_E_CUDA;      \
+  } while (0)

@@ -1,0 +1,383 @@
+// Affinity weights, degrees and the propagation operator (Eq. 4-9).
+//
+// From the kNN lists (ELL: row i lists N_i) this builds, per graph (global, cross-camera):
+//   w_ij = exp(-||x_i - x_j||^2 / gamma) for j in N_i        (Eq. 4 / Eq. 8; A~_ii = 1)
+//   D_r(i) = 1 + sum_{j in N_i} w_ij,  D_c(j) = 1 + sum_{i: j in N_i} w_ij       (Eq. 5)
+// and then one CSR matrix M_mix that a propagation layer applies:
+//   symmetric (Eq. 7, Eq. 2): M = D^{-1/2} (A~ + A~^T)/2 D^{-1/2}, D = (D_r + D_c)/2
+//   asymmetric (Eq. 6):       M = D_r^{-1/2} A~ D_c^{-1/2}
+//   M_mix = alpha M + (1 - alpha) M^cr (Eq. 9); alpha = 1 without the cross-camera graph.
+// The transpose A~^T is built by a counting sort whose segments are then sorted by source
+// row, so every sum (degrees, operator rows) runs in a fixed order: results are
+// bit-reproducible run to run. Operator rows are sorted by column with duplicate columns
+// (mutual neighbours, overlapping graphs) merged into one entry.
+#include "common.cuh"
+#include "kernels.h"
+
+namespace gcr {
+namespace {
+
+__global__ void weights_kernel(int n, int k, float gamma, const int32_t* __restrict__ nbr,
+                               const float* __restrict__ d2, float* __restrict__ w,
+                               float* __restrict__ deg_r, int* __restrict__ cnt) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  float acc = 1.0f;  // A~_ii = 1
+  for (int s = 0; s < k; ++s) {
+    const int j = nbr[(size_t)i * k + s];
+    float wij = 0.f;
+    if (j >= 0) {
+      wij = expf(-d2[(size_t)i * k + s] / gamma);
+      atomicAdd(&cnt[j], 1);
+    }
+    w[(size_t)i * k + s] = wij;
+    acc += wij;
+  }
+  deg_r[i] = acc;
+}
+
+// Exclusive scan of in[0, n) into out[0, n] (out[n] = total), one block of 1024 threads,
+// tiles of 4096 elements with a running carry.
+__global__ void scan_kernel(const int* __restrict__ in, int* __restrict__ out, int n) {
+  __shared__ int wsum[32];
+  __shared__ int carry_s;
+  const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+  if (tid == 0) carry_s = 0;
+  __syncthreads();
+  for (int base = 0; base < n; base += 4096) {
+    int v[4];
+    int loc = 0;
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+      const int idx = base + tid * 4 + e;
+      v[e] = idx < n ? in[idx] : 0;
+      loc += v[e];
+    }
+    int incl = loc;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      int t = __shfl_up_sync(GCR_FULL, incl, o);
+      if (lane >= o) incl += t;
+    }
+    if (lane == 31) wsum[w] = incl;
+    __syncthreads();
+    if (w == 0) {
+      int s = wsum[lane];
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        int t = __shfl_up_sync(GCR_FULL, s, o);
+        if (lane >= o) s += t;
+      }
+      wsum[lane] = s;
+    }
+    __syncthreads();
+    const int carry = carry_s;
+    int run = carry + (w > 0 ? wsum[w - 1] : 0) + incl - loc;
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+      const int idx = base + tid * 4 + e;
+      if (idx < n) out[idx] = run;
+      run += v[e];
+    }
+    __syncthreads();
+    if (tid == 1023) carry_s = run;
+    __syncthreads();
+  }
+  if (tid == 0) out[n] = carry_s;
+}
+
+__global__ void scatter_kernel(int n, int k, const int32_t* __restrict__ nbr, const float* __restrict__ w,
+                               const int* __restrict__ tptr, int* __restrict__ fill,
+                               int* __restrict__ src_tmp, float* __restrict__ w_tmp) {
+  const long t = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= (long)n * k) return;
+  const int i = (int)(t / k);
+  const int j = nbr[t];
+  if (j < 0) return;
+  const int pos = tptr[j] + atomicAdd(&fill[j], 1);
+  src_tmp[pos] = i;
+  w_tmp[pos] = w[t];
+}
+
+// Sorting 64-bit keys held P per lane (element e = p*32 + lane), ascending, payload float.
+template <int P>
+__device__ __forceinline__ void warp_sort_keys(unsigned long long (&key)[P], float (&pay)[P], int lane) {
+  constexpr int N = 32 * P;
+#pragma unroll
+  for (int size = 2; size <= N; size <<= 1) {
+#pragma unroll
+    for (int stride = size >> 1; stride > 0; stride >>= 1) {
+      if (stride >= 32) {
+#pragma unroll
+        for (int p = 0; p < P; ++p) {
+          const int q = p ^ (stride >> 5);
+          if (q > p) {
+            const int s = p * 32 + lane;
+            const bool asc = (s & size) == 0;
+            const bool sw = asc ? key[q] < key[p] : key[q] > key[p];
+            if (sw) {
+              unsigned long long tk = key[p]; key[p] = key[q]; key[q] = tk;
+              float tp = pay[p]; pay[p] = pay[q]; pay[q] = tp;
+            }
+          }
+        }
+      } else {
+#pragma unroll
+        for (int p = 0; p < P; ++p) {
+          const unsigned long long ok = __shfl_xor_sync(GCR_FULL, key[p], stride);
+          const float op = __shfl_xor_sync(GCR_FULL, pay[p], stride);
+          const int s = p * 32 + lane;
+          const bool asc = (s & size) == 0;
+          const bool lower = (s & stride) == 0;
+          const bool take = (lower == asc) ? ok < key[p] : ok > key[p];
+          if (take) { key[p] = ok; pay[p] = op; }
+        }
+      }
+    }
+  }
+}
+
+// Sort one transposed segment by source row (register bitonic for <= 32*P entries).
+template <int P>
+__device__ void tseg_sort_regs(int beg, int len, const int* __restrict__ src_tmp, const float* __restrict__ w_tmp,
+                               int* __restrict__ src, float* __restrict__ tw, int lane) {
+  unsigned long long key[P];
+  float pay[P];
+#pragma unroll
+  for (int p = 0; p < P; ++p) {
+    const int e = p * 32 + lane;
+    key[p] = e < len ? (unsigned long long)(unsigned)src_tmp[beg + e] : ~0ull;
+    pay[p] = e < len ? w_tmp[beg + e] : 0.f;
+  }
+  warp_sort_keys<P>(key, pay, lane);
+#pragma unroll
+  for (int p = 0; p < P; ++p) {
+    const int e = p * 32 + lane;
+    if (e < len) { src[beg + e] = (int)key[p]; tw[beg + e] = pay[p]; }
+  }
+}
+
+// One warp per transposed row j: sort its entries by source, then D_c(j) = 1 + sum.
+__global__ void tsort_kernel(int n, const int* __restrict__ tptr, const int* __restrict__ src_tmp,
+                             const float* __restrict__ w_tmp, int* __restrict__ src, float* __restrict__ tw,
+                             float* __restrict__ deg_c) {
+  const int lane = threadIdx.x & 31;
+  const int j = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  if (j >= n) return;
+  const int beg = tptr[j], len = tptr[j + 1] - beg;
+  if (len <= 32) tseg_sort_regs<1>(beg, len, src_tmp, w_tmp, src, tw, lane);
+  else if (len <= 64) tseg_sort_regs<2>(beg, len, src_tmp, w_tmp, src, tw, lane);
+  else if (len <= 128) tseg_sort_regs<4>(beg, len, src_tmp, w_tmp, src, tw, lane);
+  else if (len <= 256) tseg_sort_regs<8>(beg, len, src_tmp, w_tmp, src, tw, lane);
+  else {
+    // long segment (hub): rank sort, sources within a segment are distinct
+    for (int e = lane; e < len; e += 32) {
+      const int me = src_tmp[beg + e];
+      int rank = 0;
+      for (int f = 0; f < len; ++f) rank += src_tmp[beg + f] < me;
+      src[beg + rank] = me;
+      tw[beg + rank] = w_tmp[beg + e];
+    }
+  }
+  __syncwarp();
+  if (lane == 0) {
+    float acc = 1.0f;  // A~_jj = 1
+    for (int e = 0; e < len; ++e) acc += tw[beg + e];
+    deg_c[j] = acc;
+  }
+}
+
+struct OpArgs {
+  int n, k, kinds, symmetric;
+  float coef[2];          // alpha, 1 - alpha
+  const int32_t* nbr[2];
+  const float* w[2];
+  const float* deg_r[2];
+  const float* deg_c[2];
+  const int* tptr[2];
+  const int* tsrc[2];
+  const float* tw[2];
+  const int* rowptr;
+  int* len;
+  int* col;
+  float* val;
+  int* raw_col;
+  float* raw_val;
+};
+
+__device__ __forceinline__ double degree_sym(const OpArgs& a, int g, int i) {
+  return 0.5 * ((double)a.deg_r[g][i] + (double)a.deg_c[g][i]);
+}
+
+__global__ void op_count_kernel(OpArgs a, int* __restrict__ cnt) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= a.n) return;
+  int c = 1;
+  for (int g = 0; g < a.kinds; ++g) {
+    c += a.k;
+    if (a.symmetric) c += a.tptr[g][i + 1] - a.tptr[g][i];
+  }
+  cnt[i] = c;
+}
+
+// Raw entries of operator row i in a fixed generation order: self, then per graph its
+// N_i entries (rank order) and, when symmetric, its transposed entries (by source).
+__device__ __forceinline__ void gen_entry(const OpArgs& a, int i, int e, int& col, double& v) {
+  // e == 0: self loop
+  if (e == 0) {
+    double s = 0.0;
+    for (int g = 0; g < a.kinds; ++g) {
+      if (a.symmetric) s += a.coef[g] / degree_sym(a, g, i);
+      else s += a.coef[g] / sqrt((double)a.deg_r[g][i] * (double)a.deg_c[g][i]);
+    }
+    col = i;
+    v = s;
+    return;
+  }
+  int r = e - 1;
+  for (int g = 0; g < a.kinds; ++g) {
+    if (r < a.k) {
+      const int j = a.nbr[g][(size_t)i * a.k + r];
+      const double wij = a.w[g][(size_t)i * a.k + r];
+      if (j < 0) { col = -1; v = 0.0; return; }
+      col = j;
+      if (a.symmetric) v = a.coef[g] * 0.5 * wij / sqrt(degree_sym(a, g, i) * degree_sym(a, g, j));
+      else v = a.coef[g] * wij / sqrt((double)a.deg_r[g][i] * (double)a.deg_c[g][j]);
+      return;
+    }
+    r -= a.k;
+    if (a.symmetric) {
+      const int tb = a.tptr[g][i], tl = a.tptr[g][i + 1] - tb;
+      if (r < tl) {
+        const int s = a.tsrc[g][tb + r];
+        const double wsi = a.tw[g][tb + r];
+        col = s;
+        v = a.coef[g] * 0.5 * wsi / sqrt(degree_sym(a, g, i) * degree_sym(a, g, s));
+        return;
+      }
+      r -= tl;
+    }
+  }
+  col = -1;
+  v = 0.0;
+}
+
+template <int P>
+__device__ void op_row_regs(const OpArgs& a, int i, int beg, int L, int lane) {
+  unsigned long long key[P];
+  float pay[P];
+#pragma unroll
+  for (int p = 0; p < P; ++p) {
+    const int e = p * 32 + lane;
+    int c = -1;
+    double v = 0.0;
+    if (e < L) gen_entry(a, i, e, c, v);
+    // key: column, then generation position (invalid entries sort last)
+    key[p] = c >= 0 ? (((unsigned long long)(unsigned)c << 32) | (unsigned)e) : ~0ull;
+    pay[p] = (float)v;
+  }
+  warp_sort_keys<P>(key, pay, lane);
+  // stage sorted entries in the raw buffer, then merge runs of equal columns
+#pragma unroll
+  for (int p = 0; p < P; ++p) {
+    const int e = p * 32 + lane;
+    if (e < L) {
+      a.raw_col[beg + e] = key[p] == ~0ull ? -1 : (int)(key[p] >> 32);
+      a.raw_val[beg + e] = pay[p];
+    }
+  }
+  __syncwarp();
+  int written = 0;
+  for (int e0 = 0; e0 < L; e0 += 32) {
+    const int e = e0 + lane;
+    int c = e < L ? a.raw_col[beg + e] : -1;
+    const bool head = c >= 0 && (e == 0 || a.raw_col[beg + e - 1] != c);
+    float v = 0.f;
+    if (head) {
+      v = a.raw_val[beg + e];
+      for (int f = e + 1; f < L && a.raw_col[beg + f] == c; ++f) v += a.raw_val[beg + f];
+    }
+    const unsigned hm = __ballot_sync(GCR_FULL, head);
+    if (head) {
+      const int pos = written + __popc(hm & ((1u << lane) - 1));
+      a.col[beg + pos] = c;
+      a.val[beg + pos] = v;
+    }
+    written += __popc(hm);
+  }
+  if (lane == 0) a.len[i] = written;
+}
+
+// One warp per operator row.
+__global__ void op_fill_kernel(OpArgs a) {
+  const int lane = threadIdx.x & 31;
+  const int i = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  if (i >= a.n) return;
+  const int beg = a.rowptr[i], L = a.rowptr[i + 1] - beg;
+  if (L <= 32) op_row_regs<1>(a, i, beg, L, lane);
+  else if (L <= 64) op_row_regs<2>(a, i, beg, L, lane);
+  else if (L <= 128) op_row_regs<4>(a, i, beg, L, lane);
+  else if (L <= 256) op_row_regs<8>(a, i, beg, L, lane);
+  else {
+    // very long row (hub): keep the entries unmerged, in generation order
+    int written = 0;
+    for (int e0 = 0; e0 < L; e0 += 32) {
+      const int e = e0 + lane;
+      int c = -1;
+      double v = 0.0;
+      if (e < L) gen_entry(a, i, e, c, v);
+      const unsigned hm = __ballot_sync(GCR_FULL, c >= 0);
+      if (c >= 0) {
+        const int pos = written + __popc(hm & ((1u << lane) - 1));
+        a.col[beg + pos] = c;
+        a.val[beg + pos] = (float)v;
+      }
+      written += __popc(hm);
+    }
+    if (lane == 0) a.len[i] = written;
+  }
+}
+
+}  // namespace
+
+cudaError_t launch_build_operator(const GraphArgs& g, cudaStream_t st) {
+  const int n = g.n, k = g.k;
+  cudaError_t e;
+  for (int q = 0; q < g.kinds; ++q) {
+    e = cudaMemsetAsync(g.cnt[q], 0, sizeof(int) * (n + 1), st);
+    if (e != cudaSuccess) return e;
+    e = cudaMemsetAsync(g.fill[q], 0, sizeof(int) * n, st);
+    if (e != cudaSuccess) return e;
+    weights_kernel<<<(n + 255) / 256, 256, 0, st>>>(n, k, g.gamma, g.nbr[q], g.d2[q], g.w[q], g.deg_r[q], g.cnt[q]);
+    // exclusive scan of the in-degree counts: transposed row pointers (into scan_tmp, copied back)
+    scan_kernel<<<1, 1024, 0, st>>>(g.cnt[q], g.scan_tmp, n);
+    e = cudaMemcpyAsync(g.cnt[q], g.scan_tmp, sizeof(int) * (n + 1), cudaMemcpyDeviceToDevice, st);
+    if (e != cudaSuccess) return e;
+    if ((long)n * k > 0) {
+      // unsorted transpose into the operator's raw buffers, then sorted into t_src / t_w
+      scatter_kernel<<<(unsigned)(((long)n * k + 255) / 256), 256, 0, st>>>(
+          n, k, g.nbr[q], g.w[q], g.cnt[q], g.fill[q], g.op_col, g.op_val);
+    }
+    tsort_kernel<<<(n + 7) / 8, 256, 0, st>>>(n, g.cnt[q], g.op_col, g.op_val, g.t_src[q], g.t_w[q], g.deg_c[q]);
+  }
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+
+  OpArgs a;
+  a.n = n; a.k = k; a.kinds = g.kinds; a.symmetric = g.symmetric;
+  a.coef[0] = g.kinds == 2 ? g.alpha : 1.0f;
+  a.coef[1] = 1.0f - g.alpha;
+  for (int q = 0; q < 2; ++q) {
+    const int qq = q < g.kinds ? q : 0;
+    a.nbr[q] = g.nbr[qq]; a.w[q] = g.w[qq]; a.deg_r[q] = g.deg_r[qq]; a.deg_c[q] = g.deg_c[qq];
+    a.tptr[q] = g.cnt[qq]; a.tsrc[q] = g.t_src[qq]; a.tw[q] = g.t_w[qq];
+  }
+  a.rowptr = g.op_rowptr; a.len = g.op_len; a.col = g.op_col; a.val = g.op_val;
+  a.raw_col = g.raw_col; a.raw_val = g.raw_val;
+  op_count_kernel<<<(n + 255) / 256, 256, 0, st>>>(a, g.op_cnt);
+  scan_kernel<<<1, 1024, 0, st>>>(g.op_cnt, g.op_rowptr, n);
+  op_fill_kernel<<<(n + 7) / 8, 256, 0, st>>>(a);
+  return cudaGetLastError();
+}
+
+}  // namespace gcr

@@ -1,0 +1,470 @@
+// Certified refinement of the kNN candidate pools (exact N_i of Eq. 4 and N_i^cr of Eq. 8).
+//
+// The pool of row i holds its KP best GEMM scores s^_ij (descending); every score left
+// out is <= the last pool entry tau. With a rigorous bound |s^_ij - s_ij| <= delta_i for
+// the GEMM (FP32: gamma_d ||x_i|| max||x_j||; BF16: ||bf16(x_i)|| max||e_j|| +
+// ||e_i|| max||x_j|| + gamma_acc ||bf16(x_i)|| max||bf16(x_j)||, e = bf16(x) - x) the
+// refinement:
+//   1. re-scores in FP32 every pool entry that could still be among the k nearest
+//      (s^ >= s^_(k) - 2 delta - spread of ||x_j||^2 / 2); one warp per (row, graph), each
+//      lane a d/32 slice then a butterfly, so |s~ - s| <= gamma_{d/32+6} ||x_i|| ||x_j||;
+//   2. ranks by sigma = s~ - ||x_j||^2 / 2, which orders like -||x_i - x_j||^2;
+//   3. certifies that no sample outside the pool can enter: sigma_(k) - eps > tau + delta -
+//      min||x_j||^2 / 2; rows that fail are queued for a threshold rescan (band);
+//   4. settles the k-th / (k+1)-th boundary in FP64 where FP32 cannot separate candidates;
+//      exact FP64 ties go to the smaller index.
+#include <cuda_bf16.h>
+
+#include "common.cuh"
+#include "kernels.h"
+
+namespace gcr {
+namespace {
+
+constexpr double kU32 = 5.9604644775390625e-08;  // 2^-24
+constexpr double kU32rz = 1.1920928955078125e-07; // 2^-23 (truncating accumulation)
+
+__device__ __forceinline__ double gamma_n(double h, double u) { return h * u / (1.0 - h * u); }
+
+// ---- warp list of 32*P entries, entry e = p*32 + lane: key sig (desc), index id, value val
+template <int P>
+struct WList {
+  double sig[P];
+  int id[P];
+  double val[P];
+};
+
+template <int P>
+__device__ __forceinline__ double wl_sig(const WList<P>& L, int e) {
+  double r = 0;
+#pragma unroll
+  for (int p = 0; p < P; ++p) {
+    double t = __shfl_sync(GCR_FULL, L.sig[p], e & 31);
+    if ((e >> 5) == p) r = t;
+  }
+  return r;
+}
+template <int P>
+__device__ __forceinline__ int wl_id(const WList<P>& L, int e) {
+  int r = 0;
+#pragma unroll
+  for (int p = 0; p < P; ++p) {
+    int t = __shfl_sync(GCR_FULL, L.id[p], e & 31);
+    if ((e >> 5) == p) r = t;
+  }
+  return r;
+}
+
+// Descending bitonic sort of the whole list by (sig, smaller id first).
+template <int P>
+__device__ __forceinline__ void wl_sort(WList<P>& L, int lane) {
+  constexpr int N = 32 * P;
+#pragma unroll
+  for (int size = 2; size <= N; size <<= 1) {
+#pragma unroll
+    for (int stride = size >> 1; stride > 0; stride >>= 1) {
+      if (stride == 32) {  // only for P == 2: partner lives in the same lane
+        if (P == 2 && better_d(L.sig[P - 1], L.id[P - 1], L.sig[0], L.id[0])) {
+          double ts = L.sig[0]; L.sig[0] = L.sig[P - 1]; L.sig[P - 1] = ts;
+          int ti = L.id[0]; L.id[0] = L.id[P - 1]; L.id[P - 1] = ti;
+          double tv = L.val[0]; L.val[0] = L.val[P - 1]; L.val[P - 1] = tv;
+        }
+      } else {
+#pragma unroll
+        for (int p = 0; p < P; ++p) {
+          double os = __shfl_xor_sync(GCR_FULL, L.sig[p], stride);
+          int oi = __shfl_xor_sync(GCR_FULL, L.id[p], stride);
+          double ov = __shfl_xor_sync(GCR_FULL, L.val[p], stride);
+          const int s = p * 32 + lane;
+          const bool desc = (s & size) == 0;
+          const bool lower = (s & stride) == 0;
+          const bool take = (lower == desc) ? better_d(os, oi, L.sig[p], L.id[p])
+                                            : better_d(L.sig[p], L.id[p], os, oi);
+          if (take) { L.sig[p] = os; L.id[p] = oi; L.val[p] = ov; }
+        }
+      }
+    }
+  }
+}
+
+// Merge a sorted-descending chunk of 32 (one per lane) into a sorted list of 64: keeps the top 64.
+__device__ __forceinline__ void wl_merge64(WList<2>& L, double cs, int ci, double cv, int lane) {
+  double rs = __shfl_sync(GCR_FULL, cs, 31 - lane);
+  int ri = __shfl_sync(GCR_FULL, ci, 31 - lane);
+  double rv = __shfl_sync(GCR_FULL, cv, 31 - lane);
+  if (better_d(rs, ri, L.sig[1], L.id[1])) { L.sig[1] = rs; L.id[1] = ri; L.val[1] = rv; }
+  if (better_d(L.sig[1], L.id[1], L.sig[0], L.id[0])) {
+    double ts = L.sig[0]; L.sig[0] = L.sig[1]; L.sig[1] = ts;
+    int ti = L.id[0]; L.id[0] = L.id[1]; L.id[1] = ti;
+    double tv = L.val[0]; L.val[0] = L.val[1]; L.val[1] = tv;
+  }
+#pragma unroll
+  for (int p = 0; p < 2; ++p) {
+#pragma unroll
+    for (int stride = 16; stride > 0; stride >>= 1) {
+      double os = __shfl_xor_sync(GCR_FULL, L.sig[p], stride);
+      int oi = __shfl_xor_sync(GCR_FULL, L.id[p], stride);
+      double ov = __shfl_xor_sync(GCR_FULL, L.val[p], stride);
+      const bool lower = (lane & stride) == 0;
+      const bool take = lower ? better_d(os, oi, L.sig[p], L.id[p]) : better_d(L.sig[p], L.id[p], os, oi);
+      if (take) { L.sig[p] = os; L.id[p] = oi; L.val[p] = ov; }
+    }
+  }
+}
+
+__device__ __forceinline__ void sort32_d(double& s, int& i, double& v, int lane) {
+#pragma unroll
+  for (int size = 2; size <= 32; size <<= 1) {
+#pragma unroll
+    for (int stride = size >> 1; stride > 0; stride >>= 1) {
+      double os = __shfl_xor_sync(GCR_FULL, s, stride);
+      int oi = __shfl_xor_sync(GCR_FULL, i, stride);
+      double ov = __shfl_xor_sync(GCR_FULL, v, stride);
+      const bool desc = (lane & size) == 0 || size == 32;
+      const bool lower = (lane & stride) == 0;
+      const bool take = (lower == desc) ? better_d(os, oi, s, i) : better_d(s, i, os, oi);
+      if (take) { s = os; i = oi; v = ov; }
+    }
+  }
+}
+
+// The row's own features, lane slice: elements v*128 + lane*4 .. +3.
+template <int VPL>
+__device__ __forceinline__ void load_row(const float* __restrict__ X, int d, int row, int lane, float4 (&xi)[VPL]) {
+  const float* base = X + (size_t)row * d;
+#pragma unroll
+  for (int v = 0; v < VPL; ++v) {
+    const int off = v * 128 + lane * 4;
+    xi[v] = off < d ? *reinterpret_cast<const float4*>(base + off) : make_float4(0.f, 0.f, 0.f, 0.f);
+  }
+}
+
+// FP32 dots of x_i with up to 4 rows (j < 0: skipped); sequential per-lane chain then butterfly.
+template <int VPL>
+__device__ __forceinline__ void dot4_f32(const float* __restrict__ X, int d, const float4 (&xi)[VPL],
+                                         const int (&j)[4], int lane, float (&out)[4]) {
+  float acc[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+  for (int v = 0; v < VPL; ++v) {
+    const int off = v * 128 + lane * 4;
+    if (off < d) {
+#pragma unroll
+      for (int t = 0; t < 4; ++t) {
+        if (j[t] >= 0) {
+          const float4 y = *reinterpret_cast<const float4*>(X + (size_t)j[t] * d + off);
+          acc[t] = fmaf(xi[v].x, y.x, acc[t]);
+          acc[t] = fmaf(xi[v].y, y.y, acc[t]);
+          acc[t] = fmaf(xi[v].z, y.z, acc[t]);
+          acc[t] = fmaf(xi[v].w, y.w, acc[t]);
+        }
+      }
+    }
+  }
+#pragma unroll
+  for (int t = 0; t < 4; ++t) out[t] = warp_sum(acc[t]);
+}
+
+template <int VPL>
+__device__ __forceinline__ double dot_f64(const float* __restrict__ X, int d, const float4 (&xi)[VPL],
+                                          int j, int lane) {
+  double acc = 0.0;
+#pragma unroll
+  for (int v = 0; v < VPL; ++v) {
+    const int off = v * 128 + lane * 4;
+    if (off < d) {
+      const float4 y = *reinterpret_cast<const float4*>(X + (size_t)j * d + off);
+      acc = fma((double)xi[v].x, (double)y.x, acc);
+      acc = fma((double)xi[v].y, (double)y.y, acc);
+      acc = fma((double)xi[v].z, (double)y.z, acc);
+      acc = fma((double)xi[v].w, (double)y.w, acc);
+    }
+  }
+  return warp_sum_d(acc);
+}
+
+// Re-scores entries [0, r) of L in FP32 (entry e's index is L.id), setting sig and val.
+template <int VPL, int P>
+__device__ __forceinline__ void rescore(const RefineArgs& a, const float4 (&xi)[VPL], WList<P>& L, int r, int lane) {
+  for (int e0 = 0; e0 < r; e0 += 4) {
+    int j[4];
+#pragma unroll
+    for (int t = 0; t < 4; ++t) {
+      const int e = e0 + t;
+      const int jj = wl_id(L, e < 32 * P ? e : 0);
+      j[t] = e < r ? jj : -1;
+    }
+    float s[4];
+    dot4_f32<VPL>(a.X, a.d, xi, j, lane, s);
+#pragma unroll
+    for (int t = 0; t < 4; ++t) {
+      const int e = e0 + t;
+      if (e < r) {
+#pragma unroll
+        for (int p = 0; p < P; ++p) {
+          if (e == p * 32 + lane) {
+            L.val[p] = (double)s[t];
+            L.sig[p] = (double)s[t] - 0.5 * a.n64[j[t]];
+          }
+        }
+      }
+    }
+  }
+}
+
+// Settles the k-th boundary of the FP32-ranked list L (sorted, r >= kk finite entries) and
+// writes the kk neighbours of (row, kind) with their squared distances; pads to k.
+template <int VPL, int P>
+__device__ void finalize(const RefineArgs& a, const float4 (&xi)[VPL], WList<P>& L, int r, int kk,
+                         double eps, int row, int kind, int lane) {
+  int32_t* onbr = a.nbr[kind] + (size_t)row * a.k;
+  float* od2 = a.d2[kind] + (size_t)row * a.k;
+  const double n_i = a.n64[row];
+  int acnt = kk, zcnt = kk;
+  int rank[P];
+#pragma unroll
+  for (int p = 0; p < P; ++p) rank[p] = 0;
+  if (r > kk) {
+    const double sig_next = wl_sig(L, kk);
+    const double sig_k = wl_sig(L, kk - 1);
+    acnt = 0;
+    zcnt = 0;
+#pragma unroll
+    for (int p = 0; p < P; ++p) {
+      const int e = p * 32 + lane;
+      acnt += __popc(__ballot_sync(GCR_FULL, e < kk && L.sig[p] - eps > sig_next + eps));
+      zcnt += __popc(__ballot_sync(GCR_FULL, e < r && L.sig[p] + eps >= sig_k - eps));
+    }
+    if (acnt < kk) {
+      // FP64 for the ambiguous entries [acnt, zcnt)
+      double sig64[P];
+#pragma unroll
+      for (int p = 0; p < P; ++p) sig64[p] = -CUDART_INF;
+      for (int e = acnt; e < zcnt; ++e) {
+        const int j = wl_id(L, e);
+        const double dot = dot_f64<VPL>(a.X, a.d, xi, j, lane);
+#pragma unroll
+        for (int p = 0; p < P; ++p) {
+          if (e == p * 32 + lane) {
+            L.val[p] = dot;
+            sig64[p] = dot - 0.5 * a.n64[j];
+          }
+        }
+      }
+      // rank of each ambiguous entry among the ambiguous ones (larger sig64 first, then index)
+      for (int e = acnt; e < zcnt; ++e) {
+        double os = -CUDART_INF;
+        int oi = 0;
+#pragma unroll
+        for (int p = 0; p < P; ++p) {
+          const double t = __shfl_sync(GCR_FULL, sig64[p], e & 31);
+          const int ti = __shfl_sync(GCR_FULL, L.id[p], e & 31);
+          if ((e >> 5) == p) { os = t; oi = ti; }
+        }
+#pragma unroll
+        for (int p = 0; p < P; ++p) {
+          const int me = p * 32 + lane;
+          if (me >= acnt && me < zcnt && me != e && better_d(os, oi, sig64[p], L.id[p])) ++rank[p];
+        }
+      }
+      if (lane == 0 && a.stats) {
+        atomicAdd(&a.stats[GCR_STAT_FP64_ROWS], 1ull);
+        atomicAdd(&a.stats[GCR_STAT_FP64_DOTS], (unsigned long long)(zcnt - acnt));
+      }
+    }
+  }
+#pragma unroll
+  for (int p = 0; p < P; ++p) {
+    const int e = p * 32 + lane;
+    int slot = -1;
+    if (e < acnt) slot = e;
+    else if (e >= acnt && e < zcnt && acnt < kk && rank[p] < kk - acnt) slot = acnt + rank[p];
+    if (slot >= 0) {
+      const int j = L.id[p];
+      double dd = n_i + a.n64[j] - 2.0 * L.val[p];
+      onbr[slot] = j;
+      od2[slot] = (float)(dd > 0.0 ? dd : 0.0);
+    }
+  }
+  for (int s = kk + lane; s < a.k; s += 32) {
+    onbr[s] = -1;
+    od2[s] = CUDART_INF_F;
+  }
+}
+
+template <int P>
+__device__ __forceinline__ void bounds(const RefineArgs& a, int row, int vpl, double& delta, double& eps,
+                                       RowScalars& sc) {
+  sc = *a.sc;
+  const double b_i = sqrt(a.n64[row]);
+  if (a.precision == GCR_PREC_FP32) {
+    delta = gamma_n((double)a.d, kU32) * b_i * sc.bmax;
+  } else {
+    const double ai = a.anrm[row], ei = a.enrm[row];
+    delta = ai * sc.emax + ei * sc.bmax + gamma_n((double)a.d + 32.0, kU32rz) * ai * sc.amax;
+  }
+  delta *= 1.0 + 1e-6;
+  eps = gamma_n((double)(4 * vpl + 6), kU32) * b_i * sc.bmax * (1.0 + 1e-6);
+}
+
+// One warp per (row, kind).
+template <int VPL, int P>
+__global__ void __launch_bounds__(256) refine_pool_kernel(RefineArgs a) {
+  constexpr int KP = 32 * P;
+  const int lane = threadIdx.x & 31;
+  const long wid = (long)blockIdx.x * 8 + (threadIdx.x >> 5);
+  if (wid >= (long)a.n * a.kinds) return;
+  const int kind = (int)(wid / a.n), row = (int)(wid % a.n);
+  const float* pv = a.pool_v + ((size_t)kind * a.n + row) * KP;
+  const int* pi = a.pool_i + ((size_t)kind * a.n + row) * KP;
+  WList<P> L;
+  float pval[P];
+  int mvalid = 0;
+#pragma unroll
+  for (int p = 0; p < P; ++p) {
+    pval[p] = pv[p * 32 + lane];
+    L.id[p] = pi[p * 32 + lane];
+    L.sig[p] = -CUDART_INF;
+    L.val[p] = 0.0;
+    mvalid += __popc(__ballot_sync(GCR_FULL, L.id[p] >= 0));
+  }
+  if (lane == 0 && a.stats) atomicAdd(&a.stats[GCR_STAT_ROWS], 1ull);
+  if (mvalid == 0) {
+    for (int s = lane; s < a.k; s += 32) {
+      a.nbr[kind][(size_t)row * a.k + s] = -1;
+      a.d2[kind][(size_t)row * a.k + s] = CUDART_INF_F;
+    }
+    if (lane == 0 && a.stats && a.k > 0) atomicAdd(&a.stats[GCR_STAT_CLAMPED], 1ull);
+    return;
+  }
+  const int kk = min(a.k, mvalid);
+  if (kk < a.k && lane == 0 && a.stats) atomicAdd(&a.stats[GCR_STAT_CLAMPED], 1ull);
+  if (kk == 0) return;
+  auto pool_at = [&](int e) {
+    float r = 0.f;
+#pragma unroll
+    for (int p = 0; p < P; ++p) {
+      float t = __shfl_sync(GCR_FULL, pval[p], e & 31);
+      if ((e >> 5) == p) r = t;
+    }
+    return r;
+  };
+  const float s_k = pool_at(kk - 1);
+  const float tau = pool_at(KP - 1);
+  double delta, eps;
+  RowScalars sc;
+  bounds<P>(a, row, VPL, delta, eps, sc);
+  const double thr = (double)s_k - 2.0 * delta - 0.5 * (sc.nmax - sc.nmin);
+  int r = 0;
+#pragma unroll
+  for (int p = 0; p < P; ++p) r += __popc(__ballot_sync(GCR_FULL, L.id[p] >= 0 && (double)pval[p] >= thr));
+  float4 xi[VPL];
+  load_row<VPL>(a.X, a.d, row, lane, xi);
+  rescore<VPL, P>(a, xi, L, r, lane);
+  if (lane == 0 && a.stats) atomicAdd(&a.stats[GCR_STAT_RESCORED], (unsigned long long)r);
+  wl_sort<P>(L, lane);
+  const double sig_k = wl_sig(L, kk - 1);
+  if (mvalid == KP) {
+    const bool cert = (sig_k - eps) > ((double)tau + delta - 0.5 * sc.nmin);
+    if (!cert && lane == 0) {
+      const int u = atomicAdd(a.unc_count, 1);
+      a.unc_row[u] = row;
+      a.unc_kind[u] = kind;
+      a.unc_thr[u] = __double2float_rd(sig_k - eps + 0.5 * sc.nmin - delta);
+      if (a.stats) atomicAdd(&a.stats[GCR_STAT_UNCERTIFIED], 1ull);
+    }
+  }
+  finalize<VPL, P>(a, xi, L, r, kk, eps, row, kind, lane);
+}
+
+// One warp per uncertified (row, kind): every band entry (score >= threshold) is re-scored.
+template <int VPL>
+__global__ void __launch_bounds__(256) refine_band_kernel(RefineArgs a) {
+  const int lane = threadIdx.x & 31;
+  const int U = *a.unc_count;
+  const int nw = gridDim.x * 8;
+  for (int u = blockIdx.x * 8 + (threadIdx.x >> 5); u < U; u += nw) {
+    const int row = a.unc_row[u], kind = a.unc_kind[u];
+    const int cnt = u < a.band_rows ? a.band_cnt[u] : a.bcap + 1;
+    if (cnt > a.bcap) {
+      if (lane == 0 && a.stats) atomicAdd(&a.stats[GCR_STAT_BAND_FAILED], 1ull);
+      continue;
+    }
+    double delta, eps;
+    RowScalars sc;
+    bounds<2>(a, row, VPL, delta, eps, sc);
+    float4 xi[VPL];
+    load_row<VPL>(a.X, a.d, row, lane, xi);
+    WList<2> L;
+#pragma unroll
+    for (int p = 0; p < 2; ++p) { L.sig[p] = -CUDART_INF; L.id[p] = 0x7fffffff; L.val[p] = 0.0; }
+    const int* bi = a.band_i + (size_t)u * a.bcap;
+    for (int c0 = 0; c0 < cnt; c0 += 32) {
+      WList<1> C;
+      C.id[0] = (c0 + lane < cnt) ? bi[c0 + lane] : -1;
+      C.sig[0] = -CUDART_INF;
+      C.val[0] = 0.0;
+      rescore<VPL, 1>(a, xi, C, min(32, cnt - c0), lane);
+      if (C.id[0] < 0) C.id[0] = 0x7fffffff;
+      sort32_d(C.sig[0], C.id[0], C.val[0], lane);
+      wl_merge64(L, C.sig[0], C.id[0], C.val[0], lane);
+    }
+    if (lane == 0 && a.stats) atomicAdd(&a.stats[GCR_STAT_RESCORED], (unsigned long long)cnt);
+    const int r = min(cnt, 64);
+    const int kk = min(a.k, r);
+    finalize<VPL, 2>(a, xi, L, r, kk, eps, row, kind, lane);
+  }
+}
+
+__global__ void gather_bf16_kernel(const __nv_bfloat16* __restrict__ Xb, int d, const int* __restrict__ count,
+                                   const int* __restrict__ rows, int max_rows, __nv_bfloat16* __restrict__ out) {
+  const int U = min(*count, max_rows);
+  const int d8 = d >> 3;
+  for (long t = (long)blockIdx.x * blockDim.x + threadIdx.x; t < (long)U * d8; t += (long)gridDim.x * blockDim.x) {
+    const long u = t / d8, c = t % d8;
+    reinterpret_cast<uint4*>(out + u * d)[c] = reinterpret_cast<const uint4*>(Xb + (size_t)rows[u] * d)[c];
+  }
+}
+
+template <int P>
+cudaError_t launch_pool_vpl(const RefineArgs& a, cudaStream_t st) {
+  const long warps = (long)a.n * a.kinds;
+  dim3 grid((unsigned)((warps + 7) / 8));
+  const int vpl = (a.d + 127) / 128;
+  if (vpl <= 1) refine_pool_kernel<1, P><<<grid, 256, 0, st>>>(a);
+  else if (vpl <= 2) refine_pool_kernel<2, P><<<grid, 256, 0, st>>>(a);
+  else if (vpl <= 4) refine_pool_kernel<4, P><<<grid, 256, 0, st>>>(a);
+  else if (vpl <= 8) refine_pool_kernel<8, P><<<grid, 256, 0, st>>>(a);
+  else if (vpl <= 16) refine_pool_kernel<16, P><<<grid, 256, 0, st>>>(a);
+  else if (vpl <= 32) refine_pool_kernel<32, P><<<grid, 256, 0, st>>>(a);
+  else return cudaErrorInvalidValue;
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t launch_refine_pool(const RefineArgs& a, cudaStream_t st) {
+  if (a.kp == 32) return launch_pool_vpl<1>(a, st);
+  if (a.kp == 64) return launch_pool_vpl<2>(a, st);
+  return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_refine_band(const RefineArgs& a, cudaStream_t st) {
+  dim3 grid(152 * 4);
+  const int vpl = (a.d + 127) / 128;
+  if (vpl <= 1) refine_band_kernel<1><<<grid, 256, 0, st>>>(a);
+  else if (vpl <= 2) refine_band_kernel<2><<<grid, 256, 0, st>>>(a);
+  else if (vpl <= 4) refine_band_kernel<4><<<grid, 256, 0, st>>>(a);
+  else if (vpl <= 8) refine_band_kernel<8><<<grid, 256, 0, st>>>(a);
+  else if (vpl <= 16) refine_band_kernel<16><<<grid, 256, 0, st>>>(a);
+  else if (vpl <= 32) refine_band_kernel<32><<<grid, 256, 0, st>>>(a);
+  else return cudaErrorInvalidValue;
+  return cudaGetLastError();
+}
+
+cudaError_t launch_gather_bf16(const __nv_bfloat16* Xb, int d, const int* count, const int* rows,
+                               int max_rows, __nv_bfloat16* out, cudaStream_t st) {
+  gather_bf16_kernel<<<152 * 4, 256, 0, st>>>(Xb, d, count, rows, max_rows, out);
+  return cudaGetLastError();
+}
+
+}  // namespace gcr

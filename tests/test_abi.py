@@ -1,0 +1,133 @@
+"""The C ABI library builds, loads and exports what include/gcr.h declares (CPU only).
+
+These tests only call host-side functions (status strings, defaults, size queries and
+argument validation, which returns before anything reaches the GPU).
+"""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2306_08792_gb300 import build, _lib
+    build.build()
+    return _lib.load()
+
+
+def _declared():
+    with open(os.path.join(ROOT, "include", "gcr.h")) as f:
+        text = f.read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    names = set(re.findall(r"\b((?:gcr|gcrv)_[a-z0-9_]+)\s*\(", text))
+    return sorted(names)
+
+
+def test_every_declared_symbol_is_exported(lib):
+    from paper_2306_08792_gb300 import _lib
+    declared = _declared()
+    assert len(declared) >= 14
+    for name in declared:
+        assert hasattr(lib, name), name
+        assert name in _lib.PROTOTYPES, name
+
+
+def test_status_strings(lib):
+    assert lib.gcr_status_string(0) == b"ok"
+    assert lib.gcr_status_string(2) == b"workspace too small"
+    assert lib.gcr_status_string(99) == b"unknown status"
+
+
+def test_defaults_are_the_papers(lib):
+    """Library defaults equal the values the paper prints (tests/golden/paper_defaults.txt)."""
+    from paper_2306_08792_gb300._lib import Params
+    vals = {}
+    with open(os.path.join(ROOT, "tests", "golden", "paper_defaults.txt")) as f:
+        for line in f:
+            if line.strip() and not line.startswith("#"):
+                k, v = line.split()
+                vals[k] = float(v)
+    p = Params()
+    lib.gcr_default_params(ctypes.byref(p))
+    assert p.k == vals["k"] and p.T == vals["T"]
+    assert abs(p.gamma - vals["gamma"]) < 1e-7 and abs(p.alpha - vals["alpha"]) < 1e-7
+    assert p.symmetric == 1
+
+
+def _params(lib, **kw):
+    from paper_2306_08792_gb300._lib import Params
+    p = Params()
+    lib.gcr_default_params(ctypes.byref(p))
+    for k, v in kw.items():
+        setattr(p, k, v)
+    return p
+
+
+def test_workspace_queries(lib):
+    p = _params(lib, k=20)
+    a = lib.gcr_build_graph_workspace_size(1000, 256, ctypes.byref(p))
+    b = lib.gcr_build_graph_workspace_size(2000, 256, ctypes.byref(p))
+    assert 0 < a < b
+    assert lib.gcr_graph_op_capacity(1000, ctypes.byref(p)) == 1000 * (1 + 2 * 20)
+    p2 = _params(lib, k=20, cross_camera=1)
+    assert lib.gcr_graph_op_capacity(1000, ctypes.byref(p2)) == 1000 * (1 + 4 * 20)
+    assert lib.gcr_build_graph_workspace_size(1000, 256, ctypes.byref(p2)) > a
+    assert lib.gcr_rerank_workspace_size(100, 900, 256, ctypes.byref(p)) > 100 * 900 * 4
+    assert lib.gcr_pipeline_workspace_size(1000, 100, 256, ctypes.byref(p)) > a
+
+
+@pytest.mark.parametrize("bad", [dict(k=-1), dict(k=32), dict(gamma=0.0), dict(gamma=-1.0),
+                                 dict(cross_camera=1, alpha=1.5), dict(precision=7), dict(pool=48),
+                                 dict(symmetric=2)])
+def test_invalid_params_rejected_on_host(lib, bad):
+    p = _params(lib, **bad)
+    assert lib.gcr_build_graph_workspace_size(1000, 256, ctypes.byref(p)) == 0
+    from paper_2306_08792_gb300._lib import Graph
+    g = Graph()
+    st = lib.gcr_build_graph(ctypes.c_void_p(16), 1000, 256, ctypes.c_void_p(16), ctypes.byref(p),
+                             ctypes.byref(g), ctypes.c_void_p(16), 1 << 30, None)
+    assert st == 1  # GCR_E_INVALID
+
+
+def test_unsupported_shapes(lib):
+    p = _params(lib, k=10)
+    assert lib.gcr_normalize(ctypes.c_void_p(16), ctypes.c_void_p(32), 10, 6, None) == 5
+    pb = _params(lib, k=10, precision=1)
+    from paper_2306_08792_gb300._lib import Graph
+    g = Graph()
+    assert lib.gcr_build_graph(ctypes.c_void_p(16), 100, 12, None, ctypes.byref(pb), ctypes.byref(g),
+                               ctypes.c_void_p(16), 1 << 30, None) == 5
+    assert lib.gcr_rerank_workspace_size(10, 20000, 256, ctypes.byref(p)) == 0
+
+
+def test_null_and_short_workspace(lib):
+    p = _params(lib, k=10)
+    from paper_2306_08792_gb300._lib import Graph
+    g = Graph()
+    for f in ("nbr", "nbr_d2", "deg_r", "deg_c", "op_rowptr", "op_len", "op_col", "op_val"):
+        setattr(g, f, 16)
+    assert lib.gcr_build_graph(ctypes.c_void_p(16), 100, 64, None, ctypes.byref(p), ctypes.byref(g),
+                               None, 0, None) == 2
+    assert lib.gcr_build_graph(ctypes.c_void_p(16), 100, 64, None, ctypes.byref(p), ctypes.byref(g),
+                               ctypes.c_void_p(16), 100, None) == 2
+    g.op_len = None
+    assert lib.gcr_build_graph(ctypes.c_void_p(16), 100, 64, None, ctypes.byref(p), ctypes.byref(g),
+                               ctypes.c_void_p(16), 1 << 30, None) == 1
+    # cross-camera without camera ids
+    pc = _params(lib, k=10, cross_camera=1)
+    assert lib.gcr_build_graph(ctypes.c_void_p(16), 100, 64, None, ctypes.byref(pc), ctypes.byref(g),
+                               ctypes.c_void_p(16), 1 << 30, None) == 1
+
+
+def test_product_package_does_not_import_oracle():
+    import subprocess
+    import sys
+    code = ("import sys, paper_2306_08792_gb300; "
+            "print(any(m == 'oracle' or m.startswith('oracle.') for m in sys.modules))")
+    out = subprocess.run([sys.executable, "-c", code], cwd=ROOT, capture_output=True, text=True)
+    assert out.returncode == 0, out.stderr
+    assert out.stdout.strip() == "False"

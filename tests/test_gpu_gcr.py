@@ -1,0 +1,241 @@
+"""GPU parity tests: the CUDA path (through the C ABI) against the FP64 oracle.
+
+Staged comparisons feed the oracle the GPU's own previous-stage output (upcast to FP64),
+so near-ties created upstream are not blamed downstream. Tolerances:
+  * kNN sets: identical except certified ties (oracle FP64 gap < 1e-9);
+  * normalisation: 2 ulp of FP32 (the kernel scales in FP64);
+  * operator entries, degrees: 1e-6 relative (FP32 weights of FP64-resolved edges);
+  * one propagation layer: 2e-6 absolute on unit rows (FP32 sums of <= 4k+1 terms);
+  * re-ranked distances (FP32 path): 1e-4 absolute.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import workloads
+from tests import parity
+
+pytestmark = pytest.mark.gpu
+
+PRECISIONS = ["fp32"]
+
+
+@pytest.fixture(scope="module")
+def gcr():
+    import paper_2306_08792_gb300 as g
+    from paper_2306_08792_gb300 import build
+    build.build()
+    assert g.device_supported(0), "this library targets sm_103 GPUs"
+    return g
+
+
+def _dev(a, dtype=torch.float32):
+    return torch.from_numpy(np.ascontiguousarray(a)).to(device="cuda", dtype=dtype)
+
+
+def _graph_host(G):
+    out = {}
+    for f in ("nbr", "nbr_d2", "nbr_cr", "nbr_cr_d2", "deg_r", "deg_c", "deg_r_cr", "deg_c_cr",
+              "op_rowptr", "op_len", "op_col", "op_val"):
+        v = getattr(G, f)
+        out[f] = v.cpu().numpy() if v is not None else None
+    return out
+
+
+def test_normalize_matches_fp64(gcr):
+    X, _ = workloads.random_unit_like(0, 777, 260)
+    X[5] = 0.0                                            # a zero row stays zero
+    Y = gcr.gcr_normalize(_dev(X)).cpu().numpy()
+    ref = oracle.l2_normalize(X)
+    np.testing.assert_allclose(Y, ref, rtol=0, atol=2 * np.finfo(np.float32).eps)
+    assert np.all(Y[5] == 0)
+
+
+@pytest.mark.parametrize("precision", PRECISIONS)
+def test_knn_plain_workload(gcr, precision):
+    w = workloads.plain()
+    X0 = gcr.gcr_normalize(_dev(w.X))
+    p = gcr.default_params(k=w.k, precision=precision)
+    G = gcr.gcr_build_graph(X0, p)
+    torch.cuda.synchronize()
+    X64 = X0.double().cpu().numpy()
+    r = parity.compare_knn(X64, np.arange(w.n), G.nbr.cpu().numpy(), w.k)
+    assert r["mismatched"] == 0, r
+    st = G.stats_dict()
+    assert st["rows"] == w.n and st["band_failed"] == 0
+
+
+@pytest.mark.parametrize("precision", PRECISIONS)
+def test_knn_cross_camera(gcr, precision):
+    w = workloads.crosscam(seed=3, n_query=400, n_gallery=2600, d=256, n_clusters=120)
+    X0 = gcr.gcr_normalize(_dev(w.X))
+    cam = _dev(w.cam, torch.int32)
+    p = gcr.default_params(k=w.k, cross_camera=1, alpha=0.7, precision=precision)
+    G = gcr.gcr_build_graph(X0, p, cam)
+    torch.cuda.synchronize()
+    X64 = X0.double().cpu().numpy()
+    r = parity.compare_knn(X64, np.arange(w.n), G.nbr.cpu().numpy(), w.k)
+    assert r["mismatched"] == 0, r
+    rc = parity.compare_knn(X64, np.arange(w.n), G.nbr_cr.cpu().numpy(), w.k, w.cam, cross=True)
+    assert rc["mismatched"] == 0, rc
+    nc = G.nbr_cr.cpu().numpy()
+    assert np.all(w.cam[nc] != w.cam[:, None])
+
+
+@pytest.mark.parametrize("precision", PRECISIONS)
+@pytest.mark.parametrize("n,d,k", [(1, 8, 5), (5, 12, 10), (130, 68, 7), (300, 256, 0), (257, 36, 31)])
+def test_knn_edge_shapes(gcr, precision, n, d, k):
+    X, cam = workloads.random_unit_like(n, n, d, cams=3)
+    X0 = gcr.gcr_normalize(_dev(X))
+    p = gcr.default_params(k=k, cross_camera=1, alpha=0.5, precision=precision)
+    if k >= 32:
+        p.pool = 64
+    G = gcr.gcr_build_graph(X0, p, _dev(cam, torch.int32))
+    torch.cuda.synchronize()
+    X64 = X0.double().cpu().numpy()
+    if k > 0:
+        for nbr, cross in ((G.nbr, False), (G.nbr_cr, True)):
+            r = parity.compare_knn(X64, np.arange(n), nbr.cpu().numpy(), k, cam, cross)
+            assert r["mismatched"] == 0, (cross, r)
+    # propagation through this graph matches the oracle's operator on the same sets
+    g_o = oracle.build_graph(X64, k, p.gamma, cam, True, True, 0.5,
+                             nbr=G.nbr.cpu().numpy(), nbr_cr=G.nbr_cr.cpu().numpy())
+    Y = gcr.gcr_propagate(G, X0).cpu().numpy()
+    np.testing.assert_allclose(Y, oracle.propagate(X64, g_o["M"]), atol=2e-6, rtol=0)
+
+
+def test_knn_exact_duplicates_and_ties(gcr):
+    """Duplicated rows tie exactly: only certified-tie swaps are allowed."""
+    rng = np.random.default_rng(5)
+    base = rng.standard_normal((60, 32)).astype(np.float32)
+    X = np.concatenate([base, base[:20], base[:20]], axis=0)
+    X0 = gcr.gcr_normalize(_dev(X))
+    p = gcr.default_params(k=6)
+    G = gcr.gcr_build_graph(X0, p)
+    torch.cuda.synchronize()
+    r = parity.compare_knn(X0.double().cpu().numpy(), np.arange(100), G.nbr.cpu().numpy(), 6)
+    assert r["mismatched"] == 0, r
+
+
+@pytest.mark.parametrize("symmetric", [1, 0])
+@pytest.mark.parametrize("cross", [0, 1])
+def test_operator_and_degrees_match_oracle(gcr, symmetric, cross):
+    w = workloads.crosscam(seed=7, n_query=200, n_gallery=1100, d=128, n_clusters=60)
+    X0 = gcr.gcr_normalize(_dev(w.X))
+    p = gcr.default_params(k=12, symmetric=symmetric, cross_camera=cross, alpha=0.7)
+    G = gcr.gcr_build_graph(X0, p, _dev(w.cam, torch.int32) if cross else None)
+    torch.cuda.synchronize()
+    h = _graph_host(G)
+    X64 = X0.double().cpu().numpy()
+    g_o = oracle.build_graph(X64, 12, p.gamma, w.cam, bool(cross), bool(symmetric), 0.7,
+                             nbr=h["nbr"], nbr_cr=h["nbr_cr"] if cross else None)
+    Dr, Dc = oracle.degrees(g_o["At"])
+    np.testing.assert_allclose(h["deg_r"], Dr, rtol=1e-6)
+    np.testing.assert_allclose(h["deg_c"], Dc, rtol=1e-6)
+    # edge distances are FP32 roundings of FP64-resolved ones
+    np.testing.assert_allclose(h["nbr_d2"], g_o["d2"], rtol=0, atol=2e-6)
+    M = parity.dense_from_csr(h["op_rowptr"], h["op_len"], h["op_col"], h["op_val"], w.n)
+    Mo = g_o["M"].toarray()
+    np.testing.assert_allclose(M, Mo, rtol=0, atol=1e-6 * np.abs(Mo).max())
+    # each operator row is sorted by column with no duplicates
+    for i in range(0, w.n, 97):
+        cols = h["op_col"][h["op_rowptr"][i]:h["op_rowptr"][i] + h["op_len"][i]]
+        assert np.all(np.diff(cols) > 0)
+    if symmetric and not cross:
+        np.testing.assert_allclose(M, M.T, atol=1e-7)
+
+
+def test_propagate_matches_oracle(gcr):
+    w = workloads.plain(seed=2)
+    X0 = gcr.gcr_normalize(_dev(w.X))
+    p = gcr.default_params(k=w.k)
+    G = gcr.gcr_build_graph(X0, p)
+    X1 = gcr.gcr_propagate(G, X0)
+    torch.cuda.synchronize()
+    X64 = X0.double().cpu().numpy()
+    g_o = oracle.build_graph(X64, w.k, p.gamma, nbr=G.nbr.cpu().numpy())
+    ref = oracle.propagate(X64, g_o["M"])
+    np.testing.assert_allclose(X1.cpu().numpy(), ref, atol=2e-6, rtol=0)
+
+
+@pytest.mark.parametrize("precision", PRECISIONS)
+@pytest.mark.parametrize("topk", [0, 37])
+def test_rerank_matches_oracle(gcr, precision, topk):
+    w = workloads.plain(seed=4)
+    X0 = gcr.gcr_normalize(_dev(w.X))
+    p = gcr.default_params(topk_out=topk, precision=precision)
+    idx, dist = gcr.gcr_rerank(X0[:w.n_query].contiguous(), X0[w.n_query:].contiguous(), p)
+    torch.cuda.synchronize()
+    X64 = X0.double().cpu().numpy()
+    idx, dist = idx.cpu().numpy(), dist.cpu().numpy()
+    K = topk or (w.n - w.n_query)
+    assert idx.shape == (w.n_query, K)
+    err, viol = parity.ranking_errors(X64[:w.n_query], X64[w.n_query:], idx, dist)
+    tol = 1e-4 if precision == "fp32" else 2e-3
+    assert err < tol and viol < 2 * tol, (err, viol)
+    if topk == 0:
+        assert np.all(np.sort(idx, axis=1) == np.arange(K)[None, :])
+    # ranks agree with the oracle's where the oracle's distances are separated by > 2 tol
+    o_idx, o_d = oracle.rerank(X64[:w.n_query], X64[w.n_query:], topk)
+    sep = np.ones_like(o_d, dtype=bool)
+    sep[:, 1:] &= np.diff(o_d, axis=1) > 2 * tol
+    sep[:, :-1] &= np.diff(o_d, axis=1) > 2 * tol
+    assert np.all(idx[sep] == o_idx[sep])
+
+
+def test_pipeline_end_to_end_plain(gcr):
+    """Whole GCR (normalise, T layers, re-rank) vs the oracle run from the same raw input."""
+    w = workloads.plain(seed=1)
+    p = gcr.default_params(k=w.k, T=w.T)
+    idx, dist, XT, st = gcr.gcr_pipeline(_dev(w.X), w.n_query, p)
+    torch.cuda.synchronize()
+    Xo = oracle.gcr(w.X, w.k, p.gamma, w.T)
+    err_x = float(np.max(np.abs(XT.cpu().numpy() - Xo)))
+    assert err_x < 1e-4, err_x
+    err, viol = parity.ranking_errors(Xo[:w.n_query], Xo[w.n_query:], idx.cpu().numpy(), dist.cpu().numpy())
+    assert err < 1e-4 and viol < 2e-4, (err, viol)
+    assert st["band_failed"] == 0
+
+
+def test_pipeline_determinism(gcr):
+    w = workloads.crosscam(seed=11, n_query=300, n_gallery=1700, d=192, n_clusters=80)
+    p = gcr.default_params(k=w.k, T=2, cross_camera=1, alpha=0.7)
+    pl = gcr.Pipeline(w.n, w.n_query, w.d, p)
+    X, cam = _dev(w.X), _dev(w.cam, torch.int32)
+    a = [t.clone() for t in pl(X, cam)] + [pl.X_final.clone()]
+    b = [t.clone() for t in pl(X, cam)] + [pl.X_final.clone()]
+    for u, v in zip(a, b):
+        assert torch.equal(u, v)
+
+
+def test_full_size_crosscam_sampled(gcr):
+    """Market-1501-shaped workload (3,368 + 15,913, d = 2048, 6 cameras) at full size, in the
+    launch configuration the benchmark times; kNN sets, operator and propagation are checked on
+    a seeded sample of rows, the re-ranking on a sample of queries."""
+    w = workloads.crosscam()
+    p = gcr.default_params(k=w.k, T=w.T, cross_camera=1, alpha=w.alpha)
+    X0 = gcr.gcr_normalize(_dev(w.X))
+    cam = _dev(w.cam, torch.int32)
+    G = gcr.gcr_build_graph(X0, p, cam)
+    X1 = gcr.gcr_propagate(G, X0)
+    torch.cuda.synchronize()
+    rng = np.random.default_rng(0)
+    rows = np.sort(rng.choice(w.n, 160, replace=False))
+    X64 = X0.double().cpu().numpy()
+    nbr, nbrc = G.nbr.cpu().numpy(), G.nbr_cr.cpu().numpy()
+    r = parity.compare_knn(X64, rows, nbr[rows], w.k)
+    rc = parity.compare_knn(X64, rows, nbrc[rows], w.k, w.cam, cross=True)
+    assert r["mismatched"] == 0 and rc["mismatched"] == 0, (r, rc)
+    # propagation of sampled rows from the full GPU graph, operator rebuilt by the oracle
+    g_o = oracle.build_graph(X64, w.k, p.gamma, w.cam, True, True, w.alpha, nbr=nbr, nbr_cr=nbrc)
+    ref = oracle.propagate(X64, g_o["M"][rows])
+    np.testing.assert_allclose(X1.cpu().numpy()[rows], ref, atol=2e-6, rtol=0)
+    # whole pipeline: ranking of sampled queries against the oracle's distances on X_T
+    idx, dist, XT, st = gcr.gcr_pipeline(_dev(w.X), w.n_query, p, cam)
+    torch.cuda.synchronize()
+    XT64 = XT.double().cpu().numpy()
+    q = np.sort(rng.choice(w.n_query, 48, replace=False))
+    err, viol = parity.ranking_errors(XT64[q], XT64[w.n_query:], idx.cpu().numpy()[q], dist.cpu().numpy()[q])
+    assert err < 1e-4 and viol < 2e-4, (err, viol)
+    assert st["band_failed"] == 0
