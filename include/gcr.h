@@ -162,6 +162,23 @@ int gcr_rerank(const float* Xq, int64_t nq, const float* Xg, int64_t ng, int32_t
                const gcr_params* p, int32_t* idx_out, float* dist_out, void* ws,
                size_t ws_bytes, gcr_stream_t stream);
 
+/* gcr_rerank without a workspace argument, for callers that cannot allocate device
+ * memory: for instance a serving process whose device-memory budget is fixed at start-up
+ * and must not allocate per request (allocation can block, synchronise the device or fail
+ * once memory is fragmented), or an application that embeds this library without giving
+ * it an allocator. The paper has no counterpart; this is an interface convenience.
+ * Same arguments, results and errors as gcr_rerank, except that the scratch lives in a
+ * fixed device array of GCR_RERANK_NOALLOC_SCRATCH_BYTES compiled into the library: it is
+ * present on every GPU that loads the library until the process exits, and the call
+ * returns GCR_E_WORKSPACE, launching nothing, when gcr_rerank_workspace_size() of the
+ * problem exceeds it (for FP32, roughly nq * ng <= 4 million). The array's device address
+ * is looked up on the first call made with a given device current, so make that first call
+ * before any stream capture. Every call shares the one array: calls whose work overlaps on
+ * the GPU race and must be serialised by the caller. Allocates no memory. */
+#define GCR_RERANK_NOALLOC_SCRATCH_BYTES ((size_t)16 << 20)
+int gcr_rerank_noalloc(const float* Xq, int64_t nq, const float* Xg, int64_t ng, int32_t d,
+                       const gcr_params* p, int32_t* idx_out, float* dist_out, gcr_stream_t stream);
+
 /* ------------------------------------------------------------------ S0-S7 in one call
  * The whole offline re-ranking of Sec. III (Eq. 3 with T = p->T iterations):
  * X_0 = normalise(X), X_t = normalise(M_t X_{t-1}) with the graph rebuilt from X_{t-1}

@@ -48,6 +48,8 @@ PROTOTYPES = {
                            c_void_p, c_void_p, c_size_t, c_void_p]),
     "gcr_profile_enable": (c_int, [c_int]),
     "gcr_profile_read": (c_int, [POINTER(ctypes.c_double), POINTER(c_int64), POINTER(c_int64), c_int]),
+    "gcr_rerank_noalloc": (c_int, [c_void_p, c_int64, c_void_p, c_int64, c_int32, POINTER(Params), c_void_p,
+                                   c_void_p, c_void_p]),
     "gcr_pipeline_workspace_size": (c_size_t, [c_int64, c_int64, c_int32, POINTER(Params)]),
     "gcr_pipeline": (c_int, [c_void_p, c_int64, c_int64, c_int32, c_void_p, POINTER(Params), c_void_p,
                              c_void_p, c_void_p, c_void_p, c_void_p, c_size_t, c_void_p]),

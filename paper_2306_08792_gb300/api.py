@@ -158,6 +158,20 @@ def gcr_rerank(Xq: torch.Tensor, Xg: torch.Tensor, p: Params, stream=None):
     return idx, dist
 
 
+def gcr_rerank_noalloc(Xq: torch.Tensor, Xg: torch.Tensor, p: Params, idx: torch.Tensor, dist: torch.Tensor,
+                       stream=None):
+    """gcr_rerank with the library's fixed scratch array instead of a workspace.
+
+    For callers that must not allocate device memory during the call: the outputs are
+    passed in, and the library uses its own resident scratch (see include/gcr.h)."""
+    Xq = _dev_f32(Xq, "Xq")
+    Xg = _dev_f32(Xg, "Xg")
+    _check(_lib.load().gcr_rerank_noalloc(_ptr(Xq), Xq.shape[0], _ptr(Xg), Xg.shape[0], Xq.shape[1],
+                                          ctypes.byref(p), _ptr(idx), _ptr(dist), _stream(stream)),
+           "gcr_rerank_noalloc")
+    return idx, dist
+
+
 class Pipeline:
     """Whole re-ranking (normalise, T x (graph, propagate), re-rank) with reusable buffers."""
 
