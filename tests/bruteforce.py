@@ -82,3 +82,41 @@ def rerank(Q, G):
         keyed = sorted(range(len(G)), key=lambda g: (sqd(q, G[g]), g))
         out.append(keyed)
     return out
+
+
+def serve(Q, G0, k, gamma, T, K, symmetric=True):
+    """Serving form: gallery layers by offline GCR on the gallery alone, then each query's
+    row of the operator against the frozen layer (no query-query edges), then top-K."""
+    G = [normalize(list(map(float, r))) for r in G0]
+    ng = len(G)
+    layers, degs = [G], []
+    for _ in range(T):
+        lists = knn_lists(G, k)
+        At = affinity(G, lists, gamma)
+        Dr = [sum(At[i]) for i in range(ng)]
+        Dc = [sum(At[i][j] for i in range(ng)) for j in range(ng)]
+        degs.append([(Dr[j] + Dc[j]) / 2.0 for j in range(ng)] if symmetric else Dc)
+        M = operator(At, symmetric)
+        d = len(G[0])
+        G = [normalize([sum(M[i][j] * G[j][c] for j in range(ng)) for c in range(d)]) for i in range(ng)]
+        layers.append(G)
+    out = []
+    for q in Q:
+        x = normalize(list(map(float, q)))
+        for t in range(T):
+            L = layers[t]
+            order = sorted(range(ng), key=lambda j: (sqd(x, L[j]), j))[:k]
+            w = [math.exp(-sqd(x, L[j]) / gamma) for j in order]
+            d = len(x)
+            if symmetric:
+                Dq = (1.0 + sum(w) + 1.0) / 2.0
+                y = [x[c] / Dq + sum(w[s] / 2.0 * L[j][c] / math.sqrt(Dq * degs[t][j]) for s, j in enumerate(order))
+                     for c in range(d)]
+            else:
+                r = 1.0 + sum(w)
+                y = [x[c] / math.sqrt(r) + sum(w[s] * L[j][c] / math.sqrt(r * degs[t][j]) for s, j in enumerate(order))
+                     for c in range(d)]
+            x = normalize(y)
+        ranked = sorted(range(ng), key=lambda g: (sqd(x, layers[T][g]), g))[:K]
+        out.append(ranked)
+    return out
