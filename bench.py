@@ -45,6 +45,9 @@ def _args():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--precision", choices=["auto", "bf16", "fp32"], default="auto")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-serving", action="store_true")
+    ap.add_argument("--serving-requests", type=int, default=800)
+    ap.add_argument("--pool", type=int, default=0, help="candidate pool per row (0: library default)")
     return ap.parse_args()
 
 
@@ -200,9 +203,10 @@ def _traffic(kernel_key, files):
     return None
 
 
-def time_path(gcr, torch, w, X, cam, precision, steps, warmup, dist):
+def time_path(gcr, torch, w, X, cam, precision, steps, warmup, dist, pool=0):
     from paper_2306_08792_gb300 import _lib
-    p = gcr.default_params(k=w.k, T=w.T, cross_camera=1, alpha=w.alpha, gamma=w.gamma, precision=precision)
+    p = gcr.default_params(k=w.k, T=w.T, cross_camera=1, alpha=w.alpha, gamma=w.gamma, precision=precision,
+                           pool=pool)
     pl = gcr.Pipeline(w.n, w.n_query, w.d, p)
     stream = torch.cuda.current_stream()
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device="cuda")
@@ -289,6 +293,45 @@ def sampled_error(torch, pl, w, nsample=8):
     return err
 
 
+def serving_bench(gcr, torch, precision, n_requests):
+    """Serving workload: 500,000 x 256 resident gallery (25,000 clusters), k = 20, T = 2, top-100;
+    Poisson arrivals at 200 requests/s with log-uniform batch sizes in 1..512. Returns latency
+    percentiles and throughput of the continuous-batching loop (real time, then saturation)."""
+    import workloads
+    from paper_2306_08792_gb300.serving import Gallery, Server, make_requests
+    w = workloads.serving(n_requests=n_requests)
+    p = gcr.default_params(k=w.k, T=w.T, topk_out=100, precision=precision)
+    t0 = time.perf_counter()
+    G = Gallery(torch.from_numpy(w.gallery).cuda(), p)
+    build_s = time.perf_counter() - t0
+    srv = Server(G, n_slots=4, max_batch=512)
+    srv.warmup()
+    rt = srv.run(make_requests(w, n_requests))
+    sat = srv.run(make_requests(w, n_requests, realtime=False), realtime=False)
+    del srv, G
+    torch.cuda.empty_cache()
+    return {"precision": precision, "gallery_build_s": build_s,
+            "offered_requests_per_s": 200.0, "requests": n_requests,
+            "p50_ms": rt["p50_ms"], "p99_ms": rt["p99_ms"], "queries_per_s": rt["queries_per_s"],
+            "saturation_queries_per_s": sat["queries_per_s"], "saturation_p99_ms": sat["p99_ms"],
+            "launches": rt["launches"]}
+
+
+def max_over_ranks(value: float, dist, device=None) -> float:
+    """Largest value over all ranks (the slowest replica sets the job's time)."""
+    if dist is None:
+        return value
+    import torch
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput(world: int, queries_per_replica: int, ms_max: float) -> float:
+    """Whole-job queries/s of `world` independent replicas timed by the slowest one."""
+    return world * queries_per_replica / (ms_max / 1e3)
+
+
 def run_ours(a):
     import numpy as np
     import torch
@@ -324,7 +367,8 @@ def run_ours(a):
     sampler.mark_start()
     for prec in prec_order:
         try:
-            results[prec] = time_path(gcr, torch, w, X, cam, prec, a.steps, a.warmup, dist)
+            results[prec] = time_path(gcr, torch, w, X, cam, prec, a.steps, a.warmup, dist,
+                                      a.pool if prec == "bf16" else 0)
         except gcr.GcrError as e:
             if a.precision != "auto":
                 raise
@@ -333,20 +377,11 @@ def run_ours(a):
     clocks = sampler.result()
     primary = next(p for p in prec_order if "ms" in results[p])
     R = results[primary]
-    ms_local = R["ms"]
-    if dist:
-        t = torch.tensor([ms_local], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
-    else:
-        ms = ms_local
-    value = world * w.n_query / (ms / 1e3)
+    ms = max_over_ranks(R["ms"], dist, "cuda")
+    value = job_throughput(world, w.n_query, ms)
 
     e2e_ms, h2d, d2h = time_e2e(gcr, torch, w, Xh, camh, R["pipeline"], max(3, a.steps // 2), 2)
-    if dist:
-        t = torch.tensor([e2e_ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_ms = float(t.item())
+    e2e_ms = max_over_ranks(e2e_ms, dist, "cuda")
     # one more untimed run that keeps the features, for the sampled error check
     R["pipeline"](X, cam, keep_features=True)
     torch.cuda.synchronize()
@@ -381,7 +416,7 @@ def run_ours(a):
                        "l2": "flushed between steps (256 MB write outside the timed events); X is 158 MB > L2",
                        "parallelism": "replicas" if world > 1 else "single GPU"},
             "roofline": roof,
-            "e2e": {"value": world * w.n_query / (e2e_ms / 1e3), "unit": UNIT, "h2d_bytes_per_step": h2d,
+            "e2e": {"value": job_throughput(world, w.n_query, e2e_ms), "unit": UNIT, "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": d2h, "ms_per_step": e2e_ms},
             "gpu_launches": int(R["launches"]), "clocks": clocks,
             "stages_ms": {k: round(v["ms"], 4) for k, v in R["stages"].items()},
@@ -396,6 +431,16 @@ def run_ours(a):
                 line["speedup_vs_" + prec] = o["ms"] / R["ms"]
             else:
                 line[f"{prec}_path"] = o
+    if rank == 0 and world == 1 and not a.no_serving:
+        serving = {}
+        for prec in prec_order:
+            try:
+                serving[prec] = serving_bench(gcr, torch, prec, a.serving_requests)
+            except gcr.GcrError as e:
+                serving[prec] = {"error": str(e)}
+        line["serving"] = {"workload": "500,000 x 256 resident gallery, 25,000 clusters, k=20, T=2, top-100; "
+                                       "Poisson 200 req/s, batch log-uniform 1..512, 4 slots, CUDA graphs",
+                           **serving}
     if rank == 0 and world == 1 and not a.no_cpu_baseline:
         t0 = time.perf_counter()
         est, det = oracle_sample_step(w)

@@ -63,8 +63,10 @@ typedef struct {
                            0: D_r^{-1/2} A~ D_c^{-1/2} (Eq. 6)                            */
   int32_t cross_camera; /* 1: add the cross-camera graph (Eq. 8) and mix by Eq. 9         */
   int32_t precision;    /* gcr_precision                                                  */
-  int32_t pool;         /* per-row candidate pool of the streaming kNN search: 32 or 64;
-                           0 picks 32 for FP32 and 64 for BF16; must exceed k             */
+  int32_t pool;         /* per-row candidate pool of the streaming kNN search: 32, 64 or
+                           128; 0 picks 32 for FP32 and 64 for BF16 (BF16 needs >= 64);
+                           must exceed k. A larger pool certifies more rows without the
+                           threshold rescan at the cost of a busier GEMM epilogue.        */
   int32_t topk_out;     /* gcr_rerank: results per query; 0 = the whole gallery           */
   int32_t T;            /* iterations of Eq. 3, used by gcr_pipeline                      */
 } gcr_params;
@@ -116,8 +118,16 @@ int gcr_version(void);
 void gcr_default_params(gcr_params* p);
 /* 1 if `device` is an sm_103 GPU this library was built for, else 0. */
 int gcr_device_supported(int device);
-/* cudaStreamSynchronize(stream) and report any pending CUDA error. */
+/* cudaStreamSynchronize(stream) and report any pending CUDA error; GCR_E_TIMEOUT if a
+ * bounded device-side wait of a tensor-core kernel ran out since the last gcr_sync (that
+ * kernel aborted and its outputs are incomplete). */
 int gcr_sync(gcr_stream_t stream);
+
+/* Failure-path self-test (no counterpart in the paper): launches one warp that waits, with
+ * the same bounded wait the tensor-core kernels use, on a barrier that nothing signals. The
+ * wait gives up after limit_us microseconds (1..1e6) and the kernel returns, so the next
+ * gcr_sync on that stream reports GCR_E_TIMEOUT and the context stays usable. */
+int gcr_selftest_wait_timeout(int64_t limit_us, gcr_stream_t stream);
 
 /* ------------------------------------------------------------------ S0: normalise
  * X_out[i] = X_in[i] / ||X_in[i]||_2 (zero rows stay zero). The method works on unit
@@ -155,7 +165,9 @@ int gcr_propagate(const gcr_graph* g, const float* X_in, float* X_out, int64_t n
  * updated features): for each query q, the gallery sorted by ascending
  * ||x_q - x_g||^2, ties by gallery index. Writes idx_out[q*K + r] (gallery index of
  * rank r) and dist_out[q*K + r], K = topk_out (or ng when topk_out = 0).
- * precision = BF16 computes the distances on tensor cores (error ~1e-3 worst case).
+ * precision = BF16 computes the distances on tensor cores from compensated operands
+ * (x = bf16 hi + bf16 lo; one product of [hi|hi|lo] and [hi|lo|hi] over 3d terms), which
+ * refines them to about 1e-5 of the FP64 distance on unit rows.
  * Errors: GCR_E_INVALID, GCR_E_UNSUPPORTED (K = ng above 16384), GCR_E_WORKSPACE. */
 size_t gcr_rerank_workspace_size(int64_t nq, int64_t ng, int32_t d, const gcr_params* p);
 int gcr_rerank(const float* Xq, int64_t nq, const float* Xg, int64_t ng, int32_t d,
@@ -190,6 +202,54 @@ int gcr_pipeline(const float* X, int64_t n, int64_t nq, int32_t d, const int32_t
                  const gcr_params* p, float* X_final, int32_t* idx_out, float* dist_out,
                  int64_t* stats, void* ws, size_t ws_bytes, gcr_stream_t stream);
 
+/* ------------------------------------------------------------------ S8: GCRV profiles
+ * Profile vectors of Sec. III-D for video re-ranking (Algorithm 2 step 1):
+ *   mu_c = mean of tracklet c's L2-normalised frames                              (Eq. 10)
+ *   w_c  = (X_s^T X_s + lambda n_s I)^{-1} (mu_c - mu_s)                           (Eq. 17)
+ * X_s stacks the n_s normalised frames of every tracklet of c's camera s, mu_s is their
+ * mean (the paper prints X X^T; only the d x d matrix X^T X is dimensionally consistent and
+ * matches its "covariance matrix X^T X"). A camera with a single tracklet has mu_c = mu_s,
+ * so that tracklet keeps mu_c. W_out (C x d) is not normalised; Algorithm 2 then runs GCR
+ * with the global and the cross-camera graph on it (gcr_pipeline with cross_camera = 1 and
+ * cam = trk_cam).
+ * frames: device float32 [F][d], raw. trk_off: device int64 [C+1], tracklet c owns frames
+ * [trk_off[c], trk_off[c+1]) (non-empty, ascending). trk_cam: device int32 [C] in
+ * [0, n_cams), n_cams <= 64. The system is solved by conjugate gradients in FP32 with the
+ * iteration count fixed by the bound cond <= 1 + 1/lambda (relative error ~1e-7).
+ * Errors: GCR_E_INVALID (sizes, lambda <= 0), GCR_E_UNSUPPORTED (d % 4), GCR_E_WORKSPACE.
+ * Tracklet offsets and cameras are trusted (not re-validated on the device). */
+size_t gcrv_profiles_workspace_size(int64_t F, int32_t d, int32_t C, int32_t n_cams);
+int gcrv_profiles(const float* frames, int64_t F, int32_t d, const int64_t* trk_off,
+                  const int32_t* trk_cam, int32_t C, int32_t n_cams, float lambda, float* W_out,
+                  void* ws, size_t ws_bytes, gcr_stream_t stream);
+
+/* ------------------------------------------------------------------ S9: serving
+ * Re-ranking against a resident gallery. Sec. IV-F2 notes that with the gallery's graphs
+ * computed and stored in advance the cost per query falls to O(N log N); this is that form:
+ *  - gcr_gallery_build runs offline GCR (Eq. 3) on the gallery alone and stores, in the
+ *    caller's state buffer (gcr_gallery_bytes), the layers G_0..G_T, the degrees of each
+ *    layer's graph (D = (D_r + D_c)/2 of Eq. 7, or D_c of Eq. 6) and per-row statistics.
+ *  - gcr_serve takes a batch of b raw queries (device float32 [b][d]) and, for t = 1..T,
+ *    finds each query's certified k nearest rows of G_{t-1}, forms the query's row of the
+ *    operator with the gallery frozen and no query-query edges
+ *        symmetric:  y = x/D_q + sum_j (w_qj/2) g_j / sqrt(D_q D_j),  D_q = (2 + sum w)/2
+ *        otherwise:  y = x/sqrt(r_q) + sum_j w_qj g_j / sqrt(r_q Dc_j), r_q = 1 + sum w
+ *    (w_qj of Eq. 4) and normalises it; then it returns the certified top K = topk_out
+ *    (1..127) of the gallery on G_T: idx_out int32 [b][K] by ascending squared distance
+ *    (ties to the smaller index) and dist_out float [b][K] (FP32 re-scored distances).
+ * Every step is per query, so a query's result does not depend on its batch-mates. The
+ * state is read-only during gcr_serve: concurrent calls with distinct workspaces may share
+ * it. No host synchronisation: a call can be captured in a CUDA graph.
+ * cross_camera must be 0 (GCR_E_UNSUPPORTED otherwise). stats: as gcr_graph.stats. */
+size_t gcr_gallery_bytes(int64_t ng, int32_t d, const gcr_params* p);
+size_t gcr_gallery_build_workspace_size(int64_t ng, int32_t d, const gcr_params* p);
+int gcr_gallery_build(const float* Xg, int64_t ng, int32_t d, const gcr_params* p, void* state,
+                      size_t state_bytes, void* ws, size_t ws_bytes, gcr_stream_t stream);
+size_t gcr_serve_workspace_size(int64_t b, int64_t ng, int32_t d, const gcr_params* p);
+int gcr_serve(const void* state, size_t state_bytes, int64_t ng, const float* Xq, int64_t b,
+              int32_t d, const gcr_params* p, int32_t* idx_out, float* dist_out, int64_t* stats,
+              void* ws, size_t ws_bytes, gcr_stream_t stream);
+
 /* ------------------------------------------------------------------ stage profiler
  * Process-wide, for measurement only (not thread-safe). While enabled, every entry point
  * records a CUDA event pair on its stream around each stage below. gcr_profile_read()
@@ -206,6 +266,7 @@ enum {
   GCR_STAGE_PROPAGATE = 6, /* S5 propagation + L2 normalisation             */
   GCR_STAGE_DIST_GEMM = 7, /* S7 re-ranked distance GEMM                    */
   GCR_STAGE_SORT = 8,      /* S7 segmented sort                             */
+  GCR_STAGE_GCRV = 9,      /* S8 GCRV profile vectors                       */
   GCR_STAGES = 12
 };
 int gcr_profile_enable(int on);

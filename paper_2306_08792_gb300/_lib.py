@@ -11,7 +11,8 @@ LIB_PATH = os.path.join(PKG, "libgcr.so")
 
 GCR_OK, GCR_E_INVALID, GCR_E_WORKSPACE, GCR_E_CUDA, GCR_E_TIMEOUT, GCR_E_UNSUPPORTED = range(6)
 GCR_PREC_FP32, GCR_PREC_BF16 = 0, 1
-STAGE_NAMES = ["normalize", "prep", "sim_gemm", "refine", "band", "graph", "propagate", "dist_gemm", "sort"]
+STAGE_NAMES = ["normalize", "prep", "sim_gemm", "refine", "band", "graph", "propagate", "dist_gemm", "sort",
+               "gcrv"]
 GCR_STAGES = 12
 STAT_NAMES = ["rows", "uncertified", "band_failed", "fp64_rows", "fp64_dots", "clamped", "rescored", "reserved"]
 GCR_STATS_LEN = 8
@@ -37,6 +38,7 @@ PROTOTYPES = {
     "gcr_default_params": (None, [POINTER(Params)]),
     "gcr_device_supported": (c_int, [c_int]),
     "gcr_sync": (c_int, [c_void_p]),
+    "gcr_selftest_wait_timeout": (c_int, [c_int64, c_void_p]),
     "gcr_normalize": (c_int, [c_void_p, c_void_p, c_int64, c_int32, c_void_p]),
     "gcr_graph_op_capacity": (c_size_t, [c_int64, POINTER(Params)]),
     "gcr_build_graph_workspace_size": (c_size_t, [c_int64, c_int32, POINTER(Params)]),
@@ -50,6 +52,16 @@ PROTOTYPES = {
     "gcr_profile_read": (c_int, [POINTER(ctypes.c_double), POINTER(c_int64), POINTER(c_int64), c_int]),
     "gcr_rerank_noalloc": (c_int, [c_void_p, c_int64, c_void_p, c_int64, c_int32, POINTER(Params), c_void_p,
                                    c_void_p, c_void_p]),
+    "gcrv_profiles_workspace_size": (c_size_t, [c_int64, c_int32, c_int32, c_int32]),
+    "gcrv_profiles": (c_int, [c_void_p, c_int64, c_int32, c_void_p, c_void_p, c_int32, c_int32, c_float, c_void_p,
+                              c_void_p, c_size_t, c_void_p]),
+    "gcr_gallery_bytes": (c_size_t, [c_int64, c_int32, POINTER(Params)]),
+    "gcr_gallery_build_workspace_size": (c_size_t, [c_int64, c_int32, POINTER(Params)]),
+    "gcr_gallery_build": (c_int, [c_void_p, c_int64, c_int32, POINTER(Params), c_void_p, c_size_t, c_void_p,
+                                  c_size_t, c_void_p]),
+    "gcr_serve_workspace_size": (c_size_t, [c_int64, c_int64, c_int32, POINTER(Params)]),
+    "gcr_serve": (c_int, [c_void_p, c_size_t, c_int64, c_void_p, c_int64, c_int32, POINTER(Params), c_void_p,
+                          c_void_p, c_void_p, c_void_p, c_size_t, c_void_p]),
     "gcr_pipeline_workspace_size": (c_size_t, [c_int64, c_int64, c_int32, POINTER(Params)]),
     "gcr_pipeline": (c_int, [c_void_p, c_int64, c_int64, c_int32, c_void_p, POINTER(Params), c_void_p,
                              c_void_p, c_void_p, c_void_p, c_void_p, c_size_t, c_void_p]),

@@ -172,6 +172,27 @@ def gcr_rerank_noalloc(Xq: torch.Tensor, Xg: torch.Tensor, p: Params, idx: torch
     return idx, dist
 
 
+def gcrv_profiles(frames: torch.Tensor, trk_off: torch.Tensor, trk_cam: torch.Tensor, n_cams: int,
+                  lam: float, stream=None) -> torch.Tensor:
+    """Eq. 17 profile vectors (C x d, not normalised) of ragged tracklets of raw frames."""
+    frames = _dev_f32(frames, "frames")
+    if not (trk_off.is_cuda and trk_off.dtype == torch.int64 and trk_off.is_contiguous()):
+        raise ValueError("trk_off must be a contiguous int64 CUDA vector")
+    if not (trk_cam.is_cuda and trk_cam.dtype == torch.int32 and trk_cam.is_contiguous()):
+        raise ValueError("trk_cam must be a contiguous int32 CUDA vector")
+    F, d = frames.shape
+    C = trk_cam.numel()
+    if trk_off.numel() != C + 1:
+        raise ValueError("trk_off must have C + 1 entries")
+    lib = _lib.load()
+    need = lib.gcrv_profiles_workspace_size(F, d, C, n_cams)
+    ws = torch.empty(max(need, 1), dtype=torch.uint8, device=frames.device)
+    W = torch.empty(C, d, dtype=torch.float32, device=frames.device)
+    _check(lib.gcrv_profiles(_ptr(frames), F, d, _ptr(trk_off), _ptr(trk_cam), C, n_cams, ctypes.c_float(lam),
+                             _ptr(W), _ptr(ws), need, _stream(stream)), "gcrv_profiles")
+    return W
+
+
 class Pipeline:
     """Whole re-ranking (normalise, T x (graph, propagate), re-rank) with reusable buffers."""
 

@@ -61,8 +61,9 @@ int check_params(const gcr_params* p, int64_t n, int32_t d, Resolved* r) {
   if (p->cross_camera != 0 && p->cross_camera != 1) return GCR_E_INVALID;
   if (p->cross_camera && !(p->alpha >= 0.f && p->alpha <= 1.f)) return GCR_E_INVALID;
   int kp = p->pool ? p->pool : (p->precision == GCR_PREC_BF16 ? 64 : 32);
-  if (kp != 32 && kp != 64) return GCR_E_INVALID;
+  if (kp != 32 && kp != 64 && kp != 128) return GCR_E_INVALID;
   if (p->k < 0 || p->k >= kp) return GCR_E_INVALID;
+  if (p->precision == GCR_PREC_BF16 && kp == 32) return GCR_E_UNSUPPORTED;
   r->kp = kp;
   r->kinds = p->cross_camera ? 2 : 1;
   return GCR_OK;
@@ -163,16 +164,17 @@ int build_graph_impl(const float* X, int64_t n64_, int32_t d, const int32_t* cam
   if (p->k > 0) {
     StageScope sc_(GCR_STAGE_SIM_GEMM, st);
     if (bf) {
-      GCR_CUDA_TRY(launch_umma_pool(w.xb, n, d, camp, p->cross_camera != 0, w.pool_v, w.pool_i, w.err, st));
+      GCR_CUDA_TRY(launch_umma_pool(w.xb, n, w.xb, n, d, camp, p->cross_camera != 0, 1, r.kp, 1, w.pool_v, w.pool_i,
+                                    st));
     } else {
-      GCR_CUDA_TRY(launch_sgemm_pool(X, n, d, camp, r.kp, p->cross_camera != 0, w.pool_v, w.pool_i, st));
+      GCR_CUDA_TRY(launch_sgemm_pool(X, n, X, n, d, camp, r.kp, p->cross_camera != 0, 1, 1, w.pool_v, w.pool_i, st));
     }
   }
 
   RefineArgs ra;
   std::memset(&ra, 0, sizeof(ra));
-  ra.X = X; ra.n = n; ra.d = d; ra.k = p->k; ra.kinds = kinds; ra.precision = p->precision;
-  ra.n64 = w.n64; ra.enrm = w.enrm; ra.anrm = w.anrm; ra.sc = w.sc;
+  ra.X = X; ra.XB = X; ra.n = n; ra.d = d; ra.k = p->k; ra.kinds = kinds; ra.precision = p->precision;
+  ra.n64 = w.n64; ra.n64B = w.n64; ra.enrm = w.enrm; ra.anrm = w.anrm; ra.sc = w.sc;
   ra.pool_v = w.pool_v; ra.pool_i = w.pool_i; ra.kp = r.kp;
   ra.nbr[0] = g->nbr; ra.d2[0] = g->nbr_d2;
   ra.nbr[1] = kinds == 2 ? g->nbr_cr : g->nbr;
@@ -190,10 +192,10 @@ int build_graph_impl(const float* X, int64_t n64_, int32_t d, const int32_t* cam
     StageScope sc_(GCR_STAGE_BAND, st, bf ? 3 : 2);
     if (bf) {
       GCR_CUDA_TRY(launch_gather_bf16(w.xb, d, w.unc_count, w.unc_row, w.band_rows, w.band_a, st));
-      GCR_CUDA_TRY(launch_umma_band(w.xb, n, d, camp, w.band_a, w.unc_count, w.band_rows, w.unc_row,
-                                    w.unc_kind, w.unc_thr, kBandCap, w.band_cnt, w.band_v, w.band_i, w.err, st));
+      GCR_CUDA_TRY(launch_umma_band(w.xb, n, d, camp, 1, w.band_a, w.unc_count, w.band_rows, w.unc_row,
+                                    w.unc_kind, w.unc_thr, kBandCap, w.band_cnt, w.band_v, w.band_i, st));
     } else {
-      GCR_CUDA_TRY(launch_sgemm_band(X, n, d, camp, w.unc_count, w.band_rows, w.unc_row, w.unc_kind,
+      GCR_CUDA_TRY(launch_sgemm_band(X, X, n, d, camp, 1, w.unc_count, w.band_rows, w.unc_row, w.unc_kind,
                                      w.unc_thr, kBandCap, w.band_cnt, w.band_v, w.band_i, st));
     }
     GCR_CUDA_TRY(launch_refine_band(ra, st));
@@ -245,6 +247,12 @@ struct RerankWs {
   int* err;
 };
 
+// Top-K re-ranking through the certified pool search: used when 1 <= topk_out <= 127 and
+// topk_out < ng (any gallery size); the full ranking uses the distance GEMM + sort.
+bool rerank_uses_pool(const gcr_params* p, int64_t ng) {
+  return p->topk_out >= 1 && p->topk_out <= 127 && p->topk_out < ng;
+}
+
 size_t carve_rerank(Carve& c, int64_t nq, int64_t ng, int32_t d, bool bf, RerankWs* w) {
   RerankWs t;
   t.D = c.take<float>((size_t)nq * ng);
@@ -253,8 +261,8 @@ size_t carve_rerank(Carve& c, int64_t nq, int64_t ng, int32_t d, bool bf, Rerank
   t.nq = c.take<float>(nq);
   t.ng = c.take<float>(ng);
   t.sc = c.take<RowScalars>(2);
-  t.qb = bf ? c.take<__nv_bfloat16>((size_t)nq * d) : nullptr;
-  t.gb = bf ? c.take<__nv_bfloat16>((size_t)ng * d) : nullptr;
+  t.qb = bf ? c.take<__nv_bfloat16>((size_t)nq * 3 * d) : nullptr;
+  t.gb = bf ? c.take<__nv_bfloat16>((size_t)ng * 3 * d) : nullptr;
   t.dummy = c.take<float>(2 * (size_t)std::max(nq, ng));
   t.err = c.take<int>(4);
   if (w) *w = t;
@@ -267,15 +275,19 @@ int rerank_impl(const float* Xq, int64_t nq, const float* Xg, int64_t ng, int32_
   const int K = p->topk_out > 0 ? (int)std::min<int64_t>(p->topk_out, ng) : (int)ng;
   const size_t mx = (size_t)std::max(nq, ng);
   {
-    StageScope sc_(GCR_STAGE_PREP, st, 4);
-    GCR_CUDA_TRY(launch_row_stats(Xq, (int)nq, d, w.n64q, w.nq, bf ? w.qb : nullptr, w.dummy, w.dummy + mx, w.sc, st));
-    GCR_CUDA_TRY(launch_row_stats(Xg, (int)ng, d, w.n64g, w.ng, bf ? w.gb : nullptr, w.dummy, w.dummy + mx, w.sc + 1, st));
+    StageScope sc_(GCR_STAGE_PREP, st, bf ? 6 : 4);
+    GCR_CUDA_TRY(launch_row_stats(Xq, (int)nq, d, w.n64q, w.nq, nullptr, w.dummy, w.dummy + mx, w.sc, st));
+    GCR_CUDA_TRY(launch_row_stats(Xg, (int)ng, d, w.n64g, w.ng, nullptr, w.dummy, w.dummy + mx, w.sc + 1, st));
+    if (bf) {
+      GCR_CUDA_TRY(launch_split3(Xq, (int)nq, d, 0, w.qb, st));
+      GCR_CUDA_TRY(launch_split3(Xg, (int)ng, d, 1, w.gb, st));
+    }
   }
   if (bf) GCR_CUDA_TRY(cudaMemsetAsync(w.err, 0, sizeof(int) * 4, st));
   {
     StageScope sc_(GCR_STAGE_DIST_GEMM, st);
     if (bf) {
-    GCR_CUDA_TRY(launch_umma_dist(w.qb, (int)nq, w.gb, (int)ng, d, w.nq, w.ng, w.D, w.err, st));
+    GCR_CUDA_TRY(launch_umma_dist(w.qb, (int)nq, w.gb, (int)ng, 3 * d, w.nq, w.ng, w.D, st));
   } else {
     GCR_CUDA_TRY(launch_sgemm_dist(Xq, (int)nq, Xg, (int)ng, d, w.nq, w.ng, w.D, st));
   }
@@ -294,9 +306,14 @@ int check_rerank(int64_t nq, int64_t ng, int32_t d, const gcr_params* p) {
   if (p->precision != GCR_PREC_FP32 && p->precision != GCR_PREC_BF16) return GCR_E_INVALID;
   if (p->precision == GCR_PREC_BF16 && d % 8 != 0) return GCR_E_UNSUPPORTED;
   if (p->topk_out < 0) return GCR_E_INVALID;
-  if (ng > 16384) return GCR_E_UNSUPPORTED;
+  if (ng > 16384 && !(p->topk_out >= 1 && p->topk_out <= 127)) return GCR_E_UNSUPPORTED;
   return GCR_OK;
 }
+
+struct TopkRerankWs;
+size_t carve_topk_rerank(Carve& c, int64_t nq, int64_t ng, int32_t d, const gcr_params* p, TopkRerankWs* w);
+int topk_rerank_impl(const float* Xq, int64_t nq, const float* Xg, int64_t ng, int32_t d, const gcr_params* p,
+                     int32_t* idx_out, float* dist_out, const TopkRerankWs& w, cudaStream_t st);
 
 struct PipeWs {
   float* Xa;
@@ -331,11 +348,262 @@ size_t carve_pipe(Carve& c, int64_t n, int64_t nq, int32_t d, const gcr_params* 
   Carve cb(nullptr, 0);
   const size_t b = carve_build(cb, n, d, p, r, nullptr);
   Carve cr(nullptr, 0);
-  const size_t rr = carve_rerank(cr, nq, n - nq, d, p->precision == GCR_PREC_BF16, nullptr);
+  const size_t rr = rerank_uses_pool(p, n - nq) ? carve_topk_rerank(cr, nq, n - nq, d, p, nullptr)
+                                                : carve_rerank(cr, nq, n - nq, d, p->precision == GCR_PREC_BF16, nullptr);
   t.inner_bytes = std::max(b, rr);
   t.inner = c.take<char>(t.inner_bytes);
   if (w) *w = t;
   return c.off;
+}
+
+
+// ------------------------------------------------------------------------------------ serving
+struct GalleryView {
+  float* layers;   // (T+1) x ng x d
+  float* deg;      // T x ng
+  double* n64;     // (T+1) x ng
+  float* n32;      // (T+1) x ng
+  __nv_bfloat16* xb;  // (T+1) x ng x d (BF16 precision)
+  float* enrm;     // (T+1) x ng
+  float* anrm;     // (T+1) x ng
+  RowScalars* sc;  // T+1
+};
+
+int check_serve_params(const gcr_params* p, int64_t ng, int32_t d, Resolved* r) {
+  int s = check_params(p, ng, d, r);
+  if (s != GCR_OK) return s;
+  if (p->cross_camera) return GCR_E_UNSUPPORTED;  // the resident gallery carries no camera graph
+  if (p->T < 0 || p->T > 16) return GCR_E_INVALID;
+  if (p->topk_out < 1 || p->topk_out > 127 || p->topk_out > ng) return GCR_E_INVALID;
+  if (p->k > ng) return GCR_E_INVALID;
+  return GCR_OK;
+}
+
+size_t carve_gallery(Carve& c, int64_t ng, int32_t d, const gcr_params* p, GalleryView* v) {
+  const size_t L = (size_t)p->T + 1, n = (size_t)ng;
+  const bool bf = p->precision == GCR_PREC_BF16;
+  GalleryView t;
+  t.layers = c.take<float>(L * n * d);
+  t.deg = c.take<float>((size_t)(p->T > 0 ? p->T : 1) * n);
+  t.n64 = c.take<double>(L * n);
+  t.n32 = c.take<float>(L * n);
+  t.xb = bf ? c.take<__nv_bfloat16>(L * n * d) : nullptr;
+  t.enrm = bf ? c.take<float>(L * n) : nullptr;
+  t.anrm = bf ? c.take<float>(L * n) : nullptr;
+  t.sc = c.take<RowScalars>(L);
+  if (v) *v = t;
+  return c.off;
+}
+
+struct GalleryBuildWs {
+  gcr_graph g;
+  char* inner;
+  size_t inner_bytes;
+};
+
+size_t carve_gallery_build(Carve& c, int64_t ng, int32_t d, const gcr_params* p, const Resolved& r,
+                           GalleryBuildWs* w) {
+  const size_t n = (size_t)ng;
+  GalleryBuildWs t;
+  std::memset(&t, 0, sizeof(t));
+  t.g.nbr = c.take<int32_t>(n * p->k);
+  t.g.nbr_d2 = c.take<float>(n * p->k);
+  t.g.deg_r = c.take<float>(n);
+  t.g.deg_c = c.take<float>(n);
+  t.g.op_rowptr = c.take<int32_t>(n + 1);
+  t.g.op_len = c.take<int32_t>(n);
+  const size_t cap = op_capacity(ng, p, 1);
+  t.g.op_col = c.take<int32_t>(cap);
+  t.g.op_val = c.take<float>(cap);
+  Carve cb(nullptr, 0);
+  t.inner_bytes = carve_build(cb, ng, d, p, r, nullptr);
+  t.inner = c.take<char>(t.inner_bytes);
+  if (w) *w = t;
+  return c.off;
+}
+
+struct ServeWs {
+  float* xq[2];
+  double* n64;
+  float* n32;
+  __nv_bfloat16* qb;
+  float* enrm;
+  float* anrm;
+  RowScalars* sc;
+  float* part_v;
+  int* part_i;
+  float* pool_v;
+  int* pool_i;
+  int* unc_count;
+  int* unc_row;
+  int* unc_kind;
+  float* unc_thr;
+  int* band_cnt;
+  float* band_v;
+  int* band_i;
+  __nv_bfloat16* band_a;
+  int32_t* nbr;
+  float* d2;
+  unsigned long long* stats;
+};
+
+constexpr int kServeMaxSplits = 152;
+
+// Column splits the pool launchers actually use for `want` splits of `ntiles` tiles.
+int split_count(int want, int ntiles) {
+  want = std::max(1, std::min(want, ntiles));
+  const int tps = (ntiles + want - 1) / want;
+  return (ntiles + tps - 1) / tps;
+}
+
+int serve_kp_final(const gcr_params* p) {
+  const int K = p->topk_out;
+  if (p->precision == GCR_PREC_FP32 && K < 32) return 32;
+  return K < 64 ? 64 : 128;
+}
+
+size_t carve_serve(Carve& c, int64_t b, int32_t d, const gcr_params* p, const Resolved& r, ServeWs* w) {
+  const size_t nb = (size_t)b;
+  const bool bf = p->precision == GCR_PREC_BF16;
+  const int kpmax = std::max(r.kp, serve_kp_final(p));
+  ServeWs t;
+  t.xq[0] = c.take<float>(nb * d);
+  t.xq[1] = c.take<float>(nb * d);
+  t.n64 = c.take<double>(nb);
+  t.n32 = c.take<float>(nb);
+  t.qb = bf ? c.take<__nv_bfloat16>(nb * d) : nullptr;
+  t.enrm = bf ? c.take<float>(nb) : nullptr;
+  t.anrm = bf ? c.take<float>(nb) : nullptr;
+  t.sc = c.take<RowScalars>(1);
+  t.part_v = c.take<float>((size_t)kServeMaxSplits * nb * kpmax);
+  t.part_i = c.take<int>((size_t)kServeMaxSplits * nb * kpmax);
+  t.pool_v = c.take<float>(nb * kpmax);
+  t.pool_i = c.take<int>(nb * kpmax);
+  t.unc_count = c.take<int>(4);
+  t.unc_row = c.take<int>(nb);
+  t.unc_kind = c.take<int>(nb);
+  t.unc_thr = c.take<float>(nb);
+  t.band_cnt = c.take<int>(nb);
+  t.band_v = c.take<float>(nb * kBandCap);
+  t.band_i = c.take<int>(nb * kBandCap);
+  t.band_a = bf ? c.take<__nv_bfloat16>(nb * d) : nullptr;
+  t.nbr = c.take<int32_t>(nb * std::max(p->k, 1));
+  t.d2 = c.take<float>(nb * std::max(p->k, 1));
+  t.stats = c.take<unsigned long long>(GCR_STATS_LEN);
+  if (w) *w = t;
+  return c.off;
+}
+
+// The gallery side of a certified top-k search: FP32 rows, their BF16 shadow (BF16 path),
+// squared norms and maxima.
+struct GallerySide {
+  const float* G;
+  const __nv_bfloat16* Gb;
+  const double* n64;
+  const RowScalars* sc;
+};
+
+GallerySide gallery_layer(const GalleryView& g, int layer, int ng, int d) {
+  return GallerySide{g.layers + (size_t)layer * ng * d, g.xb ? g.xb + (size_t)layer * ng * d : nullptr,
+                     g.n64 + (size_t)layer * ng, g.sc + layer};
+}
+
+// Certified k nearest gallery rows for the b query rows xq: pool, merge, refine, band.
+int serve_knn(const float* xq, int b, int d, const gcr_params* p, int k, int kp, const GallerySide& gs, int ng,
+              const ServeWs& w, unsigned long long* stats, int32_t* nbr, float* d2, cudaStream_t st) {
+  const bool bf = p->precision == GCR_PREC_BF16;
+  const float* G = gs.G;
+  const int rblocks = (b + 127) / 128;
+  const int splits = std::max(1, std::min(kServeMaxSplits, (152 + rblocks - 1) / rblocks));
+  {
+    StageScope sc_(GCR_STAGE_PREP, st, bf ? 2 : 2);
+    GCR_CUDA_TRY(launch_row_stats(xq, b, d, w.n64, w.n32, bf ? w.qb : nullptr, w.enrm, w.anrm, w.sc, st));
+  }
+  GCR_CUDA_TRY(cudaMemsetAsync(w.unc_count, 0, sizeof(int) * 4, st));
+  GCR_CUDA_TRY(cudaMemsetAsync(w.band_cnt, 0, sizeof(int) * b, st));
+  int used_splits;
+  {
+    StageScope sc_(GCR_STAGE_SIM_GEMM, st, 2);
+    if (bf) {
+      const int ntiles = (ng + 255) / 256;
+      used_splits = split_count(splits, ntiles);
+      GCR_CUDA_TRY(launch_umma_pool(w.qb, b, gs.Gb, ng, d, nullptr, false, 0, kp, used_splits, w.part_v, w.part_i,
+                                    st));
+    } else {
+      const int ntiles = (ng + 127) / 128;
+      used_splits = split_count(splits, ntiles);
+      GCR_CUDA_TRY(launch_sgemm_pool(xq, b, G, ng, d, nullptr, kp, false, 0, used_splits, w.part_v, w.part_i, st));
+    }
+    GCR_CUDA_TRY(launch_merge_splits(w.part_v, w.part_i, used_splits, 1, b, kp, w.pool_v, w.pool_i, st));
+  }
+  RefineArgs ra;
+  std::memset(&ra, 0, sizeof(ra));
+  ra.X = xq; ra.XB = G; ra.n = b; ra.d = d; ra.k = k; ra.kinds = 1; ra.precision = p->precision;
+  ra.n64 = w.n64; ra.n64B = gs.n64;
+  ra.enrm = w.enrm; ra.anrm = w.anrm; ra.sc = gs.sc;
+  ra.pool_v = w.pool_v; ra.pool_i = w.pool_i; ra.kp = kp;
+  ra.nbr[0] = ra.nbr[1] = nbr;
+  ra.d2[0] = ra.d2[1] = d2;
+  ra.unc_count = w.unc_count; ra.unc_row = w.unc_row; ra.unc_kind = w.unc_kind; ra.unc_thr = w.unc_thr;
+  ra.stats = stats;
+  ra.band_cnt = w.band_cnt; ra.band_v = w.band_v; ra.band_i = w.band_i; ra.bcap = kBandCap; ra.band_rows = b;
+  {
+    StageScope sc_(GCR_STAGE_REFINE, st);
+    GCR_CUDA_TRY(launch_refine_pool(ra, st));
+  }
+  {
+    StageScope sc_(GCR_STAGE_BAND, st, bf ? 3 : 2);
+    if (bf) {
+      GCR_CUDA_TRY(launch_gather_bf16(w.qb, d, w.unc_count, w.unc_row, b, w.band_a, st));
+      GCR_CUDA_TRY(launch_umma_band(gs.Gb, ng, d, nullptr, 0, w.band_a, w.unc_count, b, w.unc_row, w.unc_kind,
+                                    w.unc_thr, kBandCap, w.band_cnt, w.band_v, w.band_i, st));
+    } else {
+      GCR_CUDA_TRY(launch_sgemm_band(xq, G, ng, d, nullptr, 0, w.unc_count, b, w.unc_row, w.unc_kind, w.unc_thr,
+                                     kBandCap, w.band_cnt, w.band_v, w.band_i, st));
+    }
+    GCR_CUDA_TRY(launch_refine_band(ra, st));
+  }
+  return GCR_OK;
+}
+
+struct TopkRerankWs {
+  ServeWs sw;
+  double* n64g;
+  float* n32g;
+  __nv_bfloat16* gb;
+  float* genrm;
+  float* ganrm;
+  RowScalars* scg;
+};
+
+size_t carve_topk_rerank(Carve& c, int64_t nq, int64_t ng, int32_t d, const gcr_params* p, TopkRerankWs* w) {
+  const bool bf = p->precision == GCR_PREC_BF16;
+  Resolved r;
+  r.kp = serve_kp_final(p);
+  r.kinds = 1;
+  TopkRerankWs t;
+  carve_serve(c, nq, d, p, r, &t.sw);
+  t.n64g = c.take<double>(ng);
+  t.n32g = c.take<float>(ng);
+  t.gb = bf ? c.take<__nv_bfloat16>((size_t)ng * d) : nullptr;
+  t.genrm = c.take<float>(ng);
+  t.ganrm = c.take<float>(ng);
+  t.scg = c.take<RowScalars>(1);
+  if (w) *w = t;
+  return c.off;
+}
+
+int topk_rerank_impl(const float* Xq, int64_t nq, const float* Xg, int64_t ng, int32_t d, const gcr_params* p,
+                     int32_t* idx_out, float* dist_out, const TopkRerankWs& w, cudaStream_t st) {
+  const bool bf = p->precision == GCR_PREC_BF16;
+  {
+    StageScope sc_(GCR_STAGE_PREP, st, 2);
+    GCR_CUDA_TRY(launch_row_stats(Xg, (int)ng, d, w.n64g, w.n32g, bf ? w.gb : nullptr, w.genrm, w.ganrm, w.scg, st));
+  }
+  GCR_CUDA_TRY(cudaMemsetAsync(w.sw.stats, 0, sizeof(unsigned long long) * GCR_STATS_LEN, st));
+  const GallerySide gs{Xg, w.gb, w.n64g, w.scg};
+  return serve_knn(Xq, (int)nq, d, p, p->topk_out, serve_kp_final(p), gs, (int)ng, w.sw, w.sw.stats, idx_out,
+                   dist_out, st);
 }
 
 }  // namespace
@@ -405,6 +673,15 @@ int gcr_device_supported(int device) {
 int gcr_sync(gcr_stream_t stream) {
   GCR_CUDA_TRY(cudaStreamSynchronize((cudaStream_t)stream));
   GCR_CUDA_TRY(cudaGetLastError());
+  const int t = umma_read_and_clear_timeouts();
+  if (t < 0) return GCR_E_CUDA;
+  if (t > 0) return GCR_E_TIMEOUT;
+  return GCR_OK;
+}
+
+int gcr_selftest_wait_timeout(int64_t limit_us, gcr_stream_t stream) {
+  if (limit_us < 1 || limit_us > 1000000) return GCR_E_INVALID;
+  GCR_CUDA_TRY(launch_wait_probe((unsigned long long)limit_us * 1000ull, (cudaStream_t)stream));
   return GCR_OK;
 }
 
@@ -456,6 +733,7 @@ int gcr_propagate(const gcr_graph* g, const float* X_in, float* X_out, int64_t n
 size_t gcr_rerank_workspace_size(int64_t nq, int64_t ng, int32_t d, const gcr_params* p) {
   if (check_rerank(nq, ng, d, p) != GCR_OK) return 0;
   Carve c(nullptr, 0);
+  if (rerank_uses_pool(p, ng)) return carve_topk_rerank(c, nq, ng, d, p, nullptr) + 256;
   return carve_rerank(c, nq, ng, d, p->precision == GCR_PREC_BF16, nullptr) + 256;
 }
 
@@ -466,9 +744,131 @@ int gcr_rerank(const float* Xq, int64_t nq, const float* Xg, int64_t ng, int32_t
   if (!Xq || !Xg || !idx_out || !dist_out) return GCR_E_INVALID;
   if (!ws) return GCR_E_WORKSPACE;
   Carve c(ws, ws_bytes);
+  if (rerank_uses_pool(p, ng)) {
+    TopkRerankWs tw;
+    if (carve_topk_rerank(c, nq, ng, d, p, &tw) > ws_bytes) return GCR_E_WORKSPACE;
+    return topk_rerank_impl(Xq, nq, Xg, ng, d, p, idx_out, dist_out, tw, (cudaStream_t)stream);
+  }
   RerankWs w;
   if (carve_rerank(c, nq, ng, d, p->precision == GCR_PREC_BF16, &w) > ws_bytes) return GCR_E_WORKSPACE;
   return rerank_impl(Xq, nq, Xg, ng, d, p, idx_out, dist_out, w, (cudaStream_t)stream);
+}
+
+size_t gcrv_profiles_workspace_size(int64_t F, int32_t d, int32_t C, int32_t n_cams) {
+  if (F < 1 || C < 1 || d < 4 || d > kMaxD || d % 4 || n_cams < 1 || n_cams > 64 || F > (int64_t)INT32_MAX) return 0;
+  Carve c(nullptr, 0);
+  return gcrv_carve(c, F, d, C, n_cams, nullptr) + 256;
+}
+
+int gcrv_profiles(const float* frames, int64_t F, int32_t d, const int64_t* trk_off, const int32_t* trk_cam,
+                  int32_t C, int32_t n_cams, float lambda, float* W_out, void* ws, size_t ws_bytes,
+                  gcr_stream_t stream) {
+  if (!frames || !trk_off || !trk_cam || !W_out) return GCR_E_INVALID;
+  if (F < 1 || C < 1 || n_cams < 1 || n_cams > 64 || F > (int64_t)INT32_MAX) return GCR_E_INVALID;
+  if (d < 4 || d > kMaxD) return GCR_E_INVALID;
+  if (d % 4 != 0) return GCR_E_UNSUPPORTED;
+  if (!(lambda > 0.f) || !std::isfinite(lambda)) return GCR_E_INVALID;
+  if (!ws) return GCR_E_WORKSPACE;
+  Carve c(ws, ws_bytes);
+  GcrvWs w;
+  if (gcrv_carve(c, F, d, C, n_cams, &w) > ws_bytes) return GCR_E_WORKSPACE;
+  StageScope sc_(GCR_STAGE_GCRV, (cudaStream_t)stream);
+  GCR_CUDA_TRY(launch_gcrv(frames, F, d, trk_off, trk_cam, C, n_cams, lambda, W_out, w, (cudaStream_t)stream));
+  return GCR_OK;
+}
+
+
+size_t gcr_gallery_bytes(int64_t ng, int32_t d, const gcr_params* p) {
+  Resolved r;
+  if (check_serve_params(p, ng, d, &r) != GCR_OK) return 0;
+  Carve c(nullptr, 0);
+  return carve_gallery(c, ng, d, p, nullptr) + 256;
+}
+
+size_t gcr_gallery_build_workspace_size(int64_t ng, int32_t d, const gcr_params* p) {
+  Resolved r;
+  if (check_serve_params(p, ng, d, &r) != GCR_OK) return 0;
+  Carve c(nullptr, 0);
+  return carve_gallery_build(c, ng, d, p, r, nullptr) + 256;
+}
+
+int gcr_gallery_build(const float* Xg, int64_t ng, int32_t d, const gcr_params* p, void* state, size_t state_bytes,
+                      void* ws, size_t ws_bytes, gcr_stream_t stream) {
+  Resolved r;
+  int s = check_serve_params(p, ng, d, &r);
+  if (s != GCR_OK) return s;
+  if (!Xg || !state) return GCR_E_INVALID;
+  if (!ws) return GCR_E_WORKSPACE;
+  Carve cs(state, state_bytes);
+  GalleryView g;
+  if (carve_gallery(cs, ng, d, p, &g) > state_bytes) return GCR_E_WORKSPACE;
+  Carve cw(ws, ws_bytes);
+  GalleryBuildWs w;
+  if (carve_gallery_build(cw, ng, d, p, r, &w) > ws_bytes) return GCR_E_WORKSPACE;
+  cudaStream_t st = (cudaStream_t)stream;
+  const int n = (int)ng;
+  const bool bf = p->precision == GCR_PREC_BF16;
+  GCR_CUDA_TRY(launch_normalize(Xg, g.layers, ng, d, st));
+  for (int t = 0; t < p->T; ++t) {
+    float* cur = g.layers + (size_t)t * n * d;
+    float* nxt = g.layers + (size_t)(t + 1) * n * d;
+    Carve cb(w.inner, w.inner_bytes);
+    BuildWs bw;
+    carve_build(cb, ng, d, p, r, &bw);
+    s = build_graph_impl(cur, ng, d, nullptr, p, r, &w.g, bw, st);
+    if (s != GCR_OK) return s;
+    GCR_CUDA_TRY(launch_layer_degree(w.g.deg_r, w.g.deg_c, n, p->symmetric, g.deg + (size_t)t * n, st));
+    GCR_CUDA_TRY(launch_propagate(w.g.op_rowptr, w.g.op_len, w.g.op_col, w.g.op_val, cur, nxt, n, d, st));
+  }
+  for (int t = 0; t <= p->T; ++t) {
+    GCR_CUDA_TRY(launch_row_stats(g.layers + (size_t)t * n * d, n, d, g.n64 + (size_t)t * n, g.n32 + (size_t)t * n,
+                                  bf ? g.xb + (size_t)t * n * d : nullptr, bf ? g.enrm + (size_t)t * n : nullptr,
+                                  bf ? g.anrm + (size_t)t * n : nullptr, g.sc + t, st));
+  }
+  return GCR_OK;
+}
+
+size_t gcr_serve_workspace_size(int64_t b, int64_t ng, int32_t d, const gcr_params* p) {
+  Resolved r;
+  if (b < 1 || check_serve_params(p, ng, d, &r) != GCR_OK) return 0;
+  Carve c(nullptr, 0);
+  return carve_serve(c, b, d, p, r, nullptr) + 256;
+}
+
+int gcr_serve(const void* state, size_t state_bytes, int64_t ng, const float* Xq, int64_t b, int32_t d,
+              const gcr_params* p, int32_t* idx_out, float* dist_out, int64_t* stats, void* ws, size_t ws_bytes,
+              gcr_stream_t stream) {
+  Resolved r;
+  int s = check_serve_params(p, ng, d, &r);
+  if (s != GCR_OK) return s;
+  if (!state || !Xq || !idx_out || !dist_out || b < 1 || b > (1 << 20)) return GCR_E_INVALID;
+  Carve cs(const_cast<void*>(state), state_bytes);
+  GalleryView g;
+  if (carve_gallery(cs, ng, d, p, &g) > state_bytes) return GCR_E_WORKSPACE;
+  if (!ws) return GCR_E_WORKSPACE;
+  Carve cw(ws, ws_bytes);
+  ServeWs w;
+  if (carve_serve(cw, b, d, p, r, &w) > ws_bytes) return GCR_E_WORKSPACE;
+  cudaStream_t st = (cudaStream_t)stream;
+  unsigned long long* stp = stats ? reinterpret_cast<unsigned long long*>(stats) : w.stats;
+  const int nq = (int)b, n = (int)ng;
+  {
+    StageScope sc_(GCR_STAGE_NORMALIZE, st);
+    GCR_CUDA_TRY(launch_normalize(Xq, w.xq[0], b, d, st));
+  }
+  int cur = 0;
+  for (int t = 0; t < p->T; ++t) {
+    if (p->k > 0) {
+      s = serve_knn(w.xq[cur], nq, d, p, p->k, r.kp, gallery_layer(g, t, n, d), n, w, stp, w.nbr, w.d2, st);
+      if (s != GCR_OK) return s;
+    }
+    StageScope sc_(GCR_STAGE_PROPAGATE, st);
+    GCR_CUDA_TRY(launch_query_step(w.xq[cur], nq, d, g.layers + (size_t)t * n * d, g.deg + (size_t)t * n, w.nbr,
+                                   w.d2, p->k, p->gamma, p->symmetric, w.xq[cur ^ 1], st));
+    cur ^= 1;
+  }
+  return serve_knn(w.xq[cur], nq, d, p, p->topk_out, serve_kp_final(p), gallery_layer(g, p->T, n, d), n, w, stp,
+                   idx_out, dist_out, st);
 }
 
 size_t gcr_pipeline_workspace_size(int64_t n, int64_t nq, int32_t d, const gcr_params* p) {
@@ -514,9 +914,15 @@ int gcr_pipeline(const float* X, int64_t n, int64_t nq, int32_t d, const int32_t
     float* tmp = cur; cur = nxt; nxt = tmp;
   }
   Carve cr(w.inner, w.inner_bytes);
-  RerankWs rw;
-  carve_rerank(cr, nq, n - nq, d, p->precision == GCR_PREC_BF16, &rw);
-  s = rerank_impl(cur, nq, cur + (size_t)nq * d, n - nq, d, p, idx_out, dist_out, rw, st);
+  if (rerank_uses_pool(p, n - nq)) {
+    TopkRerankWs tw;
+    carve_topk_rerank(cr, nq, n - nq, d, p, &tw);
+    s = topk_rerank_impl(cur, nq, cur + (size_t)nq * d, n - nq, d, p, idx_out, dist_out, tw, st);
+  } else {
+    RerankWs rw;
+    carve_rerank(cr, nq, n - nq, d, p->precision == GCR_PREC_BF16, &rw);
+    s = rerank_impl(cur, nq, cur + (size_t)nq * d, n - nq, d, p, idx_out, dist_out, rw, st);
+  }
   if (s != GCR_OK) return s;
   if (X_final) GCR_CUDA_TRY(cudaMemcpyAsync(X_final, cur, sizeof(float) * n * d, cudaMemcpyDeviceToDevice, st));
   return GCR_OK;

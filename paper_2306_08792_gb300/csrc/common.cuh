@@ -87,6 +87,9 @@ __device__ __forceinline__ float ordered_to_float(uint32_t u) {
   return __uint_as_float((u & 0x80000000u) ? (u & 0x7fffffffu) : ~u);
 }
 
+struct GcrvWs;
+size_t gcrv_carve(Carve& c, int64_t F, int d, int C, int ncam, GcrvWs* w);
+
 }  // namespace gcr
 
 #define GCR_CUDA_TRY(expr)                         \

@@ -19,37 +19,47 @@ cudaError_t launch_normalize(const float* X_in, float* X_out, int64_t n, int d, 
 cudaError_t launch_row_stats(const float* X, int n, int d, double* n64, float* n32,
                              __nv_bfloat16* xb, float* enrm, float* anrm, RowScalars* sc,
                              cudaStream_t st);
+cudaError_t launch_split3(const float* X, int n, int d, int gallery_order, __nv_bfloat16* out, cudaStream_t st);
 
 // ---- sgemm.cu
 size_t sgemm_pool_smem();
-cudaError_t launch_sgemm_pool(const float* X, int n, int d, const int* cam, int kp, bool cross,
-                              float* pool_v, int* pool_i, cudaStream_t st);
-cudaError_t launch_sgemm_band(const float* X, int n, int d, const int* cam, const int* count,
-                              int cap, const int* band_row, const int* band_kind, const float* band_thr,
-                              int bcap, int* band_cnt, float* band_v, int* band_i, cudaStream_t st);
+// Pools of S = A . B^T rows: [split][kind][na][kp]; self_excl skips j == i (A == B).
+cudaError_t launch_sgemm_pool(const float* A, int na, const float* B, int nb, int d, const int* cam, int kp,
+                              bool cross, int self_excl, int splits, float* pool_v, int* pool_i, cudaStream_t st);
+// Threshold rescan: rows X[band_row[u]] against all rows of Bm (n of them).
+cudaError_t launch_sgemm_band(const float* X, const float* Bm, int n, int d, const int* cam, int self_excl,
+                              const int* count, int cap, const int* band_row, const int* band_kind,
+                              const float* band_thr, int bcap, int* band_cnt, float* band_v, int* band_i,
+                              cudaStream_t st);
 cudaError_t launch_sgemm_dist(const float* Xq, int nq, const float* Xg, int ng, int d,
                               const float* nrm_q, const float* nrm_g, float* D, cudaStream_t st);
 
 // ---- umma.cu (tcgen05 BF16 path)
-cudaError_t launch_umma_pool(const __nv_bfloat16* Xb, int n, int d, const int* cam, bool cross,
-                             float* pool_v, int* pool_i, int* err_flag, cudaStream_t st);
-cudaError_t launch_umma_band(const __nv_bfloat16* Xb, int n, int d, const int* cam,
+// Pools of S = A . B^T rows: [split][kind][na][kp], kp = 64 or 128 (128 without cross).
+cudaError_t launch_umma_pool(const __nv_bfloat16* Ab, int na, const __nv_bfloat16* Bb, int nb, int d,
+                             const int* cam, bool cross, int self_excl, int kp, int splits, float* pool_v,
+                             int* pool_i, cudaStream_t st);
+// Threshold rescan: gathered rows Ab (cap rows, *count valid) against the n rows of Xb.
+cudaError_t launch_umma_band(const __nv_bfloat16* Xb, int n, int d, const int* cam, int self_excl,
                              const __nv_bfloat16* Ab, const int* count, int cap, const int* band_row,
-                             const int* band_kind, const float* band_thr, int bcap, int* band_cnt,
-                             float* band_v, int* band_i, int* err_flag, cudaStream_t st);
-cudaError_t launch_umma_dist(const __nv_bfloat16* Qb, int nq, const __nv_bfloat16* Gb, int ng,
-                             int d, const float* nrm_q, const float* nrm_g, float* D,
-                             int* err_flag, cudaStream_t st);
+                             const int* band_kind, const float* band_thr, int bcap, int* band_cnt, float* band_v,
+                             int* band_i, cudaStream_t st);
+cudaError_t launch_umma_dist(const __nv_bfloat16* Qb, int nq, const __nv_bfloat16* Gb, int ng, int d,
+                             const float* nrm_q, const float* nrm_g, float* D, cudaStream_t st);
+int umma_read_and_clear_timeouts();
+cudaError_t launch_wait_probe(unsigned long long limit_ns, cudaStream_t st);  // bounded waits that ran out since the last call (-1: error)
 
 // ---- refine.cu
 struct RefineArgs {
-  const float* X;
+  const float* X;           // rows whose neighbours are refined (n x d)
+  const float* XB;          // rows the candidates index (equal to X for the offline graph)
   int n, d, k, kinds;
   int precision;            // GCR_PREC_FP32 / GCR_PREC_BF16
-  const double* n64;
-  const float* enrm;
+  const double* n64;        // ||x_i||^2 of the rows of X
+  const double* n64B;       // ||x_j||^2 of the rows of XB
+  const float* enrm;        // BF16 statistics of the rows of X
   const float* anrm;
-  const RowScalars* sc;
+  const RowScalars* sc;     // maxima over the rows of XB
   const float* pool_v;      // [kinds][n][kp]
   const int* pool_i;
   int kp;
@@ -99,6 +109,39 @@ cudaError_t launch_build_operator(const GraphArgs& g, cudaStream_t st);
 // ---- propagate.cu
 cudaError_t launch_propagate(const int* rowptr, const int* len, const int* col, const float* val,
                              const float* X_in, float* X_out, int n, int d, cudaStream_t st);
+
+// ---- gcrv.cu
+struct GcrvWs {
+  int rows_cap;
+  float* inv;
+  int* cam_cnt;
+  int64_t* cam_nf;
+  int* blk0;
+  int* perm;
+  int* pos;
+  int64_t* fstart;
+  int64_t* foff;
+  int* row_cam;
+  int* flist;
+  float* mu;
+  float* mu_cam;
+  float* G;
+  float* X;
+  float* R;
+  float* P;
+  float* Q;
+  double* rr;
+};
+int gcrv_iterations(float lambda);
+cudaError_t launch_gcrv(const float* frames, int64_t F, int d, const int64_t* off, const int32_t* cam, int C,
+                        int ncam, float lambda, float* W, const GcrvWs& w, cudaStream_t st);
+
+// ---- serve.cu
+cudaError_t launch_merge_splits(const float* pv, const int* pi, int S, int kinds, int na, int kp, float* ov, int* oi,
+                                cudaStream_t st);
+cudaError_t launch_query_step(const float* xq, int b, int d, const float* G, const float* deg, const int32_t* nbr,
+                              const float* d2, int k, float gamma, int symmetric, float* out, cudaStream_t st);
+cudaError_t launch_layer_degree(const float* dr, const float* dc, int n, int symmetric, float* out, cudaStream_t st);
 
 // ---- sort.cu
 cudaError_t launch_rank_rows(const float* D, int nq, int ng, int K, int32_t* idx_out,

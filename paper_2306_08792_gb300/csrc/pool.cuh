@@ -30,24 +30,32 @@ __device__ __forceinline__ void pool_init(PoolOwner& o, bool valid) {
   o.len = 0;
 }
 
-__device__ __forceinline__ void pool_push(PoolOwner& o, float v, int j, float* qv, int* qi, int sw) {
-  if (v > o.tau) {
-    int s = o.qcnt ^ sw;
-    qv[s] = v;
-    qi[s] = j;
-    ++o.qcnt;
-  }
+// Branch-free append: the candidate is always written into the next free slot and the count
+// only advances when it passes (ok and v > tau). The caller guarantees qcnt < kQCap before
+// every call (pool_make_room with room = values pushed before the next check).
+__device__ __forceinline__ void pool_push(PoolOwner& o, float v, int j, bool ok, float* qv, int* qi, int sw) {
+  const int s = o.qcnt ^ sw;
+  qv[s] = v;
+  qi[s] = j;
+  o.qcnt += (ok && v > o.tau) ? 1 : 0;
 }
 
 // Warp-cooperative merge of the queue of the row owned by lane `owner` into its list.
 // qv_row/qi_row: that row's queue; lv/li: that row's list (KP entries) in global memory.
+// Kept out of line (the merge is rare and large); takes and returns plain values so that the
+// caller's owner state stays in registers. Returns the new list length and its last score.
+struct MergeResult {
+  int len;
+  float last;
+};
+
 template <int KP>
-__device__ __forceinline__ void pool_merge_row(int owner, int lane, float* lv, int* li,
-                                               const float* qv_row, const int* qi_row, int sw,
-                                               PoolOwner& me) {
+__device__ __noinline__ MergeResult pool_merge_row(int owner, int lane, float* lv, int* li,
+                                                   const float* qv_row, const int* qi_row, int sw,
+                                                   int my_qcnt, int my_len) {
   __syncwarp();  // the owner's queue writes must be visible to the whole warp
-  int q = __shfl_sync(GCR_FULL, me.qcnt, owner);
-  int L = __shfl_sync(GCR_FULL, me.len, owner);
+  int q = __shfl_sync(GCR_FULL, my_qcnt, owner);
+  int L = __shfl_sync(GCR_FULL, my_len, owner);
   float a = -CUDART_INF_F;
   int ai = -1;
   if (lane < q) {
@@ -57,62 +65,68 @@ __device__ __forceinline__ void pool_merge_row(int owner, int lane, float* lv, i
   warp_sort32_desc(a, ai, lane);
   float ar = __shfl_sync(GCR_FULL, a, 31 - lane);
   int ari = __shfl_sync(GCR_FULL, ai, 31 - lane);
-  float last;
-  if constexpr (KP == 32) {
-    float b = -CUDART_INF_F;
-    int bi = -1;
-    if (lane < L) { b = lv[lane]; bi = li[lane]; }
-    // top 32 of (list desc) U (queue desc): elementwise max against the reversed queue
-    // gives a bitonic sequence holding exactly those 32; one bitonic merge sorts it.
-    if (better(ar, ari, b, bi)) { b = ar; bi = ari; }
-    warp_merge32_desc(b, bi, lane);
-    lv[lane] = b;
-    li[lane] = bi;
-    last = __shfl_sync(GCR_FULL, b, 31);
-  } else {
-    static_assert(KP == 64, "pool size must be 32 or 64");
-    float b0 = -CUDART_INF_F, b1 = -CUDART_INF_F;
-    int bi0 = -1, bi1 = -1;
-    if (lane < L) { b0 = lv[lane]; bi0 = li[lane]; }
-    if (lane + 32 < L) { b1 = lv[lane + 32]; bi1 = li[lane + 32]; }
-    // C[s] = max(B[s], Qpad[63 - s]); Qpad is -inf past 32, so only the upper half changes.
-    if (better(ar, ari, b1, bi1)) { b1 = ar; bi1 = ari; }
-    // bitonic merge of 64: stride 32 inside the lane, then each half with shuffles
-    if (better(b1, bi1, b0, bi0)) {
-      float tv = b0; b0 = b1; b1 = tv;
-      int ti = bi0; bi0 = bi1; bi1 = ti;
+  static_assert(KP == 32 || KP == 64 || KP == 128, "pool size must be 32, 64 or 128");
+  constexpr int P = KP / 32;  // list entries per lane: entry e = p*32 + lane
+  float b[P];
+  int bi[P];
+#pragma unroll
+  for (int p = 0; p < P; ++p) {
+    const int e = p * 32 + lane;
+    b[p] = e < L ? lv[e] : -CUDART_INF_F;
+    bi[p] = e < L ? li[e] : -1;
+  }
+  // Top KP of (list, descending) U (queue, descending): C[s] = max(B[s], Q[KP-1-s]) with Q
+  // padded by -inf past 32 entries is a bitonic sequence holding exactly those KP; only the
+  // last 32 entries can change. A bitonic merge then sorts it.
+  if (better(ar, ari, b[P - 1], bi[P - 1])) { b[P - 1] = ar; bi[P - 1] = ari; }
+#pragma unroll
+  for (int stride = KP / 2; stride >= 32; stride >>= 1) {
+#pragma unroll
+    for (int p = 0; p < P; ++p) {
+      const int q2 = p ^ (stride >> 5);
+      if (q2 > p && better(b[q2], bi[q2], b[p], bi[p])) {
+        float tv = b[p]; b[p] = b[q2]; b[q2] = tv;
+        int ti = bi[p]; bi[p] = bi[q2]; bi[q2] = ti;
+      }
     }
-    warp_merge32_desc(b0, bi0, lane);
-    warp_merge32_desc(b1, bi1, lane);
-    lv[lane] = b0;
-    li[lane] = bi0;
-    lv[lane + 32] = b1;
-    li[lane + 32] = bi1;
-    last = __shfl_sync(GCR_FULL, b1, 31);
   }
-  int nl = min(KP, L + q);
-  if (lane == owner) {
-    me.len = nl;
-    me.qcnt = 0;
-    me.tau = (nl == KP) ? last : -CUDART_INF_F;
+#pragma unroll
+  for (int p = 0; p < P; ++p) {
+    warp_merge32_desc(b[p], bi[p], lane);
+    lv[p * 32 + lane] = b[p];
+    li[p * 32 + lane] = bi[p];
   }
+  const float last = __shfl_sync(GCR_FULL, b[P - 1], 31);
   __syncwarp();  // queue slots are reused only after every lane has read them
+  return MergeResult{min(KP, L + q), last};
 }
 
-// Merge every row of this warp whose queue holds more than kQCap - room entries.
-// row_of_lane0: global row of lane 0; q_base: CTA-local row index of lane 0 in the queue.
+template <int KP>
+__device__ __forceinline__ void pool_merge_apply(int owner, int lane, float* lv, int* li, const float* qv_row,
+                                                 const int* qi_row, int sw, PoolOwner& me) {
+  const MergeResult r = pool_merge_row<KP>(owner, lane, lv, li, qv_row, qi_row, sw, me.qcnt, me.len);
+  if (lane == owner) {
+    me.len = r.len;
+    me.qcnt = 0;
+    me.tau = (r.len == KP) ? r.last : -CUDART_INF_F;
+  }
+}
+
+// Merge every row of this warp whose queue could not take `room` more pushes (the branch-free
+// push writes one slot past the count, so the count must stay below kQCap - room).
+// row_of_lane0: global row of lane 0; qrow0: CTA-local queue row of lane 0.
 template <int KP>
 __device__ __forceinline__ void pool_make_room(int room, int lane, PoolOwner& me, int row_of_lane0,
                                                int qrow0, float* qv, int* qi, float* pool_v,
                                                int* pool_i) {
-  unsigned m = __ballot_sync(GCR_FULL, me.qcnt > kQCap - room);
+  unsigned m = __ballot_sync(GCR_FULL, me.qcnt >= kQCap - room);
   while (m) {
     int o = __ffs(m) - 1;
     m &= m - 1;
     int qr = qrow0 + o;
     size_t grow = (size_t)(row_of_lane0 + o);
-    pool_merge_row<KP>(o, lane, pool_v + grow * KP, pool_i + grow * KP, qv + qr * kQCap,
-                       qi + qr * kQCap, qr & 31, me);
+    pool_merge_apply<KP>(o, lane, pool_v + grow * KP, pool_i + grow * KP, qv + qr * kQCap,
+                         qi + qr * kQCap, qr & 31, me);
   }
 }
 
@@ -127,8 +141,8 @@ __device__ __forceinline__ void pool_flush(int lane, bool valid, PoolOwner& me, 
     m &= m - 1;
     int qr = qrow0 + o;
     size_t grow = (size_t)(row_of_lane0 + o);
-    pool_merge_row<KP>(o, lane, pool_v + grow * KP, pool_i + grow * KP, qv + qr * kQCap,
-                       qi + qr * kQCap, qr & 31, me);
+    pool_merge_apply<KP>(o, lane, pool_v + grow * KP, pool_i + grow * KP, qv + qr * kQCap,
+                         qi + qr * kQCap, qr & 31, me);
   }
 }
 

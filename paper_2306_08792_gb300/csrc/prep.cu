@@ -6,9 +6,26 @@
 
 namespace gcr {
 
-// X_out[i] = X_in[i] / ||X_in[i]|| with the norm and the scaling in FP64, so that each
-// output element is the FP32 rounding of the exact quotient (up to one FP64 rounding).
-// One warp per row, 16-byte loads.
+// Float-float accumulation of sum x^2 without FP64 arithmetic (GB300's FP64 rate is low):
+// each product is split exactly (x*x = p + pe with an FMA), each addition is an exact TwoSum
+// into (hi, lo); the result is accurate to about 2^-46 relative, well below the 1e-12 the
+// FP64 tie-break needs from the squared norms.
+struct FF {
+  float hi = 0.f, lo = 0.f;
+  __device__ __forceinline__ void add_sq(float x) {
+    const float p = x * x;
+    const float pe = fmaf(x, x, -p);
+    const float s = hi + p;
+    const float bp = s - hi;
+    lo += (hi - (s - bp)) + (p - bp) + pe;
+    hi = s;
+  }
+  __device__ __forceinline__ double value() const { return (double)hi + (double)lo; }
+};
+
+// X_out[i] = X_in[i] / ||X_in[i]||: the squared norm is accumulated exactly (float-float,
+// combined in FP64 once per row) and 1/||x|| is formed in FP64, so each output element is the
+// FP32 rounding of x * fl32(1/||x||), within one ulp of the exact quotient. One warp per row.
 __global__ void normalize_kernel(const float* __restrict__ X_in, float* __restrict__ X_out,
                                  int64_t n, int d) {
   const int lane = threadIdx.x & 31;
@@ -17,21 +34,23 @@ __global__ void normalize_kernel(const float* __restrict__ X_in, float* __restri
   const float4* src = reinterpret_cast<const float4*>(X_in + row * d);
   float4* dst = reinterpret_cast<float4*>(X_out + row * d);
   const int d4 = d >> 2;
-  double ss = 0.0;
+  FF acc;
   for (int v = lane; v < d4; v += 32) {
     float4 x = src[v];
-    ss += (double)x.x * x.x + (double)x.y * x.y + (double)x.z * x.z + (double)x.w * x.w;
+    acc.add_sq(x.x); acc.add_sq(x.y); acc.add_sq(x.z); acc.add_sq(x.w);
   }
-  ss = warp_sum_d(ss);
-  const double inv = ss > 0.0 ? 1.0 / sqrt(ss) : 0.0;
+  const double ss = warp_sum_d(acc.value());
+  const float inv = ss > 0.0 ? (float)(1.0 / sqrt(ss)) : 0.f;
   for (int v = lane; v < d4; v += 32) {
     float4 x = src[v];
-    dst[v] = make_float4((float)(x.x * inv), (float)(x.y * inv), (float)(x.z * inv), (float)(x.w * inv));
+    dst[v] = make_float4(x.x * inv, x.y * inv, x.z * inv, x.w * inv);
   }
 }
 
-// n64[i] = ||x_i||^2 in FP64, n32[i] = its FP32 rounding; with xb != NULL also the BF16
-// shadow xb = bf16_rn(x), enrm[i] = ||xb_i - x_i|| and anrm[i] = ||xb_i|| (FP64 sums).
+// n64[i] = ||x_i||^2 (float-float accumulation, combined in FP64), n32[i] = its FP32 rounding;
+// with xb != NULL also the BF16 shadow xb = bf16_rn(x), enrm[i] >= ||xb_i - x_i|| and
+// anrm[i] >= ||xb_i|| (FP32 sums rounded up by a relative margin that covers their own
+// accumulation error: at most (d/32 + 5) * 2^-24 < 1e-3 for d <= 4096).
 __global__ void row_stats_kernel(const float* __restrict__ X, int n, int d, double* __restrict__ n64,
                                  float* __restrict__ n32, __nv_bfloat16* __restrict__ xb,
                                  float* __restrict__ enrm, float* __restrict__ anrm) {
@@ -40,34 +59,35 @@ __global__ void row_stats_kernel(const float* __restrict__ X, int n, int d, doub
   if (row >= n) return;
   const float4* src = reinterpret_cast<const float4*>(X + (size_t)row * d);
   const int d4 = d >> 2;
-  double ss = 0.0, ee = 0.0, aa = 0.0;
+  FF acc;
+  float ee = 0.f, aa = 0.f;
   for (int v = lane; v < d4; v += 32) {
     float4 x = src[v];
-    ss += (double)x.x * x.x + (double)x.y * x.y + (double)x.z * x.z + (double)x.w * x.w;
+    acc.add_sq(x.x); acc.add_sq(x.y); acc.add_sq(x.z); acc.add_sq(x.w);
     if (xb) {
       __nv_bfloat16 b0 = __float2bfloat16_rn(x.x), b1 = __float2bfloat16_rn(x.y);
       __nv_bfloat16 b2 = __float2bfloat16_rn(x.z), b3 = __float2bfloat16_rn(x.w);
       __nv_bfloat162* o = reinterpret_cast<__nv_bfloat162*>(xb + (size_t)row * d + 4 * v);
       o[0] = __halves2bfloat162(b0, b1);
       o[1] = __halves2bfloat162(b2, b3);
-      double f0 = __bfloat162float(b0), f1 = __bfloat162float(b1);
-      double f2 = __bfloat162float(b2), f3 = __bfloat162float(b3);
-      double e0 = f0 - x.x, e1 = f1 - x.y, e2 = f2 - x.z, e3 = f3 - x.w;
-      ee += e0 * e0 + e1 * e1 + e2 * e2 + e3 * e3;
-      aa += f0 * f0 + f1 * f1 + f2 * f2 + f3 * f3;
+      const float f0 = __bfloat162float(b0), f1 = __bfloat162float(b1);
+      const float f2 = __bfloat162float(b2), f3 = __bfloat162float(b3);
+      const float e0 = f0 - x.x, e1 = f1 - x.y, e2 = f2 - x.z, e3 = f3 - x.w;  // exact differences
+      ee = fmaf(e0, e0, fmaf(e1, e1, fmaf(e2, e2, fmaf(e3, e3, ee))));
+      aa = fmaf(f0, f0, fmaf(f1, f1, fmaf(f2, f2, fmaf(f3, f3, aa))));
     }
   }
-  ss = warp_sum_d(ss);
+  const double ss = warp_sum_d(acc.value());
   if (xb) {
-    ee = warp_sum_d(ee);
-    aa = warp_sum_d(aa);
+    ee = warp_sum(ee);
+    aa = warp_sum(aa);
   }
   if (lane == 0) {
     n64[row] = ss;
     n32[row] = (float)ss;
     if (xb) {
-      enrm[row] = (float)(sqrt(ee) * (1.0 + 1e-6));
-      anrm[row] = (float)(sqrt(aa) * (1.0 + 1e-6));
+      enrm[row] = sqrtf(ee * 1.002f) * 1.0001f;
+      anrm[row] = sqrtf(aa * 1.002f) * 1.0001f;
     }
   }
 }
@@ -115,6 +135,31 @@ __global__ void row_scalars_kernel(const double* __restrict__ n64, const float* 
       sc->amax = amax;
     }
   }
+}
+
+// Compensated BF16 operands for the re-ranked distances: x = hi + e exactly (e in FP32),
+// hi = bf16(x), lo = bf16(e). Queries become [hi | hi | lo], gallery rows [hi | lo | hi], so
+// one BF16 product over 3d terms gives hi.hi' + hi.lo' + lo.hi', whose error against x.x'
+// is <= ||x|| ||e'-lo'|| + ||e-lo|| ||x'|| + ||e|| ||e'|| + accumulation <= ~3 * 2^-16 for
+// unit rows (instead of ~2^-7 for hi.hi' alone).
+__global__ void split3_kernel(const float* __restrict__ X, int n, int d, int gallery_order,
+                              __nv_bfloat16* __restrict__ out) {
+  const long t = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= (long)n * d) return;
+  const long row = t / d, c = t % d;
+  const float x = X[t];
+  const __nv_bfloat16 hi = __float2bfloat16_rn(x);
+  const __nv_bfloat16 lo = __float2bfloat16_rn(x - __bfloat162float(hi));
+  __nv_bfloat16* o = out + row * 3 * d;
+  o[c] = hi;
+  o[d + c] = gallery_order ? lo : hi;
+  o[2 * d + c] = gallery_order ? hi : lo;
+}
+
+cudaError_t launch_split3(const float* X, int n, int d, int gallery_order, __nv_bfloat16* out, cudaStream_t st) {
+  const long total = (long)n * d;
+  split3_kernel<<<(unsigned)((total + 255) / 256), 256, 0, st>>>(X, n, d, gallery_order, out);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_normalize(const float* X_in, float* X_out, int64_t n, int d, cudaStream_t st) {

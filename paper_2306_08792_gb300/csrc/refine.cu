@@ -63,11 +63,21 @@ __device__ __forceinline__ void wl_sort(WList<P>& L, int lane) {
   for (int size = 2; size <= N; size <<= 1) {
 #pragma unroll
     for (int stride = size >> 1; stride > 0; stride >>= 1) {
-      if (stride == 32) {  // only for P == 2: partner lives in the same lane
-        if (P == 2 && better_d(L.sig[P - 1], L.id[P - 1], L.sig[0], L.id[0])) {
-          double ts = L.sig[0]; L.sig[0] = L.sig[P - 1]; L.sig[P - 1] = ts;
-          int ti = L.id[0]; L.id[0] = L.id[P - 1]; L.id[P - 1] = ti;
-          double tv = L.val[0]; L.val[0] = L.val[P - 1]; L.val[P - 1] = tv;
+      if (stride >= 32) {  // partner lives in the same lane: entry p ^ (stride / 32)
+#pragma unroll
+        for (int p = 0; p < P; ++p) {
+          const int q2 = p ^ (stride >> 5);
+          if (q2 > p) {
+            const int s = p * 32 + lane;
+            const bool desc = (s & size) == 0;
+            const bool sw = desc ? better_d(L.sig[q2], L.id[q2], L.sig[p], L.id[p])
+                                 : better_d(L.sig[p], L.id[p], L.sig[q2], L.id[q2]);
+            if (sw) {
+              double ts = L.sig[p]; L.sig[p] = L.sig[q2]; L.sig[q2] = ts;
+              int ti = L.id[p]; L.id[p] = L.id[q2]; L.id[q2] = ti;
+              double tv = L.val[p]; L.val[p] = L.val[q2]; L.val[q2] = tv;
+            }
+          }
         }
       } else {
 #pragma unroll
@@ -87,19 +97,27 @@ __device__ __forceinline__ void wl_sort(WList<P>& L, int lane) {
   }
 }
 
-// Merge a sorted-descending chunk of 32 (one per lane) into a sorted list of 64: keeps the top 64.
-__device__ __forceinline__ void wl_merge64(WList<2>& L, double cs, int ci, double cv, int lane) {
+// Merge a sorted-descending chunk of 32 (one per lane) into a sorted list of 32P: keeps the top 32P.
+template <int P>
+__device__ __forceinline__ void wl_merge(WList<P>& L, double cs, int ci, double cv, int lane) {
   double rs = __shfl_sync(GCR_FULL, cs, 31 - lane);
   int ri = __shfl_sync(GCR_FULL, ci, 31 - lane);
   double rv = __shfl_sync(GCR_FULL, cv, 31 - lane);
-  if (better_d(rs, ri, L.sig[1], L.id[1])) { L.sig[1] = rs; L.id[1] = ri; L.val[1] = rv; }
-  if (better_d(L.sig[1], L.id[1], L.sig[0], L.id[0])) {
-    double ts = L.sig[0]; L.sig[0] = L.sig[1]; L.sig[1] = ts;
-    int ti = L.id[0]; L.id[0] = L.id[1]; L.id[1] = ti;
-    double tv = L.val[0]; L.val[0] = L.val[1]; L.val[1] = tv;
+  if (better_d(rs, ri, L.sig[P - 1], L.id[P - 1])) { L.sig[P - 1] = rs; L.id[P - 1] = ri; L.val[P - 1] = rv; }
+#pragma unroll
+  for (int stride = 16 * P; stride >= 32; stride >>= 1) {
+#pragma unroll
+    for (int p = 0; p < P; ++p) {
+      const int q2 = p ^ (stride >> 5);
+      if (q2 > p && better_d(L.sig[q2], L.id[q2], L.sig[p], L.id[p])) {
+        double ts = L.sig[p]; L.sig[p] = L.sig[q2]; L.sig[q2] = ts;
+        int ti = L.id[p]; L.id[p] = L.id[q2]; L.id[q2] = ti;
+        double tv = L.val[p]; L.val[p] = L.val[q2]; L.val[q2] = tv;
+      }
+    }
   }
 #pragma unroll
-  for (int p = 0; p < 2; ++p) {
+  for (int p = 0; p < P; ++p) {
 #pragma unroll
     for (int stride = 16; stride > 0; stride >>= 1) {
       double os = __shfl_xor_sync(GCR_FULL, L.sig[p], stride);
@@ -194,7 +212,7 @@ __device__ __forceinline__ void rescore(const RefineArgs& a, const float4 (&xi)[
       j[t] = e < r ? jj : -1;
     }
     float s[4];
-    dot4_f32<VPL>(a.X, a.d, xi, j, lane, s);
+    dot4_f32<VPL>(a.XB, a.d, xi, j, lane, s);
 #pragma unroll
     for (int t = 0; t < 4; ++t) {
       const int e = e0 + t;
@@ -203,7 +221,7 @@ __device__ __forceinline__ void rescore(const RefineArgs& a, const float4 (&xi)[
         for (int p = 0; p < P; ++p) {
           if (e == p * 32 + lane) {
             L.val[p] = (double)s[t];
-            L.sig[p] = (double)s[t] - 0.5 * a.n64[j[t]];
+            L.sig[p] = (double)s[t] - 0.5 * a.n64B[j[t]];
           }
         }
       }
@@ -241,12 +259,12 @@ __device__ void finalize(const RefineArgs& a, const float4 (&xi)[VPL], WList<P>&
       for (int p = 0; p < P; ++p) sig64[p] = -CUDART_INF;
       for (int e = acnt; e < zcnt; ++e) {
         const int j = wl_id(L, e);
-        const double dot = dot_f64<VPL>(a.X, a.d, xi, j, lane);
+        const double dot = dot_f64<VPL>(a.XB, a.d, xi, j, lane);
 #pragma unroll
         for (int p = 0; p < P; ++p) {
           if (e == p * 32 + lane) {
             L.val[p] = dot;
-            sig64[p] = dot - 0.5 * a.n64[j];
+            sig64[p] = dot - 0.5 * a.n64B[j];
           }
         }
       }
@@ -280,7 +298,7 @@ __device__ void finalize(const RefineArgs& a, const float4 (&xi)[VPL], WList<P>&
     else if (e >= acnt && e < zcnt && acnt < kk && rank[p] < kk - acnt) slot = acnt + rank[p];
     if (slot >= 0) {
       const int j = L.id[p];
-      double dd = n_i + a.n64[j] - 2.0 * L.val[p];
+      double dd = n_i + a.n64B[j] - 2.0 * L.val[p];
       onbr[slot] = j;
       od2[slot] = (float)(dd > 0.0 ? dd : 0.0);
     }
@@ -377,7 +395,7 @@ __global__ void __launch_bounds__(256) refine_pool_kernel(RefineArgs a) {
 }
 
 // One warp per uncertified (row, kind): every band entry (score >= threshold) is re-scored.
-template <int VPL>
+template <int VPL, int P>
 __global__ void __launch_bounds__(256) refine_band_kernel(RefineArgs a) {
   const int lane = threadIdx.x & 31;
   const int U = *a.unc_count;
@@ -391,12 +409,12 @@ __global__ void __launch_bounds__(256) refine_band_kernel(RefineArgs a) {
     }
     double delta, eps;
     RowScalars sc;
-    bounds<2>(a, row, VPL, delta, eps, sc);
+    bounds<P>(a, row, VPL, delta, eps, sc);
     float4 xi[VPL];
     load_row<VPL>(a.X, a.d, row, lane, xi);
-    WList<2> L;
+    WList<P> L;
 #pragma unroll
-    for (int p = 0; p < 2; ++p) { L.sig[p] = -CUDART_INF; L.id[p] = 0x7fffffff; L.val[p] = 0.0; }
+    for (int p = 0; p < P; ++p) { L.sig[p] = -CUDART_INF; L.id[p] = 0x7fffffff; L.val[p] = 0.0; }
     const int* bi = a.band_i + (size_t)u * a.bcap;
     for (int c0 = 0; c0 < cnt; c0 += 32) {
       WList<1> C;
@@ -406,12 +424,12 @@ __global__ void __launch_bounds__(256) refine_band_kernel(RefineArgs a) {
       rescore<VPL, 1>(a, xi, C, min(32, cnt - c0), lane);
       if (C.id[0] < 0) C.id[0] = 0x7fffffff;
       sort32_d(C.sig[0], C.id[0], C.val[0], lane);
-      wl_merge64(L, C.sig[0], C.id[0], C.val[0], lane);
+      wl_merge<P>(L, C.sig[0], C.id[0], C.val[0], lane);
     }
     if (lane == 0 && a.stats) atomicAdd(&a.stats[GCR_STAT_RESCORED], (unsigned long long)cnt);
-    const int r = min(cnt, 64);
+    const int r = min(cnt, 32 * P);
     const int kk = min(a.k, r);
-    finalize<VPL, 2>(a, xi, L, r, kk, eps, row, kind, lane);
+    finalize<VPL, P>(a, xi, L, r, kk, eps, row, kind, lane);
   }
 }
 
@@ -445,20 +463,26 @@ cudaError_t launch_pool_vpl(const RefineArgs& a, cudaStream_t st) {
 cudaError_t launch_refine_pool(const RefineArgs& a, cudaStream_t st) {
   if (a.kp == 32) return launch_pool_vpl<1>(a, st);
   if (a.kp == 64) return launch_pool_vpl<2>(a, st);
+  if (a.kp == 128) return launch_pool_vpl<4>(a, st);
   return cudaErrorInvalidValue;
 }
 
-cudaError_t launch_refine_band(const RefineArgs& a, cudaStream_t st) {
+template <int P>
+cudaError_t launch_band_p(const RefineArgs& a, cudaStream_t st) {
   dim3 grid(152 * 4);
   const int vpl = (a.d + 127) / 128;
-  if (vpl <= 1) refine_band_kernel<1><<<grid, 256, 0, st>>>(a);
-  else if (vpl <= 2) refine_band_kernel<2><<<grid, 256, 0, st>>>(a);
-  else if (vpl <= 4) refine_band_kernel<4><<<grid, 256, 0, st>>>(a);
-  else if (vpl <= 8) refine_band_kernel<8><<<grid, 256, 0, st>>>(a);
-  else if (vpl <= 16) refine_band_kernel<16><<<grid, 256, 0, st>>>(a);
-  else if (vpl <= 32) refine_band_kernel<32><<<grid, 256, 0, st>>>(a);
+  if (vpl <= 1) refine_band_kernel<1, P><<<grid, 256, 0, st>>>(a);
+  else if (vpl <= 2) refine_band_kernel<2, P><<<grid, 256, 0, st>>>(a);
+  else if (vpl <= 4) refine_band_kernel<4, P><<<grid, 256, 0, st>>>(a);
+  else if (vpl <= 8) refine_band_kernel<8, P><<<grid, 256, 0, st>>>(a);
+  else if (vpl <= 16) refine_band_kernel<16, P><<<grid, 256, 0, st>>>(a);
+  else if (vpl <= 32) refine_band_kernel<32, P><<<grid, 256, 0, st>>>(a);
   else return cudaErrorInvalidValue;
   return cudaGetLastError();
+}
+
+cudaError_t launch_refine_band(const RefineArgs& a, cudaStream_t st) {
+  return a.k >= 64 ? launch_band_p<4>(a, st) : launch_band_p<2>(a, st);
 }
 
 cudaError_t launch_gather_bf16(const __nv_bfloat16* Xb, int d, const int* count, const int* rows,

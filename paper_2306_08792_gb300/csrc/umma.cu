@@ -1,9 +1,562 @@
-// placeholder, replaced by the tcgen05 kernels
+// BF16 similarity GEMM on the 5th-generation tensor cores (tcgen05), sm_103a.
+//
+// S = A . B^T with A, B row-major BF16 (K = d contiguous, "K-major"): A holds 128 rows of X,
+// B 256 rows. Per CTA:
+//   warp 0        TMA producer: 64-wide K blocks of A (128 x 64) and B (256 x 64) into a
+//                 3-stage shared-memory ring (128-byte swizzle), mbarrier transaction counts;
+//   warp 1        allocates 512 TMEM columns (two 128 x 256 FP32 accumulators) and, from one
+//                 thread, issues tcgen05.mma.kind::f16 (M=128, N=256, K=16) for each K block,
+//                 committing stage releases and "accumulator full" to mbarriers;
+//   warps 2..5    epilogue for the global graph, warps 6..9 for the cross-camera graph:
+//                 tcgen05.ld.32x32b gives each thread one accumulator row (32 columns per
+//                 load); the scores go into the streaming per-row pool (pool.cuh), or are
+//                 appended to the band buffer, or written out as distances.
+// The accumulator is double-buffered so the MMAs of column tile j+1 overlap the epilogue of
+// tile j. Every mbarrier wait is bounded (2 s of %globaltimer); on a timeout the CTA raises a
+// shared abort flag that every role polls, waits (bounded) for its in-flight MMAs, frees TMEM
+// and returns; the timeout is counted in a device word that gcr_sync reports.
+#include <cuda.h>
+#include <cuda_bf16.h>
+
 #include "common.cuh"
 #include "kernels.h"
+#include "pool.cuh"
+
 namespace gcr {
-cudaError_t launch_umma_pool(const __nv_bfloat16*, int, int, const int*, bool, float*, int*, int*, cudaStream_t) { return cudaErrorNotSupported; }
-cudaError_t launch_umma_band(const __nv_bfloat16*, int, int, const int*, const __nv_bfloat16*, const int*, int, const int*,
-                             const int*, const float*, int, int*, float*, int*, int*, cudaStream_t) { return cudaErrorNotSupported; }
-cudaError_t launch_umma_dist(const __nv_bfloat16*, int, const __nv_bfloat16*, int, int, const float*, const float*, float*, int*, cudaStream_t) { return cudaErrorNotSupported; }
+
+__device__ int g_umma_timeouts;  // bounded waits that ran out since the last gcr_sync
+
+namespace {
+
+constexpr int BM = 128;            // rows of A per tile (UMMA M)
+constexpr int BN = 256;            // rows of B per tile (UMMA N)
+constexpr int BK = 64;             // K elements per stage (128 bytes of BF16: one swizzle row)
+constexpr int NST = 3;             // pipeline stages
+constexpr int A_BYTES = BM * BK * 2;
+constexpr int B_BYTES = BN * BK * 2;
+constexpr int STAGE_BYTES = A_BYTES + B_BYTES;
+constexpr uint32_t TMEM_COLS = 512;
+constexpr unsigned long long kTimeoutNs = 2000000000ull;
+
+enum Mode { POOL = 0, BAND = 1, DIST = 2 };
+
+// ------------------------------------------------------------------------ PTX wrappers
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
 }
+__device__ __forceinline__ unsigned long long globaltimer() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// Bounded wait: false when the CTA is aborting (or this wait ran out and started the abort).
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, volatile int* abort_flag,
+                                          unsigned long long limit_ns = kTimeoutNs) {
+  if (mbar_try_wait(bar, parity)) return true;
+  const unsigned long long t0 = globaltimer();
+  for (uint32_t it = 1;; ++it) {
+    if (mbar_try_wait(bar, parity)) return true;
+    if ((it & 63) == 0) {
+      if (*abort_flag) return false;
+      if (globaltimer() - t0 > limit_ns) {
+        *abort_flag = 1;
+        atomicAdd(&g_umma_timeouts, 1);
+        return false;
+      }
+    }
+  }
+}
+__device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, uint64_t* bar, int x, int y) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4}], [%2];"
+      ::"r"(smem_u32(dst)), "l"(reinterpret_cast<uint64_t>(map)), "r"(smem_u32(bar)), "r"(x), "r"(y)
+      : "memory");
+}
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+// Shared-memory matrix descriptor: K-major tile of rows of 128 bytes, 128-byte swizzle,
+// 8-row core groups 1024 bytes apart (SBO), tile base 1024-byte aligned.
+__device__ __forceinline__ uint64_t smem_desc(uint32_t saddr) {
+  uint64_t d = 0;
+  d |= (uint64_t)((saddr >> 4) & 0x3FFF);          // start address
+  d |= (uint64_t)1 << 16;                          // leading byte offset (unused for swizzled K-major)
+  d |= (uint64_t)(1024 >> 4) << 32;                // stride byte offset
+  d |= (uint64_t)1 << 46;                          // descriptor version (sm_100 family)
+  d |= (uint64_t)2 << 61;                          // layout: 128-byte swizzle
+  return d;
+}
+// Instruction descriptor, kind::f16: D = F32, A = B = BF16, both K-major, N = 256, M = 128.
+constexpr uint32_t kIdesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(BN >> 3) << 17) |
+                            ((uint32_t)(BM >> 4) << 24);
+
+__device__ __forceinline__ void umma_bf16(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc, uint32_t accum) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n"
+      ::"r"(tmem_d), "l"(adesc), "l"(bdesc), "r"(kIdesc), "r"(accum));
+}
+__device__ __forceinline__ void umma_commit(uint64_t* bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
+               : "memory");
+}
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
+  uint32_t r[32];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
+      "%15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+        "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+        "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+// ------------------------------------------------------------------------ kernel
+struct UmmaArgs {
+  int mode;
+  int n;          // rows of B (columns of S)
+  int d;
+  int a_rows;     // rows of A (POOL: rows owning pools; DIST: nq; BAND: band capacity)
+  int self_excl;  // skip column j == row i (A and B are the same matrix)
+  int tps;        // POOL: column tiles per split (grid.y = splits)
+  const int* cam;
+  // POOL
+  float* pool_v;
+  int* pool_i;
+  // BAND
+  const int* count;
+  int cap;
+  const int* band_row;
+  const int* band_kind;
+  const float* band_thr;
+  int bcap;
+  int* band_cnt;
+  float* band_v;
+  int* band_i;
+  // DIST
+  const float* nrm_q;
+  const float* nrm_g;
+  float* D;
+};
+
+struct __align__(8) Bars {
+  uint64_t full[NST];
+  uint64_t empty[NST];
+  uint64_t tfull[2];
+  uint64_t tempty[2];
+  uint64_t drain;
+  uint32_t tmem_base;
+  int abort_flag;
+};
+
+// Work list of a CTA: tiles (row block of A, column tile of B) in order.
+struct Tiles {
+  int count;
+  __device__ int row0(const UmmaArgs& a, int t) const {
+    if (a.mode == POOL) return blockIdx.x * BM;
+    if (a.mode == BAND) return t * BM;
+    return blockIdx.y * BM;
+  }
+  __device__ int col0(const UmmaArgs& a, int t) const {
+    if (a.mode == POOL) return (blockIdx.y * a.tps + t) * BN;
+    return blockIdx.x * BN;
+  }
+};
+
+template <int KP, bool CROSS>
+__global__ void __launch_bounds__(320, 1)
+umma_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, UmmaArgs a) {
+  extern __shared__ __align__(1024) unsigned char dyn_raw[];
+  unsigned char* dyn = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(dyn_raw) + 1023) & ~uintptr_t(1023));
+  unsigned char* stages = dyn;                                        // NST * STAGE_BYTES
+  float* qv = reinterpret_cast<float*>(dyn + NST * STAGE_BYTES);     // [2][BM][kQCap]
+  int* qi = reinterpret_cast<int*>(qv + 2 * BM * kQCap);
+  __shared__ Bars bars;
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int kb_count = (a.d + BK - 1) / BK;
+
+  Tiles tl;
+  if (a.mode == POOL) tl.count = max(0, min(a.tps, (a.n + BN - 1) / BN - (int)blockIdx.y * a.tps));
+  else if (a.mode == BAND) {
+    const int U = min(*a.count, a.cap);
+    tl.count = (U + BM - 1) / BM;
+  } else tl.count = 1;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < NST; ++s) {
+      mbar_init(&bars.full[s], 1);
+      mbar_init(&bars.empty[s], 1);
+    }
+    const int epi_warps = CROSS ? 8 : 4;
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(&bars.tfull[b], 1);
+      mbar_init(&bars.tempty[b], epi_warps);
+    }
+    mbar_init(&bars.drain, 1);
+    bars.abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&bars.tmem_base)),
+                 "r"(TMEM_COLS));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = bars.tmem_base;
+  volatile int* abort_flag = &bars.abort_flag;
+
+  if (warp == 0) {
+    // ------------------------------------------------------------ TMA producer
+    if (lane == 0) {
+      int it = 0;
+      for (int t = 0; t < tl.count && !*abort_flag; ++t) {
+        const int r0 = tl.row0(a, t), c0 = tl.col0(a, t);
+        for (int kb = 0; kb < kb_count; ++kb, ++it) {
+          const int s = it % NST;
+          const uint32_t round = it / NST;
+          if (!mbar_wait(&bars.empty[s], (round & 1) ^ 1, abort_flag)) break;
+          unsigned char* sa = stages + s * STAGE_BYTES;
+          mbar_arrive_expect_tx(&bars.full[s], STAGE_BYTES);
+          tma_load_2d(sa, &tmA, &bars.full[s], kb * BK, r0);
+          tma_load_2d(sa + A_BYTES, &tmB, &bars.full[s], kb * BK, c0);
+        }
+      }
+      // in-flight loads land before the CTA can exit: wait for the last armed stages
+      if (*abort_flag) {
+        for (int back = 1; back <= NST && back <= it; ++back) {
+          const int j = it - back;
+          const unsigned long long t0 = globaltimer();
+          while (!mbar_try_wait(&bars.full[j % NST], (j / NST) & 1) && globaltimer() - t0 < kTimeoutNs) {
+          }
+        }
+      }
+    }
+  } else if (warp == 1) {
+    // ------------------------------------------------------------ MMA issuer
+    if (lane == 0) {
+      int it = 0;
+      bool ok = true;
+      for (int t = 0; t < tl.count && ok; ++t) {
+        const int buf = t & 1;
+        const uint32_t use = t >> 1;
+        if (!mbar_wait(&bars.tempty[buf], (use & 1) ^ 1, abort_flag)) break;
+        tc_fence_after();
+        const uint32_t dcol = tmem + buf * BN;
+        for (int kb = 0; kb < kb_count; ++kb, ++it) {
+          const int s = it % NST;
+          if (!mbar_wait(&bars.full[s], (it / NST) & 1, abort_flag)) { ok = false; break; }
+          tc_fence_after();
+          const uint32_t sa = smem_u32(stages + s * STAGE_BYTES);
+          const uint64_t ad = smem_desc(sa), bd = smem_desc(sa + A_BYTES);
+#pragma unroll
+          for (int k = 0; k < BK / 16; ++k)  // +32 bytes per K=16 step inside the swizzle row
+            umma_bf16(dcol, ad + (uint64_t)(2 * k), bd + (uint64_t)(2 * k), (kb | k) != 0);
+          umma_commit(&bars.empty[s]);
+        }
+        if (ok) umma_commit(&bars.tfull[buf]);
+      }
+      // all issued MMAs complete before TMEM is released
+      umma_commit(&bars.drain);
+      const unsigned long long t0 = globaltimer();
+      while (!mbar_try_wait(&bars.drain, 0) && globaltimer() - t0 < kTimeoutNs) {
+      }
+    }
+  } else {
+    // ------------------------------------------------------------ epilogue warps
+    const int ew = warp - 2;                 // 0..7
+    const int kind = ew >> 2;                // 0: global graph, 1: cross-camera graph
+    const int quad = warp & 3;               // TMEM lanes 32*quad .. 32*quad+31
+    const int r = quad * 32 + lane;          // row of the accumulator owned by this thread
+    const uint32_t lane_addr = (uint32_t)(quad * 32) << 16;
+    PoolOwner me;
+    int my_row = -1, my_cam = 0;
+    float my_thr = 0.f, my_nq = 0.f;
+    int my_kind = 0;
+    const int qrow = kind * BM + r;
+    const int sw = qrow & 31;
+    const size_t pbase = ((size_t)blockIdx.y * (CROSS ? 2 : 1) + kind) * a.a_rows * KP;
+    float* pv = a.pool_v ? a.pool_v + pbase : nullptr;
+    int* pi = a.pool_i ? a.pool_i + pbase : nullptr;
+    if (a.mode == POOL) {
+      my_row = blockIdx.x * BM + r;
+      const bool valid = my_row < a.a_rows;
+      pool_init(me, valid);
+      if (CROSS && valid) my_cam = a.cam[my_row];
+    }
+    for (int t = 0; t < tl.count; ++t) {
+      const int buf = t & 1;
+      const uint32_t use = t >> 1;
+      if (!mbar_wait(&bars.tfull[buf], use & 1, abort_flag)) break;
+      tc_fence_after();
+      const int r0 = tl.row0(a, t), c0 = tl.col0(a, t);
+      int u = -1;
+      if (a.mode == BAND) {
+        u = r0 + r;
+        const int U = min(*a.count, a.cap);
+        if (u < U) {
+          my_row = a.band_row[u];
+          my_kind = a.band_kind[u];
+          my_thr = a.band_thr[u];
+          if (a.cam) my_cam = a.cam[my_row];
+        } else {
+          u = -1;
+        }
+      } else if (a.mode == DIST) {
+        my_row = r0 + r;
+        my_nq = my_row < a.a_rows ? a.nrm_q[my_row] : 0.f;
+      }
+      const int ncol = min(BN, a.n - c0);
+      for (int ch = 0; ch < BN / 32; ++ch) {
+        if (ch * 32 >= ncol) break;
+        float v[32];
+        tmem_ld32(tmem + lane_addr + buf * BN + ch * 32, v);
+        const int cb = c0 + ch * 32;
+        if (a.mode == POOL) {
+          if (kind == 0 || CROSS) {
+            int ccam = 0;
+            if (CROSS && kind == 1) ccam = (cb + lane < a.n) ? a.cam[cb + lane] : -1;
+#pragma unroll
+            for (int g = 0; g < 4; ++g) {
+              pool_make_room<KP>(8, lane, me, blockIdx.x * BM + quad * 32, kind * BM + quad * 32, qv, qi, pv, pi);
+#pragma unroll
+              for (int c = 0; c < 8; ++c) {
+                const int cc = g * 8 + c;
+                const int j = cb + cc;
+                // the shuffle runs on every lane (a full-mask shuffle must not sit behind a branch)
+                const int cj = __shfl_sync(GCR_FULL, ccam, cc);
+                bool ok = j < a.n && !(a.self_excl && j == my_row);
+                if (CROSS && kind == 1) ok = ok && cj != my_cam;
+                pool_push(me, v[cc], j, ok, qv + qrow * kQCap, qi + qrow * kQCap, sw);
+              }
+            }
+          }
+        } else if (a.mode == BAND) {
+          if (kind == 0) {
+            int ccam = 0;
+            if (a.cam) ccam = (cb + lane < a.n) ? a.cam[cb + lane] : -1;
+#pragma unroll
+            for (int cc = 0; cc < 32; ++cc) {
+              const int j = cb + cc;
+              const int cjv = __shfl_sync(GCR_FULL, ccam, cc);
+              const int cj = a.cam ? cjv : 0;
+              if (u < 0 || j >= a.n || (a.self_excl && j == my_row) || v[cc] < my_thr) continue;
+              if (my_kind == 1 && cj == my_cam) continue;
+              const int pos = atomicAdd(&a.band_cnt[u], 1);
+              if (pos < a.bcap) {
+                a.band_v[(size_t)u * a.bcap + pos] = v[cc];
+                a.band_i[(size_t)u * a.bcap + pos] = j;
+              }
+            }
+          }
+        } else {
+          if (kind == 0) {
+            const float ngv = (cb + lane < a.n) ? a.nrm_g[cb + lane] : 0.f;
+            const bool row_ok = my_row < a.a_rows;
+            float* out = a.D + (size_t)(row_ok ? my_row : 0) * a.n + cb;
+#pragma unroll
+            for (int cc = 0; cc < 32; ++cc) {
+              const float g = __shfl_sync(GCR_FULL, ngv, cc);
+              if (row_ok && cb + cc < a.n) out[cc] = my_nq + g - 2.f * v[cc];
+            }
+          }
+        }
+      }
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&bars.tempty[buf]);
+    }
+    if (a.mode == POOL && (kind == 0 || CROSS) && !*abort_flag)
+      pool_flush<KP>(lane, my_row < a.a_rows, me, blockIdx.x * BM + quad * 32, kind * BM + quad * 32, qv, qi, pv, pi);
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 1) {
+    __syncwarp();
+    tc_fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS));
+  }
+}
+
+// Self-test of the bounded wait: one warp waits on an mbarrier that nothing signals; the wait
+// gives up after limit_ns, counts a timeout (reported by gcr_sync) and the kernel returns.
+__global__ void wait_probe_kernel(unsigned long long limit_ns, int* result) {
+  __shared__ uint64_t bar;
+  __shared__ int abort_flag;
+  if (threadIdx.x == 0) {
+    mbar_init(&bar, 1);
+    abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
+  bool ok = true;
+  if (threadIdx.x == 0) ok = mbar_wait(&bar, 0, &abort_flag, limit_ns);
+  __syncthreads();
+  if (threadIdx.x == 0 && result) *result = ok ? 1 : 0;
+}
+
+// ------------------------------------------------------------------------ host side
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                  const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeTiledFn encode_fn() {
+  static EncodeTiledFn fn = nullptr;
+  if (!fn) {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+        q != cudaDriverEntryPointSuccess)
+      return nullptr;
+    fn = reinterpret_cast<EncodeTiledFn>(p);
+  }
+  return fn;
+}
+
+// Row-major BF16 matrix [rows][d] viewed as a 2-D tensor, box = 64 (K) x box_rows.
+cudaError_t make_map(CUtensorMap* m, const __nv_bfloat16* base, int rows, int d, int box_rows) {
+  EncodeTiledFn fn = encode_fn();
+  if (!fn) return cudaErrorNotSupported;
+  if ((reinterpret_cast<uintptr_t>(base) & 15) || (d % 8)) return cudaErrorInvalidValue;
+  cuuint64_t dims[2] = {(cuuint64_t)d, (cuuint64_t)rows};
+  cuuint64_t strides[1] = {(cuuint64_t)d * 2};
+  cuuint32_t box[2] = {(cuuint32_t)BK, (cuuint32_t)box_rows};
+  cuuint32_t estr[2] = {1, 1};
+  CUresult r = fn(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<__nv_bfloat16*>(base), dims, strides, box, estr,
+                  CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                  CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
+}
+
+size_t smem_bytes(int mode) {
+  size_t s = 1024 + (size_t)NST * STAGE_BYTES;
+  if (mode == POOL) s += 2 * BM * kQCap * (sizeof(float) + sizeof(int));
+  return s;
+}
+
+template <int KP, bool CROSS>
+cudaError_t launch(const CUtensorMap& ta, const CUtensorMap& tb, const UmmaArgs& a, dim3 grid, cudaStream_t st) {
+  auto fn = umma_kernel<KP, CROSS>;
+  const size_t smem = smem_bytes(a.mode);
+  cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  fn<<<grid, CROSS ? 320 : 192, smem, st>>>(ta, tb, a);
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t launch_wait_probe(unsigned long long limit_ns, cudaStream_t st) {
+  wait_probe_kernel<<<1, 32, 0, st>>>(limit_ns, nullptr);
+  return cudaGetLastError();
+}
+
+int umma_read_and_clear_timeouts() {
+  int h = 0, z = 0;
+  if (cudaMemcpyFromSymbol(&h, g_umma_timeouts, sizeof(int)) != cudaSuccess) return -1;
+  if (h) cudaMemcpyToSymbol(g_umma_timeouts, &z, sizeof(int));
+  return h;
+}
+
+cudaError_t launch_umma_pool(const __nv_bfloat16* Ab, int na, const __nv_bfloat16* Bb, int nb, int d,
+                             const int* cam, bool cross, int self_excl, int kp, int splits, float* pool_v,
+                             int* pool_i, cudaStream_t st) {
+  CUtensorMap ta, tb;
+  cudaError_t e = make_map(&ta, Ab, na, d, BM);
+  if (e != cudaSuccess) return e;
+  e = make_map(&tb, Bb, nb, d, BN);
+  if (e != cudaSuccess) return e;
+  const int ntiles = (nb + BN - 1) / BN;
+  if (splits < 1) splits = 1;
+  if (splits > ntiles) splits = ntiles;
+  const int tps = (ntiles + splits - 1) / splits;
+  splits = (ntiles + tps - 1) / tps;  // no split is left without a column tile
+  UmmaArgs a{};
+  a.mode = POOL;
+  a.n = nb;
+  a.d = d;
+  a.a_rows = na;
+  a.self_excl = self_excl;
+  a.tps = tps;
+  a.cam = cam;
+  a.pool_v = pool_v;
+  a.pool_i = pool_i;
+  dim3 grid((na + BM - 1) / BM, splits);
+  if (kp == 64) return cross ? launch<64, true>(ta, tb, a, grid, st) : launch<64, false>(ta, tb, a, grid, st);
+  if (kp == 128) return cross ? launch<128, true>(ta, tb, a, grid, st) : launch<128, false>(ta, tb, a, grid, st);
+  return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_umma_band(const __nv_bfloat16* Xb, int n, int d, const int* cam, int self_excl,
+                             const __nv_bfloat16* Ab, const int* count, int cap, const int* band_row,
+                             const int* band_kind, const float* band_thr, int bcap, int* band_cnt, float* band_v,
+                             int* band_i, cudaStream_t st) {
+  CUtensorMap ta, tb;
+  cudaError_t e = make_map(&ta, Ab, cap, d, BM);
+  if (e != cudaSuccess) return e;
+  e = make_map(&tb, Xb, n, d, BN);
+  if (e != cudaSuccess) return e;
+  UmmaArgs a{};
+  a.mode = BAND;
+  a.n = n;
+  a.d = d;
+  a.a_rows = cap;
+  a.self_excl = self_excl;
+  a.cam = cam;
+  a.count = count;
+  a.cap = cap;
+  a.band_row = band_row;
+  a.band_kind = band_kind;
+  a.band_thr = band_thr;
+  a.bcap = bcap;
+  a.band_cnt = band_cnt;
+  a.band_v = band_v;
+  a.band_i = band_i;
+  dim3 grid((n + BN - 1) / BN);
+  return launch<64, false>(ta, tb, a, grid, st);
+}
+
+cudaError_t launch_umma_dist(const __nv_bfloat16* Qb, int nq, const __nv_bfloat16* Gb, int ng, int d,
+                             const float* nrm_q, const float* nrm_g, float* D, cudaStream_t st) {
+  CUtensorMap ta, tb;
+  cudaError_t e = make_map(&ta, Qb, nq, d, BM);
+  if (e != cudaSuccess) return e;
+  e = make_map(&tb, Gb, ng, d, BN);
+  if (e != cudaSuccess) return e;
+  UmmaArgs a{};
+  a.mode = DIST;
+  a.n = ng;
+  a.d = d;
+  a.a_rows = nq;
+  a.nrm_q = nrm_q;
+  a.nrm_g = nrm_g;
+  a.D = D;
+  dim3 grid((ng + BN - 1) / BN, (nq + BM - 1) / BM);
+  return launch<64, false>(ta, tb, a, grid, st);
+}
+
+}  // namespace gcr

@@ -81,7 +81,7 @@ def test_workspace_queries(lib):
 
 
 @pytest.mark.parametrize("bad", [dict(k=-1), dict(k=32), dict(gamma=0.0), dict(gamma=-1.0),
-                                 dict(cross_camera=1, alpha=1.5), dict(precision=7), dict(pool=48),
+                                 dict(cross_camera=1, alpha=1.5), dict(precision=7), dict(pool=48), dict(pool=256),
                                  dict(symmetric=2)])
 def test_invalid_params_rejected_on_host(lib, bad):
     p = _params(lib, **bad)
@@ -131,3 +131,29 @@ def test_product_package_does_not_import_oracle():
     out = subprocess.run([sys.executable, "-c", code], cwd=ROOT, capture_output=True, text=True)
     assert out.returncode == 0, out.stderr
     assert out.stdout.strip() == "False"
+
+
+def test_gcrv_validation_on_host(lib):
+    assert lib.gcrv_profiles_workspace_size(1000, 128, 50, 6) > 0
+    assert lib.gcrv_profiles_workspace_size(1000, 128, 50, 65) == 0      # at most 64 cameras
+    assert lib.gcrv_profiles_workspace_size(1000, 130, 50, 6) == 0       # d % 4
+    p = ctypes.c_void_p(16)
+    assert lib.gcrv_profiles(p, 1000, 128, p, p, 50, 6, ctypes.c_float(0.0), p, p, 1 << 30, None) == 1
+    assert lib.gcrv_profiles(p, 1000, 130, p, p, 50, 6, ctypes.c_float(10.0), p, p, 1 << 30, None) == 5
+    assert lib.gcrv_profiles(p, 1000, 128, p, p, 50, 6, ctypes.c_float(10.0), p, p, 100, None) == 2
+    assert lib.gcrv_profiles(None, 1000, 128, p, p, 50, 6, ctypes.c_float(10.0), p, p, 1 << 30, None) == 1
+
+
+def test_serving_validation_on_host(lib):
+    p = _params(lib, k=20, T=2, topk_out=100)
+    assert lib.gcr_gallery_bytes(500000, 256, ctypes.byref(p)) > 3 * 500000 * 256 * 4
+    assert lib.gcr_serve_workspace_size(512, 500000, 256, ctypes.byref(p)) > 0
+    assert lib.gcr_serve_workspace_size(0, 500000, 256, ctypes.byref(p)) == 0
+    for bad in (dict(topk_out=0), dict(topk_out=128), dict(cross_camera=1), dict(T=-1)):
+        kw = dict(k=20, T=2, topk_out=100)
+        kw.update(bad)
+        q = _params(lib, **kw)
+        assert lib.gcr_gallery_bytes(500000, 256, ctypes.byref(q)) == 0, bad
+    v = ctypes.c_void_p(16)
+    assert lib.gcr_serve(v, 1 << 40, 500000, v, 8, 256, ctypes.byref(p), v, v, None, None, 0, None) == 2
+    assert lib.gcr_serve(None, 1 << 40, 500000, v, 8, 256, ctypes.byref(p), v, v, None, v, 1 << 40, None) == 1
