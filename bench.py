@@ -34,6 +34,7 @@ WORKLOAD = ("crosscam: 3,368 queries + 15,913 gallery (Market-1501 shape), d=204
             "symmetric operator, global + cross-camera graphs, full gallery ranking per query")
 L2_FLUSH_BYTES = 256 << 20
 FP32_LANES_PER_SM = 128
+TF32_PER_BF16 = 1.1 / 2.25   # nominal dense tensor rates of the GB300 (PFLOP/s)
 N_SMS = 152
 
 
@@ -43,7 +44,7 @@ def _args():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--precision", choices=["auto", "bf16", "fp32"], default="auto")
+    ap.add_argument("--precision", choices=["auto", "tf32", "bf16", "fp32"], default="auto")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-serving", action="store_true")
     ap.add_argument("--serving-requests", type=int, default=800)
@@ -361,21 +362,22 @@ def run_ours(a):
     cam = camh.cuda()
 
     from paper_2306_08792_gb300 import _lib
-    prec_order = ["bf16", "fp32"] if a.precision == "auto" else [a.precision]
+    prec_order = ["tf32", "bf16", "fp32"] if a.precision == "auto" else [a.precision]
     results = {}
     sampler = ClockSampler(local)
     sampler.mark_start()
     for prec in prec_order:
         try:
             results[prec] = time_path(gcr, torch, w, X, cam, prec, a.steps, a.warmup, dist,
-                                      a.pool if prec == "bf16" else 0)
+                                      a.pool if prec != "fp32" else 0)
         except gcr.GcrError as e:
             if a.precision != "auto":
                 raise
             results[prec] = {"error": str(e)}
     sampler.mark_end()
     clocks = sampler.result()
-    primary = next(p for p in prec_order if "ms" in results[p])
+    # the headline is the fastest mode; every mode returns the same certified neighbour sets
+    primary = min((p for p in prec_order if "ms" in results[p]), key=lambda p: results[p]["ms"])
     R = results[primary]
     ms = max_over_ranks(R["ms"], dist, "cuda")
     value = job_throughput(world, w.n_query, ms)
@@ -397,8 +399,16 @@ def run_ours(a):
         peak = peaks["bf16_tflops"]
         roof = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                 "frac": achieved / peak, "peak_source": f"bf16_tflops (burst) of {psrc}",
-                "kernel": "umma_pool_kernel (similarity GEMM + streaming top-k)",
+                "kernel": "umma_kernel POOL, BF16 (similarity GEMM + streaming top-k)",
                 "traffic": _traffic("umma_pool", ["umma.cu", "pool.cuh"])}
+    elif primary == "tf32":
+        # TF32 dense peak: the measured BF16 peak x the nominal TF32/BF16 ratio (1.1 / 2.25 PFLOP/s)
+        peak = peaks["bf16_tflops"] * TF32_PER_BF16
+        roof = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                "frac": achieved / peak,
+                "peak_source": f"bf16_tflops (burst) of {psrc} x {TF32_PER_BF16:.4f} (nominal tf32/bf16)",
+                "kernel": "umma_kernel POOL, TF32 (similarity GEMM + streaming top-k)",
+                "traffic": _traffic("umma_pool_tf32", ["umma.cu", "pool.cuh"])}
     else:
         peak = N_SMS * FP32_LANES_PER_SM * 2 * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
         roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
@@ -411,7 +421,7 @@ def run_ours(a):
 
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": a.steps,
             "warmup": a.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": primary if primary == "bf16" else "f32", "data": "synthetic",
+            "vs_baseline": None, "dtype": "f32" if primary == "fp32" else primary, "data": "synthetic",
             "config": {"workload": WORKLOAD, "precision": primary,
                        "l2": "flushed between steps (256 MB write outside the timed events); X is 158 MB > L2",
                        "parallelism": "replicas" if world > 1 else "single GPU"},

@@ -48,8 +48,13 @@ typedef enum {
 
 typedef enum {
   GCR_PREC_FP32 = 0, /* similarity GEMM on CUDA cores in FP32 (the reference path) */
-  GCR_PREC_BF16 = 1  /* similarity GEMM on tcgen05 tensor cores, BF16 x BF16 -> FP32,
+  GCR_PREC_BF16 = 1, /* similarity GEMM on tcgen05 tensor cores, BF16 x BF16 -> FP32,
                         then boundary candidates re-scored in FP32 (FP64 for ties) */
+  GCR_PREC_TF32 = 2  /* as BF16 with the rows rounded to TF32 (kind::tf32): a rounding
+                        bound 8x tighter, so fewer candidates need the FP32 re-score.
+                        Both tensor-core modes need d % 8 == 0 (BF16 also pool >= 64);
+                        their certified re-score returns the neighbour sets of the exact
+                        search */
 } gcr_precision;
 
 /* Hyper-parameters of one GCR run. gcr_default_params() fills the paper's defaults:
@@ -64,7 +69,8 @@ typedef struct {
   int32_t cross_camera; /* 1: add the cross-camera graph (Eq. 8) and mix by Eq. 9         */
   int32_t precision;    /* gcr_precision                                                  */
   int32_t pool;         /* per-row candidate pool of the streaming kNN search: 32, 64 or
-                           128; 0 picks 32 for FP32 and 64 for BF16 (BF16 needs >= 64);
+                           128; 0 picks 32 for FP32 and 64 for BF16 and TF32 (BF16
+                           needs >= 64);
                            must exceed k. A larger pool certifies more rows without the
                            threshold rescan at the cost of a busier GEMM epilogue.        */
   int32_t topk_out;     /* gcr_rerank: results per query; 0 = the whole gallery           */
@@ -108,6 +114,10 @@ typedef struct {
   int32_t* op_col;    /* [op_capacity]                                              */
   float*   op_val;    /* [op_capacity]                                              */
   int64_t* stats;     /* [GCR_STATS_LEN] device counters (may be NULL)              */
+  int32_t* row_order; /* [n] optional (may be NULL): filled by gcr_build_graph with a
+                         cluster-local order of the rows (rows sharing their nearest
+                         candidates end up adjacent), used by gcr_propagate to walk the
+                         rows in that order. Results do not depend on it.             */
 } gcr_graph;
 
 /* ------------------------------------------------------------------ utilities */
@@ -145,7 +155,8 @@ int gcr_normalize(const float* X_in, float* X_out, int64_t n, int32_t d, gcr_str
  * exact FP64 ties go to the smaller index.
  * cam: device int32[n], required when cross_camera = 1, else may be NULL.
  * Errors: GCR_E_INVALID (n < 1, k out of range, gamma <= 0, alpha outside [0,1],
- * pool <= k, missing arrays), GCR_E_UNSUPPORTED (d % 4, or d % 8 with BF16),
+ * pool <= k, missing arrays), GCR_E_UNSUPPORTED (d % 4, d % 8 with BF16 or TF32,
+ * pool 32 with BF16),
  * GCR_E_WORKSPACE. */
 size_t gcr_graph_op_capacity(int64_t n, const gcr_params* p);
 size_t gcr_build_graph_workspace_size(int64_t n, int32_t d, const gcr_params* p);

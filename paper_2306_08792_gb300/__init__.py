@@ -6,4 +6,4 @@ this package is its thin Python binding.
 from .api import (GcrError, GraphTensors, Pipeline, alloc_graph, default_params, device_supported,  # noqa: F401
                   gcr_build_graph, gcr_normalize, gcr_pipeline, gcr_propagate, gcr_rerank, gcr_rerank_noalloc,
                   gcr_sync, gcrv_profiles)
-from ._lib import GCR_PREC_BF16, GCR_PREC_FP32, STAT_NAMES  # noqa: F401
+from ._lib import GCR_PREC_BF16, GCR_PREC_FP32, GCR_PREC_TF32, STAT_NAMES  # noqa: F401

@@ -10,7 +10,7 @@ PKG = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(PKG, "libgcr.so")
 
 GCR_OK, GCR_E_INVALID, GCR_E_WORKSPACE, GCR_E_CUDA, GCR_E_TIMEOUT, GCR_E_UNSUPPORTED = range(6)
-GCR_PREC_FP32, GCR_PREC_BF16 = 0, 1
+GCR_PREC_FP32, GCR_PREC_BF16, GCR_PREC_TF32 = 0, 1, 2
 STAGE_NAMES = ["normalize", "prep", "sim_gemm", "refine", "band", "graph", "propagate", "dist_gemm", "sort",
                "gcrv"]
 GCR_STAGES = 12
@@ -28,7 +28,7 @@ class Graph(ctypes.Structure):
     _fields_ = [("nbr", c_void_p), ("nbr_d2", c_void_p), ("nbr_cr", c_void_p), ("nbr_cr_d2", c_void_p),
                 ("deg_r", c_void_p), ("deg_c", c_void_p), ("deg_r_cr", c_void_p), ("deg_c_cr", c_void_p),
                 ("op_rowptr", c_void_p), ("op_len", c_void_p), ("op_col", c_void_p), ("op_val", c_void_p),
-                ("stats", c_void_p)]
+                ("stats", c_void_p), ("row_order", c_void_p)]
 
 
 # name -> (restype, argtypes)

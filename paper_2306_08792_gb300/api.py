@@ -14,7 +14,7 @@ from typing import Optional
 import torch
 
 from . import _lib
-from ._lib import GCR_PREC_BF16, GCR_PREC_FP32, Graph, Params
+from ._lib import GCR_PREC_BF16, GCR_PREC_FP32, GCR_PREC_TF32, Graph, Params
 
 
 class GcrError(RuntimeError):
@@ -50,7 +50,7 @@ def default_params(**kw) -> Params:
     _lib.load().gcr_default_params(ctypes.byref(p))
     for k, v in kw.items():
         if k == "precision" and isinstance(v, str):
-            v = {"fp32": GCR_PREC_FP32, "bf16": GCR_PREC_BF16}[v]
+            v = {"fp32": GCR_PREC_FP32, "bf16": GCR_PREC_BF16, "tf32": GCR_PREC_TF32}[v]
         setattr(p, k, v)
     return p
 
@@ -78,6 +78,7 @@ class GraphTensors:
     op_col: torch.Tensor
     op_val: torch.Tensor
     stats: torch.Tensor
+    row_order: Optional[torch.Tensor] = None
 
     def struct(self) -> Graph:
         g = Graph()
@@ -104,7 +105,8 @@ def alloc_graph(n: int, p: Params, device) -> GraphTensors:
         deg_r_cr=e(n, dt=f32) if cross else None, deg_c_cr=e(n, dt=f32) if cross else None,
         op_rowptr=e(n + 1, dt=i32), op_len=e(n, dt=i32), op_col=e(max(cap, 1), dt=i32),
         op_val=e(max(cap, 1), dt=f32),
-        stats=torch.zeros(_lib.GCR_STATS_LEN, dtype=torch.int64, device=device))
+        stats=torch.zeros(_lib.GCR_STATS_LEN, dtype=torch.int64, device=device),
+        row_order=e(n, dt=i32))
 
 
 def gcr_build_graph(X: torch.Tensor, p: Params, cam: Optional[torch.Tensor] = None,

@@ -50,19 +50,33 @@ struct Resolved {
   int kinds;
 };
 
+// The tensor-core modes (BF16, TF32) search on rounded operand copies; FP32 runs on the CUDA cores.
+bool tensor_mode(const gcr_params* p) { return p->precision != GCR_PREC_FP32; }
+Elt elt_of(const gcr_params* p) { return p->precision == GCR_PREC_TF32 ? Elt::TF32 : Elt::BF16; }
+size_t elt_size(const gcr_params* p) { return elt_bytes(elt_of(p)); }
+
+int check_precision(const gcr_params* p, int32_t d) {
+  if (p->precision != GCR_PREC_FP32 && p->precision != GCR_PREC_BF16 && p->precision != GCR_PREC_TF32)
+    return GCR_E_INVALID;
+  // BF16 rows (and the compensated BF16 distance operands of both modes) need 16-byte rows
+  if (tensor_mode(p) && d % 8 != 0) return GCR_E_UNSUPPORTED;
+  return GCR_OK;
+}
+
 int check_params(const gcr_params* p, int64_t n, int32_t d, Resolved* r) {
   if (!p || n < 1 || n > (1 << 24)) return GCR_E_INVALID;
   if (d < 4 || d > kMaxD) return GCR_E_INVALID;
   if (d % 4 != 0) return GCR_E_UNSUPPORTED;
-  if (p->precision != GCR_PREC_FP32 && p->precision != GCR_PREC_BF16) return GCR_E_INVALID;
-  if (p->precision == GCR_PREC_BF16 && d % 8 != 0) return GCR_E_UNSUPPORTED;
+  const int pc = check_precision(p, d);
+  if (pc != GCR_OK) return pc;
   if (!(p->gamma > 0.f) || !std::isfinite(p->gamma)) return GCR_E_INVALID;
   if (p->symmetric != 0 && p->symmetric != 1) return GCR_E_INVALID;
   if (p->cross_camera != 0 && p->cross_camera != 1) return GCR_E_INVALID;
   if (p->cross_camera && !(p->alpha >= 0.f && p->alpha <= 1.f)) return GCR_E_INVALID;
-  int kp = p->pool ? p->pool : (p->precision == GCR_PREC_BF16 ? 64 : 32);
+  int kp = p->pool ? p->pool : (tensor_mode(p) ? 64 : 32);
   if (kp != 32 && kp != 64 && kp != 128) return GCR_E_INVALID;
   if (p->k < 0 || p->k >= kp) return GCR_E_INVALID;
+  // the BF16 rounding bound is too loose for a 32-entry pool to certify most rows
   if (p->precision == GCR_PREC_BF16 && kp == 32) return GCR_E_UNSUPPORTED;
   r->kp = kp;
   r->kinds = p->cross_camera ? 2 : 1;
@@ -78,7 +92,7 @@ struct BuildWs {
   double* n64;
   float* n32;
   RowScalars* sc;
-  __nv_bfloat16* xb;
+  void* xr;            // rounded operand copy (tensor-core modes)
   float* enrm;
   float* anrm;
   float* pool_v;
@@ -90,7 +104,7 @@ struct BuildWs {
   int* band_cnt;
   float* band_v;
   int* band_i;
-  __nv_bfloat16* band_a;
+  void* band_a;        // gathered rounded rows of the band rescan
   float* w;
   int* cnt;
   int* fill;
@@ -102,20 +116,26 @@ struct BuildWs {
   int* scan_tmp;
   unsigned long long* stats;
   int* err;
+  int* okey;
+  int* ocnt;
+  int* ooff;
+  int* ofill;
+  int* order;
   int band_rows;
 };
 
 size_t carve_build(Carve& c, int64_t n, int32_t d, const gcr_params* p, const Resolved& r, BuildWs* w) {
   const size_t nn = (size_t)n;
   const int kinds = r.kinds;
-  const bool bf = p->precision == GCR_PREC_BF16;
+  const bool bf = tensor_mode(p);
+  const size_t es = elt_size(p);
   const int band_rows = (int)std::min<int64_t>((int64_t)kinds * n, kBandRowsMax);
   const size_t cap = op_capacity(n, p, kinds);
   BuildWs t;
   t.n64 = c.take<double>(nn);
   t.n32 = c.take<float>(nn);
   t.sc = c.take<RowScalars>(1);
-  t.xb = bf ? c.take<__nv_bfloat16>(nn * d) : nullptr;
+  t.xr = bf ? c.take<char>(nn * d * es) : nullptr;
   t.enrm = bf ? c.take<float>(nn) : nullptr;
   t.anrm = bf ? c.take<float>(nn) : nullptr;
   t.pool_v = c.take<float>((size_t)kinds * nn * r.kp);
@@ -127,7 +147,7 @@ size_t carve_build(Carve& c, int64_t n, int32_t d, const gcr_params* p, const Re
   t.band_cnt = c.take<int>(band_rows);
   t.band_v = c.take<float>((size_t)band_rows * kBandCap);
   t.band_i = c.take<int>((size_t)band_rows * kBandCap);
-  t.band_a = bf ? c.take<__nv_bfloat16>((size_t)band_rows * d) : nullptr;
+  t.band_a = bf ? c.take<char>((size_t)band_rows * d * es) : nullptr;
   t.w = c.take<float>((size_t)kinds * nn * p->k);
   t.cnt = c.take<int>((size_t)kinds * (nn + 1));
   t.fill = c.take<int>((size_t)kinds * nn);
@@ -139,6 +159,11 @@ size_t carve_build(Carve& c, int64_t n, int32_t d, const gcr_params* p, const Re
   t.scan_tmp = c.take<int>(nn + 1);
   t.stats = c.take<unsigned long long>(GCR_STATS_LEN);
   t.err = c.take<int>(4);
+  t.okey = c.take<int>(nn);
+  t.ocnt = c.take<int>(nn + 1);
+  t.ooff = c.take<int>(nn + 1);
+  t.ofill = c.take<int>(nn);
+  t.order = c.take<int>(nn);
   t.band_rows = band_rows;
   if (w) *w = t;
   return c.off;
@@ -148,13 +173,14 @@ int build_graph_impl(const float* X, int64_t n64_, int32_t d, const int32_t* cam
                      const Resolved& r, gcr_graph* g, const BuildWs& w, cudaStream_t st) {
   const int n = (int)n64_;
   const int kinds = r.kinds;
-  const bool bf = p->precision == GCR_PREC_BF16;
+  const bool bf = tensor_mode(p);
+  const Elt elt = elt_of(p);
   unsigned long long* stats = g->stats ? reinterpret_cast<unsigned long long*>(g->stats) : w.stats;
   if (!g->stats) GCR_CUDA_TRY(cudaMemsetAsync(w.stats, 0, sizeof(unsigned long long) * GCR_STATS_LEN, st));
 
   {
     StageScope sc_(GCR_STAGE_PREP, st, 2);
-    GCR_CUDA_TRY(launch_row_stats(X, n, d, w.n64, w.n32, bf ? w.xb : nullptr, w.enrm, w.anrm, w.sc, st));
+    GCR_CUDA_TRY(launch_row_stats(X, n, d, w.n64, w.n32, bf ? w.xr : nullptr, elt, w.enrm, w.anrm, w.sc, st));
   }
   GCR_CUDA_TRY(cudaMemsetAsync(w.unc_count, 0, sizeof(int) * 4, st));
   GCR_CUDA_TRY(cudaMemsetAsync(w.band_cnt, 0, sizeof(int) * w.band_rows, st));
@@ -164,8 +190,8 @@ int build_graph_impl(const float* X, int64_t n64_, int32_t d, const int32_t* cam
   if (p->k > 0) {
     StageScope sc_(GCR_STAGE_SIM_GEMM, st);
     if (bf) {
-      GCR_CUDA_TRY(launch_umma_pool(w.xb, n, w.xb, n, d, camp, p->cross_camera != 0, 1, r.kp, 1, w.pool_v, w.pool_i,
-                                    st));
+      GCR_CUDA_TRY(launch_umma_pool(w.xr, n, w.xr, n, d, elt, camp, p->cross_camera != 0, 1, r.kp, 1, w.pool_v,
+                                    w.pool_i, st));
     } else {
       GCR_CUDA_TRY(launch_sgemm_pool(X, n, X, n, d, camp, r.kp, p->cross_camera != 0, 1, 1, w.pool_v, w.pool_i, st));
     }
@@ -183,16 +209,24 @@ int build_graph_impl(const float* X, int64_t n64_, int32_t d, const int32_t* cam
   ra.stats = stats;
   ra.band_cnt = w.band_cnt; ra.band_v = w.band_v; ra.band_i = w.band_i; ra.bcap = kBandCap;
   ra.band_rows = w.band_rows;
+  // cluster-local processing order for the refinement and the propagation of this graph; it
+  // is always written when the caller provides row_order (the identity when k = 0)
+  int* order = g->row_order ? g->row_order : w.order;
+  if (p->k == 0 && g->row_order)
+    GCR_CUDA_TRY(launch_row_order(w.pool_i, n, r.kp, 0, w.okey, w.ocnt, w.ooff, w.ofill, order, st));
   if (p->k > 0) {
     {
-      StageScope sc_(GCR_STAGE_REFINE, st);
+      StageScope sc_(GCR_STAGE_REFINE, st, 5);
+      GCR_CUDA_TRY(launch_row_order(w.pool_i, n, r.kp, p->k, w.okey, w.ocnt, w.ooff, w.ofill, order, st));
+      ra.order = order;
       GCR_CUDA_TRY(launch_refine_pool(ra, st));
     }
     // threshold rescan of the rows whose pool could not certify the k-th neighbour
     StageScope sc_(GCR_STAGE_BAND, st, bf ? 3 : 2);
     if (bf) {
-      GCR_CUDA_TRY(launch_gather_bf16(w.xb, d, w.unc_count, w.unc_row, w.band_rows, w.band_a, st));
-      GCR_CUDA_TRY(launch_umma_band(w.xb, n, d, camp, 1, w.band_a, w.unc_count, w.band_rows, w.unc_row,
+      GCR_CUDA_TRY(launch_gather_rows(w.xr, (size_t)d * elt_bytes(elt), w.unc_count, w.unc_row, w.band_rows,
+                                      w.band_a, st));
+      GCR_CUDA_TRY(launch_umma_band(w.xr, n, d, elt, camp, 1, w.band_a, w.unc_count, w.band_rows, w.unc_row,
                                     w.unc_kind, w.unc_thr, kBandCap, w.band_cnt, w.band_v, w.band_i, st));
     } else {
       GCR_CUDA_TRY(launch_sgemm_band(X, X, n, d, camp, 1, w.unc_count, w.band_rows, w.unc_row, w.unc_kind,
@@ -271,13 +305,15 @@ size_t carve_rerank(Carve& c, int64_t nq, int64_t ng, int32_t d, bool bf, Rerank
 
 int rerank_impl(const float* Xq, int64_t nq, const float* Xg, int64_t ng, int32_t d, const gcr_params* p,
                 int32_t* idx_out, float* dist_out, const RerankWs& w, cudaStream_t st) {
-  const bool bf = p->precision == GCR_PREC_BF16;
+  // the distance GEMM of both tensor-core modes runs on compensated BF16 operands
+  const bool bf = tensor_mode(p);
   const int K = p->topk_out > 0 ? (int)std::min<int64_t>(p->topk_out, ng) : (int)ng;
   const size_t mx = (size_t)std::max(nq, ng);
   {
     StageScope sc_(GCR_STAGE_PREP, st, bf ? 6 : 4);
-    GCR_CUDA_TRY(launch_row_stats(Xq, (int)nq, d, w.n64q, w.nq, nullptr, w.dummy, w.dummy + mx, w.sc, st));
-    GCR_CUDA_TRY(launch_row_stats(Xg, (int)ng, d, w.n64g, w.ng, nullptr, w.dummy, w.dummy + mx, w.sc + 1, st));
+    GCR_CUDA_TRY(launch_row_stats(Xq, (int)nq, d, w.n64q, w.nq, nullptr, Elt::BF16, w.dummy, w.dummy + mx, w.sc, st));
+    GCR_CUDA_TRY(
+        launch_row_stats(Xg, (int)ng, d, w.n64g, w.ng, nullptr, Elt::BF16, w.dummy, w.dummy + mx, w.sc + 1, st));
     if (bf) {
       GCR_CUDA_TRY(launch_split3(Xq, (int)nq, d, 0, w.qb, st));
       GCR_CUDA_TRY(launch_split3(Xg, (int)ng, d, 1, w.gb, st));
@@ -303,8 +339,8 @@ int check_rerank(int64_t nq, int64_t ng, int32_t d, const gcr_params* p) {
   if (!p || nq < 1 || ng < 1 || ng > (1 << 24) || nq > (1 << 24)) return GCR_E_INVALID;
   if (d < 4 || d > kMaxD) return GCR_E_INVALID;
   if (d % 4 != 0) return GCR_E_UNSUPPORTED;
-  if (p->precision != GCR_PREC_FP32 && p->precision != GCR_PREC_BF16) return GCR_E_INVALID;
-  if (p->precision == GCR_PREC_BF16 && d % 8 != 0) return GCR_E_UNSUPPORTED;
+  const int pc = check_precision(p, d);
+  if (pc != GCR_OK) return pc;
   if (p->topk_out < 0) return GCR_E_INVALID;
   if (ng > 16384 && !(p->topk_out >= 1 && p->topk_out <= 127)) return GCR_E_UNSUPPORTED;
   return GCR_OK;
@@ -343,13 +379,14 @@ size_t carve_pipe(Carve& c, int64_t n, int64_t nq, int32_t d, const gcr_params* 
   const size_t cap = op_capacity(n, p, kinds);
   t.g.op_col = c.take<int32_t>(cap);
   t.g.op_val = c.take<float>(cap);
+  t.g.row_order = c.take<int32_t>(nn);
   t.g.stats = nullptr;
   // the build and re-rank scratch run one after the other: they share one region
   Carve cb(nullptr, 0);
   const size_t b = carve_build(cb, n, d, p, r, nullptr);
   Carve cr(nullptr, 0);
   const size_t rr = rerank_uses_pool(p, n - nq) ? carve_topk_rerank(cr, nq, n - nq, d, p, nullptr)
-                                                : carve_rerank(cr, nq, n - nq, d, p->precision == GCR_PREC_BF16, nullptr);
+                                                : carve_rerank(cr, nq, n - nq, d, tensor_mode(p), nullptr);
   t.inner_bytes = std::max(b, rr);
   t.inner = c.take<char>(t.inner_bytes);
   if (w) *w = t;
@@ -363,7 +400,7 @@ struct GalleryView {
   float* deg;      // T x ng
   double* n64;     // (T+1) x ng
   float* n32;      // (T+1) x ng
-  __nv_bfloat16* xb;  // (T+1) x ng x d (BF16 precision)
+  char* xr;        // (T+1) x ng x d rounded operand copies (tensor-core modes)
   float* enrm;     // (T+1) x ng
   float* anrm;     // (T+1) x ng
   RowScalars* sc;  // T+1
@@ -381,13 +418,13 @@ int check_serve_params(const gcr_params* p, int64_t ng, int32_t d, Resolved* r) 
 
 size_t carve_gallery(Carve& c, int64_t ng, int32_t d, const gcr_params* p, GalleryView* v) {
   const size_t L = (size_t)p->T + 1, n = (size_t)ng;
-  const bool bf = p->precision == GCR_PREC_BF16;
+  const bool bf = tensor_mode(p);
   GalleryView t;
   t.layers = c.take<float>(L * n * d);
   t.deg = c.take<float>((size_t)(p->T > 0 ? p->T : 1) * n);
   t.n64 = c.take<double>(L * n);
   t.n32 = c.take<float>(L * n);
-  t.xb = bf ? c.take<__nv_bfloat16>(L * n * d) : nullptr;
+  t.xr = bf ? c.take<char>(L * n * d * elt_size(p)) : nullptr;
   t.enrm = bf ? c.take<float>(L * n) : nullptr;
   t.anrm = bf ? c.take<float>(L * n) : nullptr;
   t.sc = c.take<RowScalars>(L);
@@ -415,6 +452,7 @@ size_t carve_gallery_build(Carve& c, int64_t ng, int32_t d, const gcr_params* p,
   const size_t cap = op_capacity(ng, p, 1);
   t.g.op_col = c.take<int32_t>(cap);
   t.g.op_val = c.take<float>(cap);
+  t.g.row_order = c.take<int32_t>(n);
   Carve cb(nullptr, 0);
   t.inner_bytes = carve_build(cb, ng, d, p, r, nullptr);
   t.inner = c.take<char>(t.inner_bytes);
@@ -426,7 +464,7 @@ struct ServeWs {
   float* xq[2];
   double* n64;
   float* n32;
-  __nv_bfloat16* qb;
+  void* qr;            // rounded query rows (tensor-core modes)
   float* enrm;
   float* anrm;
   RowScalars* sc;
@@ -441,7 +479,7 @@ struct ServeWs {
   int* band_cnt;
   float* band_v;
   int* band_i;
-  __nv_bfloat16* band_a;
+  void* band_a;
   int32_t* nbr;
   float* d2;
   unsigned long long* stats;
@@ -464,14 +502,15 @@ int serve_kp_final(const gcr_params* p) {
 
 size_t carve_serve(Carve& c, int64_t b, int32_t d, const gcr_params* p, const Resolved& r, ServeWs* w) {
   const size_t nb = (size_t)b;
-  const bool bf = p->precision == GCR_PREC_BF16;
+  const bool bf = tensor_mode(p);
+  const size_t es = elt_size(p);
   const int kpmax = std::max(r.kp, serve_kp_final(p));
   ServeWs t;
   t.xq[0] = c.take<float>(nb * d);
   t.xq[1] = c.take<float>(nb * d);
   t.n64 = c.take<double>(nb);
   t.n32 = c.take<float>(nb);
-  t.qb = bf ? c.take<__nv_bfloat16>(nb * d) : nullptr;
+  t.qr = bf ? c.take<char>(nb * d * es) : nullptr;
   t.enrm = bf ? c.take<float>(nb) : nullptr;
   t.anrm = bf ? c.take<float>(nb) : nullptr;
   t.sc = c.take<RowScalars>(1);
@@ -486,7 +525,7 @@ size_t carve_serve(Carve& c, int64_t b, int32_t d, const gcr_params* p, const Re
   t.band_cnt = c.take<int>(nb);
   t.band_v = c.take<float>(nb * kBandCap);
   t.band_i = c.take<int>(nb * kBandCap);
-  t.band_a = bf ? c.take<__nv_bfloat16>(nb * d) : nullptr;
+  t.band_a = bf ? c.take<char>(nb * d * es) : nullptr;
   t.nbr = c.take<int32_t>(nb * std::max(p->k, 1));
   t.d2 = c.take<float>(nb * std::max(p->k, 1));
   t.stats = c.take<unsigned long long>(GCR_STATS_LEN);
@@ -494,30 +533,31 @@ size_t carve_serve(Carve& c, int64_t b, int32_t d, const gcr_params* p, const Re
   return c.off;
 }
 
-// The gallery side of a certified top-k search: FP32 rows, their BF16 shadow (BF16 path),
-// squared norms and maxima.
+// The gallery side of a certified top-k search: FP32 rows, their rounded operand copy
+// (tensor-core modes), squared norms and maxima.
 struct GallerySide {
   const float* G;
-  const __nv_bfloat16* Gb;
+  const void* Gr;
   const double* n64;
   const RowScalars* sc;
 };
 
-GallerySide gallery_layer(const GalleryView& g, int layer, int ng, int d) {
-  return GallerySide{g.layers + (size_t)layer * ng * d, g.xb ? g.xb + (size_t)layer * ng * d : nullptr,
+GallerySide gallery_layer(const GalleryView& g, int layer, int ng, int d, size_t es) {
+  return GallerySide{g.layers + (size_t)layer * ng * d, g.xr ? g.xr + (size_t)layer * ng * d * es : nullptr,
                      g.n64 + (size_t)layer * ng, g.sc + layer};
 }
 
 // Certified k nearest gallery rows for the b query rows xq: pool, merge, refine, band.
 int serve_knn(const float* xq, int b, int d, const gcr_params* p, int k, int kp, const GallerySide& gs, int ng,
               const ServeWs& w, unsigned long long* stats, int32_t* nbr, float* d2, cudaStream_t st) {
-  const bool bf = p->precision == GCR_PREC_BF16;
+  const bool bf = tensor_mode(p);
+  const Elt elt = elt_of(p);
   const float* G = gs.G;
   const int rblocks = (b + 127) / 128;
   const int splits = std::max(1, std::min(kServeMaxSplits, (152 + rblocks - 1) / rblocks));
   {
     StageScope sc_(GCR_STAGE_PREP, st, bf ? 2 : 2);
-    GCR_CUDA_TRY(launch_row_stats(xq, b, d, w.n64, w.n32, bf ? w.qb : nullptr, w.enrm, w.anrm, w.sc, st));
+    GCR_CUDA_TRY(launch_row_stats(xq, b, d, w.n64, w.n32, bf ? w.qr : nullptr, elt, w.enrm, w.anrm, w.sc, st));
   }
   GCR_CUDA_TRY(cudaMemsetAsync(w.unc_count, 0, sizeof(int) * 4, st));
   GCR_CUDA_TRY(cudaMemsetAsync(w.band_cnt, 0, sizeof(int) * b, st));
@@ -527,8 +567,8 @@ int serve_knn(const float* xq, int b, int d, const gcr_params* p, int k, int kp,
     if (bf) {
       const int ntiles = (ng + 255) / 256;
       used_splits = split_count(splits, ntiles);
-      GCR_CUDA_TRY(launch_umma_pool(w.qb, b, gs.Gb, ng, d, nullptr, false, 0, kp, used_splits, w.part_v, w.part_i,
-                                    st));
+      GCR_CUDA_TRY(launch_umma_pool(w.qr, b, gs.Gr, ng, d, elt, nullptr, false, 0, kp, used_splits, w.part_v,
+                                    w.part_i, st));
     } else {
       const int ntiles = (ng + 127) / 128;
       used_splits = split_count(splits, ntiles);
@@ -554,8 +594,8 @@ int serve_knn(const float* xq, int b, int d, const gcr_params* p, int k, int kp,
   {
     StageScope sc_(GCR_STAGE_BAND, st, bf ? 3 : 2);
     if (bf) {
-      GCR_CUDA_TRY(launch_gather_bf16(w.qb, d, w.unc_count, w.unc_row, b, w.band_a, st));
-      GCR_CUDA_TRY(launch_umma_band(gs.Gb, ng, d, nullptr, 0, w.band_a, w.unc_count, b, w.unc_row, w.unc_kind,
+      GCR_CUDA_TRY(launch_gather_rows(w.qr, (size_t)d * elt_bytes(elt), w.unc_count, w.unc_row, b, w.band_a, st));
+      GCR_CUDA_TRY(launch_umma_band(gs.Gr, ng, d, elt, nullptr, 0, w.band_a, w.unc_count, b, w.unc_row, w.unc_kind,
                                     w.unc_thr, kBandCap, w.band_cnt, w.band_v, w.band_i, st));
     } else {
       GCR_CUDA_TRY(launch_sgemm_band(xq, G, ng, d, nullptr, 0, w.unc_count, b, w.unc_row, w.unc_kind, w.unc_thr,
@@ -570,14 +610,14 @@ struct TopkRerankWs {
   ServeWs sw;
   double* n64g;
   float* n32g;
-  __nv_bfloat16* gb;
+  void* gr;            // rounded gallery rows (tensor-core modes)
   float* genrm;
   float* ganrm;
   RowScalars* scg;
 };
 
 size_t carve_topk_rerank(Carve& c, int64_t nq, int64_t ng, int32_t d, const gcr_params* p, TopkRerankWs* w) {
-  const bool bf = p->precision == GCR_PREC_BF16;
+  const bool bf = tensor_mode(p);
   Resolved r;
   r.kp = serve_kp_final(p);
   r.kinds = 1;
@@ -585,7 +625,7 @@ size_t carve_topk_rerank(Carve& c, int64_t nq, int64_t ng, int32_t d, const gcr_
   carve_serve(c, nq, d, p, r, &t.sw);
   t.n64g = c.take<double>(ng);
   t.n32g = c.take<float>(ng);
-  t.gb = bf ? c.take<__nv_bfloat16>((size_t)ng * d) : nullptr;
+  t.gr = bf ? c.take<char>((size_t)ng * d * elt_size(p)) : nullptr;
   t.genrm = c.take<float>(ng);
   t.ganrm = c.take<float>(ng);
   t.scg = c.take<RowScalars>(1);
@@ -595,13 +635,14 @@ size_t carve_topk_rerank(Carve& c, int64_t nq, int64_t ng, int32_t d, const gcr_
 
 int topk_rerank_impl(const float* Xq, int64_t nq, const float* Xg, int64_t ng, int32_t d, const gcr_params* p,
                      int32_t* idx_out, float* dist_out, const TopkRerankWs& w, cudaStream_t st) {
-  const bool bf = p->precision == GCR_PREC_BF16;
+  const bool bf = tensor_mode(p);
   {
     StageScope sc_(GCR_STAGE_PREP, st, 2);
-    GCR_CUDA_TRY(launch_row_stats(Xg, (int)ng, d, w.n64g, w.n32g, bf ? w.gb : nullptr, w.genrm, w.ganrm, w.scg, st));
+    GCR_CUDA_TRY(launch_row_stats(Xg, (int)ng, d, w.n64g, w.n32g, bf ? w.gr : nullptr, elt_of(p), w.genrm, w.ganrm,
+                                  w.scg, st));
   }
   GCR_CUDA_TRY(cudaMemsetAsync(w.sw.stats, 0, sizeof(unsigned long long) * GCR_STATS_LEN, st));
-  const GallerySide gs{Xg, w.gb, w.n64g, w.scg};
+  const GallerySide gs{Xg, w.gr, w.n64g, w.scg};
   return serve_knn(Xq, (int)nq, d, p, p->topk_out, serve_kp_final(p), gs, (int)ng, w.sw, w.sw.stats, idx_out,
                    dist_out, st);
 }
@@ -726,7 +767,7 @@ int gcr_propagate(const gcr_graph* g, const float* X_in, float* X_out, int64_t n
   if (d % 4 != 0) return GCR_E_UNSUPPORTED;
   StageScope sc_(GCR_STAGE_PROPAGATE, (cudaStream_t)stream);
   GCR_CUDA_TRY(launch_propagate(g->op_rowptr, g->op_len, g->op_col, g->op_val, X_in, X_out, (int)n, d,
-                                (cudaStream_t)stream));
+                                g->row_order, (cudaStream_t)stream));
   return GCR_OK;
 }
 
@@ -734,7 +775,7 @@ size_t gcr_rerank_workspace_size(int64_t nq, int64_t ng, int32_t d, const gcr_pa
   if (check_rerank(nq, ng, d, p) != GCR_OK) return 0;
   Carve c(nullptr, 0);
   if (rerank_uses_pool(p, ng)) return carve_topk_rerank(c, nq, ng, d, p, nullptr) + 256;
-  return carve_rerank(c, nq, ng, d, p->precision == GCR_PREC_BF16, nullptr) + 256;
+  return carve_rerank(c, nq, ng, d, tensor_mode(p), nullptr) + 256;
 }
 
 int gcr_rerank(const float* Xq, int64_t nq, const float* Xg, int64_t ng, int32_t d, const gcr_params* p,
@@ -750,7 +791,7 @@ int gcr_rerank(const float* Xq, int64_t nq, const float* Xg, int64_t ng, int32_t
     return topk_rerank_impl(Xq, nq, Xg, ng, d, p, idx_out, dist_out, tw, (cudaStream_t)stream);
   }
   RerankWs w;
-  if (carve_rerank(c, nq, ng, d, p->precision == GCR_PREC_BF16, &w) > ws_bytes) return GCR_E_WORKSPACE;
+  if (carve_rerank(c, nq, ng, d, tensor_mode(p), &w) > ws_bytes) return GCR_E_WORKSPACE;
   return rerank_impl(Xq, nq, Xg, ng, d, p, idx_out, dist_out, w, (cudaStream_t)stream);
 }
 
@@ -807,7 +848,8 @@ int gcr_gallery_build(const float* Xg, int64_t ng, int32_t d, const gcr_params* 
   if (carve_gallery_build(cw, ng, d, p, r, &w) > ws_bytes) return GCR_E_WORKSPACE;
   cudaStream_t st = (cudaStream_t)stream;
   const int n = (int)ng;
-  const bool bf = p->precision == GCR_PREC_BF16;
+  const bool bf = tensor_mode(p);
+  const size_t es = elt_size(p);
   GCR_CUDA_TRY(launch_normalize(Xg, g.layers, ng, d, st));
   for (int t = 0; t < p->T; ++t) {
     float* cur = g.layers + (size_t)t * n * d;
@@ -818,11 +860,13 @@ int gcr_gallery_build(const float* Xg, int64_t ng, int32_t d, const gcr_params* 
     s = build_graph_impl(cur, ng, d, nullptr, p, r, &w.g, bw, st);
     if (s != GCR_OK) return s;
     GCR_CUDA_TRY(launch_layer_degree(w.g.deg_r, w.g.deg_c, n, p->symmetric, g.deg + (size_t)t * n, st));
-    GCR_CUDA_TRY(launch_propagate(w.g.op_rowptr, w.g.op_len, w.g.op_col, w.g.op_val, cur, nxt, n, d, st));
+    GCR_CUDA_TRY(launch_propagate(w.g.op_rowptr, w.g.op_len, w.g.op_col, w.g.op_val, cur, nxt, n, d,
+                                  p->k > 0 ? w.g.row_order : nullptr, st));
   }
   for (int t = 0; t <= p->T; ++t) {
     GCR_CUDA_TRY(launch_row_stats(g.layers + (size_t)t * n * d, n, d, g.n64 + (size_t)t * n, g.n32 + (size_t)t * n,
-                                  bf ? g.xb + (size_t)t * n * d : nullptr, bf ? g.enrm + (size_t)t * n : nullptr,
+                                  bf ? g.xr + (size_t)t * n * d * es : nullptr, elt_of(p),
+                                  bf ? g.enrm + (size_t)t * n : nullptr,
                                   bf ? g.anrm + (size_t)t * n : nullptr, g.sc + t, st));
   }
   return GCR_OK;
@@ -859,7 +903,7 @@ int gcr_serve(const void* state, size_t state_bytes, int64_t ng, const float* Xq
   int cur = 0;
   for (int t = 0; t < p->T; ++t) {
     if (p->k > 0) {
-      s = serve_knn(w.xq[cur], nq, d, p, p->k, r.kp, gallery_layer(g, t, n, d), n, w, stp, w.nbr, w.d2, st);
+      s = serve_knn(w.xq[cur], nq, d, p, p->k, r.kp, gallery_layer(g, t, n, d, elt_size(p)), n, w, stp, w.nbr, w.d2, st);
       if (s != GCR_OK) return s;
     }
     StageScope sc_(GCR_STAGE_PROPAGATE, st);
@@ -867,7 +911,7 @@ int gcr_serve(const void* state, size_t state_bytes, int64_t ng, const float* Xq
                                    w.d2, p->k, p->gamma, p->symmetric, w.xq[cur ^ 1], st));
     cur ^= 1;
   }
-  return serve_knn(w.xq[cur], nq, d, p, p->topk_out, serve_kp_final(p), gallery_layer(g, p->T, n, d), n, w, stp,
+  return serve_knn(w.xq[cur], nq, d, p, p->topk_out, serve_kp_final(p), gallery_layer(g, p->T, n, d, elt_size(p)), n, w, stp,
                    idx_out, dist_out, st);
 }
 
@@ -909,7 +953,8 @@ int gcr_pipeline(const float* X, int64_t n, int64_t nq, int32_t d, const int32_t
     if (s != GCR_OK) return s;
     {
       StageScope sc_(GCR_STAGE_PROPAGATE, st);
-      GCR_CUDA_TRY(launch_propagate(w.g.op_rowptr, w.g.op_len, w.g.op_col, w.g.op_val, cur, nxt, (int)n, d, st));
+      GCR_CUDA_TRY(launch_propagate(w.g.op_rowptr, w.g.op_len, w.g.op_col, w.g.op_val, cur, nxt, (int)n, d,
+                                    p->k > 0 ? w.g.row_order : nullptr, st));
     }
     float* tmp = cur; cur = nxt; nxt = tmp;
   }
@@ -920,7 +965,7 @@ int gcr_pipeline(const float* X, int64_t n, int64_t nq, int32_t d, const int32_t
     s = topk_rerank_impl(cur, nq, cur + (size_t)nq * d, n - nq, d, p, idx_out, dist_out, tw, st);
   } else {
     RerankWs rw;
-    carve_rerank(cr, nq, n - nq, d, p->precision == GCR_PREC_BF16, &rw);
+    carve_rerank(cr, nq, n - nq, d, tensor_mode(p), &rw);
     s = rerank_impl(cur, nq, cur + (size_t)nq * d, n - nq, d, p, idx_out, dist_out, rw, st);
   }
   if (s != GCR_OK) return s;

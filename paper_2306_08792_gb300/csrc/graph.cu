@@ -340,6 +340,11 @@ __global__ void op_fill_kernel(OpArgs a) {
 
 }  // namespace
 
+cudaError_t launch_scan(const int* in, int* out, int n, cudaStream_t st) {
+  scan_kernel<<<1, 1024, 0, st>>>(in, out, n);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_build_operator(const GraphArgs& g, cudaStream_t st) {
   const int n = g.n, k = g.k;
   cudaError_t e;

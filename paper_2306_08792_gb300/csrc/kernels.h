@@ -6,18 +6,25 @@
 
 namespace gcr {
 
+// Element type of the tensor-core GEMM operands: BF16 copies of the rows, or FP32 rows
+// rounded to TF32 (10 explicit mantissa bits, low 13 bits zero).
+enum class Elt : int { BF16 = 0, TF32 = 1 };
+inline size_t elt_bytes(Elt e) { return e == Elt::TF32 ? 4 : 2; }
+
 // Per-call scalars reduced over the rows of X (device memory).
 struct RowScalars {
   double nmin, nmax;   // min / max of ||x_j||^2
   double bmax;         // max ||x_j||
-  double emax;         // max ||bf16(x_j) - x_j||   (BF16 path)
-  double amax;         // max ||bf16(x_j)||         (BF16 path)
+  double emax;         // max ||round(x_j) - x_j||   (tensor-core paths)
+  double amax;         // max ||round(x_j)||         (tensor-core paths)
 };
 
 // ---- prep.cu
 cudaError_t launch_normalize(const float* X_in, float* X_out, int64_t n, int d, cudaStream_t st);
+// xr (may be NULL): the rounded operand copy (BF16, or TF32 held as FP32) written alongside
+// the rounding-error norms enrm and the norms of the rounded rows anrm.
 cudaError_t launch_row_stats(const float* X, int n, int d, double* n64, float* n32,
-                             __nv_bfloat16* xb, float* enrm, float* anrm, RowScalars* sc,
+                             void* xr, Elt elt, float* enrm, float* anrm, RowScalars* sc,
                              cudaStream_t st);
 cudaError_t launch_split3(const float* X, int n, int d, int gallery_order, __nv_bfloat16* out, cudaStream_t st);
 
@@ -34,14 +41,14 @@ cudaError_t launch_sgemm_band(const float* X, const float* Bm, int n, int d, con
 cudaError_t launch_sgemm_dist(const float* Xq, int nq, const float* Xg, int ng, int d,
                               const float* nrm_q, const float* nrm_g, float* D, cudaStream_t st);
 
-// ---- umma.cu (tcgen05 BF16 path)
-// Pools of S = A . B^T rows: [split][kind][na][kp], kp = 64 or 128 (128 without cross).
-cudaError_t launch_umma_pool(const __nv_bfloat16* Ab, int na, const __nv_bfloat16* Bb, int nb, int d,
+// ---- umma.cu (tcgen05 path; operands BF16 or TF32)
+// Pools of S = A . B^T rows: [split][kind][na][kp], kp = 32, 64 or 128.
+cudaError_t launch_umma_pool(const void* Ab, int na, const void* Bb, int nb, int d, Elt elt,
                              const int* cam, bool cross, int self_excl, int kp, int splits, float* pool_v,
                              int* pool_i, cudaStream_t st);
 // Threshold rescan: gathered rows Ab (cap rows, *count valid) against the n rows of Xb.
-cudaError_t launch_umma_band(const __nv_bfloat16* Xb, int n, int d, const int* cam, int self_excl,
-                             const __nv_bfloat16* Ab, const int* count, int cap, const int* band_row,
+cudaError_t launch_umma_band(const void* Xb, int n, int d, Elt elt, const int* cam, int self_excl,
+                             const void* Ab, const int* count, int cap, const int* band_row,
                              const int* band_kind, const float* band_thr, int bcap, int* band_cnt, float* band_v,
                              int* band_i, cudaStream_t st);
 cudaError_t launch_umma_dist(const __nv_bfloat16* Qb, int nq, const __nv_bfloat16* Gb, int ng, int d,
@@ -54,10 +61,10 @@ struct RefineArgs {
   const float* X;           // rows whose neighbours are refined (n x d)
   const float* XB;          // rows the candidates index (equal to X for the offline graph)
   int n, d, k, kinds;
-  int precision;            // GCR_PREC_FP32 / GCR_PREC_BF16
+  int precision;            // GCR_PREC_FP32 / GCR_PREC_BF16 / GCR_PREC_TF32
   const double* n64;        // ||x_i||^2 of the rows of X
   const double* n64B;       // ||x_j||^2 of the rows of XB
-  const float* enrm;        // BF16 statistics of the rows of X
+  const float* enrm;        // rounding statistics of the rows of X (tensor-core paths)
   const float* anrm;
   const RowScalars* sc;     // maxima over the rows of XB
   const float* pool_v;      // [kinds][n][kp]
@@ -76,11 +83,16 @@ struct RefineArgs {
   const int* band_i;
   int bcap;
   int band_rows;            // capacity of the band buffers (rows beyond it are not rescanned)
+  const int* order;         // processing order of the rows (NULL: 0..n-1); results do not depend on it
 };
 cudaError_t launch_refine_pool(const RefineArgs& a, cudaStream_t st);
 cudaError_t launch_refine_band(const RefineArgs& a, cudaStream_t st);
-cudaError_t launch_gather_bf16(const __nv_bfloat16* Xb, int d, const int* count, const int* rows,
-                               int max_rows, __nv_bfloat16* out, cudaStream_t st);
+// Cluster-local row order from the pools (first k candidates): order[0..n) is a permutation.
+cudaError_t launch_row_order(const int* pool_i, int n, int kp, int k, int* key, int* cnt, int* off, int* fill,
+                             int* order, cudaStream_t st);
+// Copies rows[u] of src (row_bytes each, a multiple of 16) to row u of out, u < min(*count, max_rows).
+cudaError_t launch_gather_rows(const void* src, size_t row_bytes, const int* count, const int* rows,
+                               int max_rows, void* out, cudaStream_t st);
 
 // ---- graph.cu
 struct GraphArgs {
@@ -105,10 +117,12 @@ struct GraphArgs {
   int* scan_tmp;            // [n+1] scratch
 };
 cudaError_t launch_build_operator(const GraphArgs& g, cudaStream_t st);
+cudaError_t launch_scan(const int* in, int* out, int n, cudaStream_t st);
 
 // ---- propagate.cu
+// order (may be NULL): the rows in processing order; results do not depend on it.
 cudaError_t launch_propagate(const int* rowptr, const int* len, const int* col, const float* val,
-                             const float* X_in, float* X_out, int n, int d, cudaStream_t st);
+                             const float* X_in, float* X_out, int n, int d, const int* order, cudaStream_t st);
 
 // ---- gcrv.cu
 struct GcrvWs {

@@ -16,8 +16,9 @@
 
 namespace gcr {
 
-// Queue layout in shared memory: for CTA-local row r, slot s lives at r*kQCap + (s ^ (r & 31)),
-// so that the owner's appends and the warp's reads during a merge are both conflict-free.
+// Queue layout in shared memory: float2 entries (score, index bits); for CTA-local row r,
+// slot s lives at r*kQCap + (s ^ (r & 31)), so that the owner's 8-byte appends and the warp's
+// reads during a merge are both conflict-free.
 struct PoolOwner {
   float tau;
   int qcnt;
@@ -33,10 +34,8 @@ __device__ __forceinline__ void pool_init(PoolOwner& o, bool valid) {
 // Branch-free append: the candidate is always written into the next free slot and the count
 // only advances when it passes (ok and v > tau). The caller guarantees qcnt < kQCap before
 // every call (pool_make_room with room = values pushed before the next check).
-__device__ __forceinline__ void pool_push(PoolOwner& o, float v, int j, bool ok, float* qv, int* qi, int sw) {
-  const int s = o.qcnt ^ sw;
-  qv[s] = v;
-  qi[s] = j;
+__device__ __forceinline__ void pool_push(PoolOwner& o, float v, int j, bool ok, float2* q, int sw) {
+  q[o.qcnt ^ sw] = make_float2(v, __int_as_float(j));
   o.qcnt += (ok && v > o.tau) ? 1 : 0;
 }
 
@@ -51,20 +50,18 @@ struct MergeResult {
 
 template <int KP>
 __device__ __noinline__ MergeResult pool_merge_row(int owner, int lane, float* lv, int* li,
-                                                   const float* qv_row, const int* qi_row, int sw,
-                                                   int my_qcnt, int my_len) {
+                                                   const float2* q_row, int sw, int my_qcnt, int my_len) {
   __syncwarp();  // the owner's queue writes must be visible to the whole warp
   int q = __shfl_sync(GCR_FULL, my_qcnt, owner);
   int L = __shfl_sync(GCR_FULL, my_len, owner);
   float a = -CUDART_INF_F;
   int ai = -1;
   if (lane < q) {
-    a = qv_row[lane ^ sw];
-    ai = qi_row[lane ^ sw];
+    const float2 e = q_row[lane ^ sw];
+    a = e.x;
+    ai = __float_as_int(e.y);
   }
-  warp_sort32_desc(a, ai, lane);
-  float ar = __shfl_sync(GCR_FULL, a, 31 - lane);
-  int ari = __shfl_sync(GCR_FULL, ai, 31 - lane);
+  // the list loads (L2 latency) are issued before the queue sort so that the two overlap
   static_assert(KP == 32 || KP == 64 || KP == 128, "pool size must be 32, 64 or 128");
   constexpr int P = KP / 32;  // list entries per lane: entry e = p*32 + lane
   float b[P];
@@ -75,6 +72,9 @@ __device__ __noinline__ MergeResult pool_merge_row(int owner, int lane, float* l
     b[p] = e < L ? lv[e] : -CUDART_INF_F;
     bi[p] = e < L ? li[e] : -1;
   }
+  warp_sort32_desc(a, ai, lane);
+  float ar = __shfl_sync(GCR_FULL, a, 31 - lane);
+  int ari = __shfl_sync(GCR_FULL, ai, 31 - lane);
   // Top KP of (list, descending) U (queue, descending): C[s] = max(B[s], Q[KP-1-s]) with Q
   // padded by -inf past 32 entries is a bitonic sequence holding exactly those KP; only the
   // last 32 entries can change. A bitonic merge then sorts it.
@@ -102,9 +102,9 @@ __device__ __noinline__ MergeResult pool_merge_row(int owner, int lane, float* l
 }
 
 template <int KP>
-__device__ __forceinline__ void pool_merge_apply(int owner, int lane, float* lv, int* li, const float* qv_row,
-                                                 const int* qi_row, int sw, PoolOwner& me) {
-  const MergeResult r = pool_merge_row<KP>(owner, lane, lv, li, qv_row, qi_row, sw, me.qcnt, me.len);
+__device__ __forceinline__ void pool_merge_apply(int owner, int lane, float* lv, int* li, const float2* q_row,
+                                                 int sw, PoolOwner& me) {
+  const MergeResult r = pool_merge_row<KP>(owner, lane, lv, li, q_row, sw, me.qcnt, me.len);
   if (lane == owner) {
     me.len = r.len;
     me.qcnt = 0;
@@ -117,32 +117,28 @@ __device__ __forceinline__ void pool_merge_apply(int owner, int lane, float* lv,
 // row_of_lane0: global row of lane 0; qrow0: CTA-local queue row of lane 0.
 template <int KP>
 __device__ __forceinline__ void pool_make_room(int room, int lane, PoolOwner& me, int row_of_lane0,
-                                               int qrow0, float* qv, int* qi, float* pool_v,
-                                               int* pool_i) {
+                                               int qrow0, float2* q, float* pool_v, int* pool_i) {
   unsigned m = __ballot_sync(GCR_FULL, me.qcnt >= kQCap - room);
   while (m) {
     int o = __ffs(m) - 1;
     m &= m - 1;
     int qr = qrow0 + o;
     size_t grow = (size_t)(row_of_lane0 + o);
-    pool_merge_apply<KP>(o, lane, pool_v + grow * KP, pool_i + grow * KP, qv + qr * kQCap,
-                         qi + qr * kQCap, qr & 31, me);
+    pool_merge_apply<KP>(o, lane, pool_v + grow * KP, pool_i + grow * KP, q + qr * kQCap, qr & 31, me);
   }
 }
 
 // Final merge of every valid row of the warp (writes the list even if nothing is queued).
 template <int KP>
 __device__ __forceinline__ void pool_flush(int lane, bool valid, PoolOwner& me, int row_of_lane0,
-                                           int qrow0, float* qv, int* qi, float* pool_v,
-                                           int* pool_i) {
+                                           int qrow0, float2* q, float* pool_v, int* pool_i) {
   unsigned m = __ballot_sync(GCR_FULL, valid);
   while (m) {
     int o = __ffs(m) - 1;
     m &= m - 1;
     int qr = qrow0 + o;
     size_t grow = (size_t)(row_of_lane0 + o);
-    pool_merge_apply<KP>(o, lane, pool_v + grow * KP, pool_i + grow * KP, qv + qr * kQCap,
-                         qi + qr * kQCap, qr & 31, me);
+    pool_merge_apply<KP>(o, lane, pool_v + grow * KP, pool_i + grow * KP, q + qr * kQCap, qr & 31, me);
   }
 }
 

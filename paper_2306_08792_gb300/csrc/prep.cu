@@ -47,12 +47,21 @@ __global__ void normalize_kernel(const float* __restrict__ X_in, float* __restri
   }
 }
 
+// Rounding of an FP32 value to TF32 (10 explicit mantissa bits): round to nearest, ties away
+// from zero, by adding half a unit of the 13th bit to the magnitude and clearing the low 13
+// bits (a carry into the exponent gives the next power of two). Finite inputs only.
+__device__ __forceinline__ float round_tf32(float x) {
+  return __uint_as_float((__float_as_uint(x) + 0x1000u) & 0xFFFFE000u);
+}
+
 // n64[i] = ||x_i||^2 (float-float accumulation, combined in FP64), n32[i] = its FP32 rounding;
-// with xb != NULL also the BF16 shadow xb = bf16_rn(x), enrm[i] >= ||xb_i - x_i|| and
-// anrm[i] >= ||xb_i|| (FP32 sums rounded up by a relative margin that covers their own
-// accumulation error: at most (d/32 + 5) * 2^-24 < 1e-3 for d <= 4096).
+// with xr != NULL also the rounded operand copy xr = round(x) (BF16 round-to-nearest-even, or
+// TF32 as above, held as FP32), enrm[i] >= ||round(x_i) - x_i|| and anrm[i] >= ||round(x_i)||
+// (FP32 sums rounded up by a relative margin that covers their own accumulation error: at most
+// (d/32 + 5) * 2^-24 < 1e-3 for d <= 4096). Each difference round(x) - x is exact in FP32.
+template <Elt E>
 __global__ void row_stats_kernel(const float* __restrict__ X, int n, int d, double* __restrict__ n64,
-                                 float* __restrict__ n32, __nv_bfloat16* __restrict__ xb,
+                                 float* __restrict__ n32, void* __restrict__ xr,
                                  float* __restrict__ enrm, float* __restrict__ anrm) {
   const int lane = threadIdx.x & 31;
   const int row = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
@@ -64,28 +73,35 @@ __global__ void row_stats_kernel(const float* __restrict__ X, int n, int d, doub
   for (int v = lane; v < d4; v += 32) {
     float4 x = src[v];
     acc.add_sq(x.x); acc.add_sq(x.y); acc.add_sq(x.z); acc.add_sq(x.w);
-    if (xb) {
-      __nv_bfloat16 b0 = __float2bfloat16_rn(x.x), b1 = __float2bfloat16_rn(x.y);
-      __nv_bfloat16 b2 = __float2bfloat16_rn(x.z), b3 = __float2bfloat16_rn(x.w);
-      __nv_bfloat162* o = reinterpret_cast<__nv_bfloat162*>(xb + (size_t)row * d + 4 * v);
-      o[0] = __halves2bfloat162(b0, b1);
-      o[1] = __halves2bfloat162(b2, b3);
-      const float f0 = __bfloat162float(b0), f1 = __bfloat162float(b1);
-      const float f2 = __bfloat162float(b2), f3 = __bfloat162float(b3);
+    if (xr) {
+      float f0, f1, f2, f3;
+      if constexpr (E == Elt::BF16) {
+        __nv_bfloat16 b0 = __float2bfloat16_rn(x.x), b1 = __float2bfloat16_rn(x.y);
+        __nv_bfloat16 b2 = __float2bfloat16_rn(x.z), b3 = __float2bfloat16_rn(x.w);
+        __nv_bfloat162* o = reinterpret_cast<__nv_bfloat162*>(static_cast<__nv_bfloat16*>(xr) + (size_t)row * d + 4 * v);
+        o[0] = __halves2bfloat162(b0, b1);
+        o[1] = __halves2bfloat162(b2, b3);
+        f0 = __bfloat162float(b0); f1 = __bfloat162float(b1);
+        f2 = __bfloat162float(b2); f3 = __bfloat162float(b3);
+      } else {
+        f0 = round_tf32(x.x); f1 = round_tf32(x.y);
+        f2 = round_tf32(x.z); f3 = round_tf32(x.w);
+        reinterpret_cast<float4*>(static_cast<float*>(xr) + (size_t)row * d)[v] = make_float4(f0, f1, f2, f3);
+      }
       const float e0 = f0 - x.x, e1 = f1 - x.y, e2 = f2 - x.z, e3 = f3 - x.w;  // exact differences
       ee = fmaf(e0, e0, fmaf(e1, e1, fmaf(e2, e2, fmaf(e3, e3, ee))));
       aa = fmaf(f0, f0, fmaf(f1, f1, fmaf(f2, f2, fmaf(f3, f3, aa))));
     }
   }
   const double ss = warp_sum_d(acc.value());
-  if (xb) {
+  if (xr) {
     ee = warp_sum(ee);
     aa = warp_sum(aa);
   }
   if (lane == 0) {
     n64[row] = ss;
     n32[row] = (float)ss;
-    if (xb) {
+    if (xr) {
       enrm[row] = sqrtf(ee * 1.002f) * 1.0001f;
       anrm[row] = sqrtf(aa * 1.002f) * 1.0001f;
     }
@@ -170,13 +186,16 @@ cudaError_t launch_normalize(const float* X_in, float* X_out, int64_t n, int d, 
 }
 
 cudaError_t launch_row_stats(const float* X, int n, int d, double* n64, float* n32,
-                             __nv_bfloat16* xb, float* enrm, float* anrm, RowScalars* sc,
+                             void* xr, Elt elt, float* enrm, float* anrm, RowScalars* sc,
                              cudaStream_t st) {
   const int wpb = 8;
-  row_stats_kernel<<<(n + wpb - 1) / wpb, wpb * 32, 0, st>>>(X, n, d, n64, n32, xb, enrm, anrm);
+  if (elt == Elt::TF32)
+    row_stats_kernel<Elt::TF32><<<(n + wpb - 1) / wpb, wpb * 32, 0, st>>>(X, n, d, n64, n32, xr, enrm, anrm);
+  else
+    row_stats_kernel<Elt::BF16><<<(n + wpb - 1) / wpb, wpb * 32, 0, st>>>(X, n, d, n64, n32, xr, enrm, anrm);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  row_scalars_kernel<<<1, 1024, 0, st>>>(n64, xb ? enrm : nullptr, xb ? anrm : nullptr, n, sc);
+  row_scalars_kernel<<<1, 1024, 0, st>>>(n64, xr ? enrm : nullptr, xr ? anrm : nullptr, n, sc);
   return cudaGetLastError();
 }
 

@@ -14,10 +14,11 @@ template <int VPL>
 __global__ void __launch_bounds__(256) propagate_kernel(const int* __restrict__ rowptr, const int* __restrict__ len,
                                                         const int* __restrict__ col, const float* __restrict__ val,
                                                         const float* __restrict__ X_in, float* __restrict__ X_out,
-                                                        int n, int d) {
+                                                        int n, int d, const int* __restrict__ order) {
   const int lane = threadIdx.x & 31;
-  const int i = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-  if (i >= n) return;
+  const int w = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  if (w >= n) return;
+  const int i = order ? order[w] : w;
   float4 acc[VPL];
 #pragma unroll
   for (int v = 0; v < VPL; ++v) acc[v] = make_float4(0.f, 0.f, 0.f, 0.f);
@@ -80,15 +81,15 @@ __global__ void __launch_bounds__(256) propagate_kernel(const int* __restrict__ 
 }  // namespace
 
 cudaError_t launch_propagate(const int* rowptr, const int* len, const int* col, const float* val,
-                             const float* X_in, float* X_out, int n, int d, cudaStream_t st) {
+                             const float* X_in, float* X_out, int n, int d, const int* order, cudaStream_t st) {
   dim3 grid((n + 7) / 8);
   const int vpl = (d + 127) / 128;
-  if (vpl <= 1) propagate_kernel<1><<<grid, 256, 0, st>>>(rowptr, len, col, val, X_in, X_out, n, d);
-  else if (vpl <= 2) propagate_kernel<2><<<grid, 256, 0, st>>>(rowptr, len, col, val, X_in, X_out, n, d);
-  else if (vpl <= 4) propagate_kernel<4><<<grid, 256, 0, st>>>(rowptr, len, col, val, X_in, X_out, n, d);
-  else if (vpl <= 8) propagate_kernel<8><<<grid, 256, 0, st>>>(rowptr, len, col, val, X_in, X_out, n, d);
-  else if (vpl <= 16) propagate_kernel<16><<<grid, 256, 0, st>>>(rowptr, len, col, val, X_in, X_out, n, d);
-  else if (vpl <= 32) propagate_kernel<32><<<grid, 256, 0, st>>>(rowptr, len, col, val, X_in, X_out, n, d);
+  if (vpl <= 1) propagate_kernel<1><<<grid, 256, 0, st>>>(rowptr, len, col, val, X_in, X_out, n, d, order);
+  else if (vpl <= 2) propagate_kernel<2><<<grid, 256, 0, st>>>(rowptr, len, col, val, X_in, X_out, n, d, order);
+  else if (vpl <= 4) propagate_kernel<4><<<grid, 256, 0, st>>>(rowptr, len, col, val, X_in, X_out, n, d, order);
+  else if (vpl <= 8) propagate_kernel<8><<<grid, 256, 0, st>>>(rowptr, len, col, val, X_in, X_out, n, d, order);
+  else if (vpl <= 16) propagate_kernel<16><<<grid, 256, 0, st>>>(rowptr, len, col, val, X_in, X_out, n, d, order);
+  else if (vpl <= 32) propagate_kernel<32><<<grid, 256, 0, st>>>(rowptr, len, col, val, X_in, X_out, n, d, order);
   else return cudaErrorInvalidValue;
   return cudaGetLastError();
 }

@@ -331,7 +331,8 @@ __global__ void __launch_bounds__(256) refine_pool_kernel(RefineArgs a) {
   const int lane = threadIdx.x & 31;
   const long wid = (long)blockIdx.x * 8 + (threadIdx.x >> 5);
   if (wid >= (long)a.n * a.kinds) return;
-  const int kind = (int)(wid / a.n), row = (int)(wid % a.n);
+  const int kind = (int)(wid / a.n);
+  const int row = a.order ? a.order[wid % a.n] : (int)(wid % a.n);
   const float* pv = a.pool_v + ((size_t)kind * a.n + row) * KP;
   const int* pi = a.pool_i + ((size_t)kind * a.n + row) * KP;
   WList<P> L;
@@ -433,13 +434,37 @@ __global__ void __launch_bounds__(256) refine_band_kernel(RefineArgs a) {
   }
 }
 
-__global__ void gather_bf16_kernel(const __nv_bfloat16* __restrict__ Xb, int d, const int* __restrict__ count,
-                                   const int* __restrict__ rows, int max_rows, __nv_bfloat16* __restrict__ out) {
+// Cluster-local processing order. key(i) = the smallest index among i and its first k pool
+// candidates: rows of one tight cluster share it, so a counting sort by key puts them next to
+// each other and their (largely common) candidate rows are fetched from memory once.
+__global__ void order_key_kernel(const int* __restrict__ pool_i, int n, int kp, int k, int* __restrict__ key,
+                                 int* __restrict__ cnt) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  int m = i;
+  for (int s = 0; s < k; ++s) {
+    const int j = pool_i[(size_t)i * kp + s];
+    if (j >= 0 && j < m) m = j;
+  }
+  key[i] = m;
+  atomicAdd(&cnt[m], 1);
+}
+
+__global__ void order_scatter_kernel(const int* __restrict__ key, const int* __restrict__ off, int n,
+                                     int* __restrict__ fill, int* __restrict__ order) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const int m = key[i];
+  order[off[m] + atomicAdd(&fill[m], 1)] = i;
+}
+
+// Row gather in 16-byte units: w16 units per row.
+__global__ void gather_rows_kernel(const uint4* __restrict__ src, long w16, const int* __restrict__ count,
+                                   const int* __restrict__ rows, int max_rows, uint4* __restrict__ out) {
   const int U = min(*count, max_rows);
-  const int d8 = d >> 3;
-  for (long t = (long)blockIdx.x * blockDim.x + threadIdx.x; t < (long)U * d8; t += (long)gridDim.x * blockDim.x) {
-    const long u = t / d8, c = t % d8;
-    reinterpret_cast<uint4*>(out + u * d)[c] = reinterpret_cast<const uint4*>(Xb + (size_t)rows[u] * d)[c];
+  for (long t = (long)blockIdx.x * blockDim.x + threadIdx.x; t < (long)U * w16; t += (long)gridDim.x * blockDim.x) {
+    const long u = t / w16, c = t % w16;
+    out[u * w16 + c] = src[(size_t)rows[u] * w16 + c];
   }
 }
 
@@ -485,9 +510,24 @@ cudaError_t launch_refine_band(const RefineArgs& a, cudaStream_t st) {
   return a.k >= 64 ? launch_band_p<4>(a, st) : launch_band_p<2>(a, st);
 }
 
-cudaError_t launch_gather_bf16(const __nv_bfloat16* Xb, int d, const int* count, const int* rows,
-                               int max_rows, __nv_bfloat16* out, cudaStream_t st) {
-  gather_bf16_kernel<<<152 * 4, 256, 0, st>>>(Xb, d, count, rows, max_rows, out);
+cudaError_t launch_row_order(const int* pool_i, int n, int kp, int k, int* key, int* cnt, int* off, int* fill,
+                             int* order, cudaStream_t st) {
+  cudaError_t e = cudaMemsetAsync(cnt, 0, sizeof(int) * (n + 1), st);
+  if (e != cudaSuccess) return e;
+  e = cudaMemsetAsync(fill, 0, sizeof(int) * n, st);
+  if (e != cudaSuccess) return e;
+  order_key_kernel<<<(n + 255) / 256, 256, 0, st>>>(pool_i, n, kp, k, key, cnt);
+  e = launch_scan(cnt, off, n, st);
+  if (e != cudaSuccess) return e;
+  order_scatter_kernel<<<(n + 255) / 256, 256, 0, st>>>(key, off, n, fill, order);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_gather_rows(const void* src, size_t row_bytes, const int* count, const int* rows,
+                               int max_rows, void* out, cudaStream_t st) {
+  if (row_bytes % 16) return cudaErrorInvalidValue;
+  gather_rows_kernel<<<152 * 4, 256, 0, st>>>(static_cast<const uint4*>(src), (long)(row_bytes / 16), count, rows,
+                                              max_rows, static_cast<uint4*>(out));
   return cudaGetLastError();
 }
 

@@ -34,8 +34,7 @@ sgemm_pool_kernel(const float* __restrict__ A, int na, const float* __restrict__
   __shared__ TileSmem sm;
   extern __shared__ __align__(16) unsigned char dyn[];
   float (*S)[SP] = reinterpret_cast<float (*)[SP]>(dyn);
-  float* qv = reinterpret_cast<float*>(dyn + sizeof(float) * BM * SP);
-  int* qi = reinterpret_cast<int*>(qv + 2 * BM * kQCap);
+  float2* q = reinterpret_cast<float2*>(dyn + sizeof(float) * BM * SP);
   __shared__ int cam_tile[BN];
 
   const int tid = threadIdx.x, lane = tid & 31;
@@ -50,8 +49,7 @@ sgemm_pool_kernel(const float* __restrict__ A, int na, const float* __restrict__
   pool_init(me, valid);
   const int qrow = kind * BM + r;     // queue row of this owner
   const int sw = qrow & 31;
-  float* my_qv = qv + qrow * kQCap;
-  int* my_qi = qi + qrow * kQCap;
+  float2* my_q = q + qrow * kQCap;
   const int kinds = CROSS ? 2 : 1;
   const size_t pbase = ((size_t)blockIdx.y * kinds + kind) * na * KP;
   float* pv = pool_v + pbase;
@@ -76,7 +74,7 @@ sgemm_pool_kernel(const float* __restrict__ A, int na, const float* __restrict__
     __syncthreads();
     if (kind == 0 || CROSS) {
       for (int c0 = 0; c0 < brows; c0 += 8) {
-        pool_make_room<KP>(8, lane, me, warp_row0, warp_qrow0, qv, qi, pv, pi);
+        pool_make_room<KP>(8, lane, me, warp_row0, warp_qrow0, q, pv, pi);
 #pragma unroll
         for (int c = 0; c < 8; ++c) {
           const int cc = c0 + c;
@@ -84,12 +82,12 @@ sgemm_pool_kernel(const float* __restrict__ A, int na, const float* __restrict__
           float v = S[r][cc];
           bool ok = cc < brows && !(self_excl && j == row);
           if (CROSS && kind == 1) ok = ok && cam_tile[cc] != my_cam;
-          pool_push(me, v, j, ok, my_qv, my_qi, sw);
+          pool_push(me, v, j, ok, my_q, sw);
         }
       }
     }
   }
-  if (kind == 0 || CROSS) pool_flush<KP>(lane, valid, me, warp_row0, warp_qrow0, qv, qi, pv, pi);
+  if (kind == 0 || CROSS) pool_flush<KP>(lane, valid, me, warp_row0, warp_qrow0, q, pv, pi);
 }
 
 // ---------------------------------------------------------------------------------- BAND

@@ -1,12 +1,21 @@
 // Segmented sort of the re-ranked distances (one segment per query).
 //
-// Each query's gallery distances become 64-bit keys (order-preserving bits of the FP32
-// distance, gallery index), so one ascending sort yields the ranking with ties broken by the
-// smaller gallery index. One CTA per query sorts the whole segment (up to 16384 keys) with a
-// bitonic network whose data stay in registers: each thread holds E consecutive keys, so
-// strides below E are exchanged inside a thread, strides below 32E through warp shuffles, and
-// only the strides of 32E and more (15 of the 105 stages for 16384 keys) go through shared
-// memory. The first K keys are written out.
+// Each query's gallery distances are ranked ascending with ties broken by the smaller gallery
+// index, and the first K (index, distance) pairs are written out. One CTA per query sorts the
+// whole segment (up to 16384 keys):
+//  * segments of 2048 keys and more: a stable LSD radix sort of the order-preserving 32-bit
+//    images of the distances, four 8-bit digit passes (a pass whose digit is the same for
+//    every key of the segment is skipped). Keys start in gallery-index order and every pass is
+//    stable, so equal distances stay in index order. Each thread keeps 16 keys in registers in
+//    a warp-striped layout (key e = (warp*16 + slot)*32 + lane); per pass a warp ranks its keys
+//    slot by slot with __match_any_sync (peers with the same digit, ranked by lane), per-warp
+//    digit counts go to shared memory, one block-wide scan in (digit, warp) order gives every
+//    key its destination, and keys and gallery indices are scattered to shared memory (the
+//    indices stay there, double-buffered; the keys are reloaded into registers).
+//  * shorter segments: a bitonic network on 64-bit keys (distance image, index) whose data stay
+//    in registers: each thread holds E consecutive keys, so strides below E are exchanged
+//    inside a thread, strides below 32E through warp shuffles, and only the strides of 32E and
+//    more go through shared memory.
 #include "common.cuh"
 #include "kernels.h"
 
@@ -118,11 +127,154 @@ __global__ void __launch_bounds__(1024) rank_rows_kernel(const float* __restrict
   }
 }
 
+
+// ---------------------------------------------------------------------------- radix sort
+constexpr int kHistStride = 257;  // per-warp digit counts, padded against bank conflicts in the scan
+
+// NT threads (NW = NT/32 warps, a multiple of 8), IPT keys per thread (even), segment <= NT*IPT.
+// Keys live in registers; the gallery indices live in shared memory (two buffers, swapped per
+// pass); the per-key offsets among the warp's keys of the same digit are packed two per register.
+template <int NT, int IPT>
+__global__ void __launch_bounds__(NT, 1)
+rank_rows_radix_kernel(const float* __restrict__ D, int ng, int K, int32_t* __restrict__ idx_out,
+                       float* __restrict__ dist_out) {
+  constexpr int NW = NT / 32;
+  constexpr int GPD = NW / 8;  // scan threads per digit (8 warp counts each)
+  constexpr int N = NT * IPT;
+  static_assert(NW % 8 == 0 && IPT % 2 == 0, "warps: a multiple of 8; keys per thread: even");
+  static_assert(N <= 65536, "gallery indices are held in 16 bits");
+  extern __shared__ unsigned char smem_raw[];
+  uint32_t* sk = reinterpret_cast<uint32_t*>(smem_raw);           // [N] keys
+  uint16_t* si0 = reinterpret_cast<uint16_t*>(sk + N);            // [N] gallery indices
+  uint16_t* si1 = si0 + N;                                        // [N] (second buffer)
+  uint32_t* hist = reinterpret_cast<uint32_t*>(si1 + N);          // [NW][kHistStride]
+  __shared__ uint32_t red_and[NW], red_or[NW], wsum[NW];
+
+  const int q = blockIdx.x;
+  const int t = threadIdx.x, lane = t & 31, w = t >> 5;
+  const unsigned lt = (1u << lane) - 1u;
+  const int e0 = w * 32 * IPT + lane;  // position of this thread's slot 0 (slot i: e0 + 32*i)
+  const float* row = D + (size_t)q * ng;
+  uint32_t key[IPT];
+  uint32_t offp[IPT / 2];
+  uint32_t kand = 0xffffffffu, kor = 0u;
+#pragma unroll
+  for (int i = 0; i < IPT; ++i) {
+    const int e = e0 + 32 * i;
+    key[i] = e < ng ? float_to_ordered(row[e]) : 0xffffffffu;  // padding sorts last (larger index)
+    si0[e] = (uint16_t)e;
+    if (e < ng) {
+      kand &= key[i];
+      kor |= key[i];
+    }
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    kand &= __shfl_xor_sync(GCR_FULL, kand, o);
+    kor |= __shfl_xor_sync(GCR_FULL, kor, o);
+  }
+  if (lane == 0) { red_and[w] = kand; red_or[w] = kor; }
+  __syncthreads();
+  // the bits in which the real keys differ: a digit they all share needs no pass (the padding
+  // keys are all ones, so they stay after every real key on the remaining digits)
+  uint32_t diff;
+  {
+    uint32_t a = 0xffffffffu, o = 0u;
+    for (int v = 0; v < NW; ++v) { a &= red_and[v]; o |= red_or[v]; }
+    diff = a ^ o;
+  }
+
+  uint32_t* hw = hist + w * kHistStride;
+  uint16_t* src = si0;
+  uint16_t* dstb = si1;
+  for (int shift = 0; shift < 32; shift += 8) {
+    if (((diff >> shift) & 255u) == 0) continue;  // block-uniform
+    for (int v = t; v < NW * kHistStride; v += NT) hist[v] = 0;
+    __syncthreads();
+    // per-warp stable ranking, slot by slot (slot order = key order inside the warp)
+#pragma unroll
+    for (int i = 0; i < IPT; ++i) {
+      const uint32_t dg = (key[i] >> shift) & 255u;
+      const unsigned peers = __match_any_sync(GCR_FULL, dg);
+      const uint32_t base = hw[dg];
+      __syncwarp();
+      if ((peers & lt) == 0) hw[dg] = base + (uint32_t)__popc(peers);  // the lowest peer updates
+      __syncwarp();
+      const uint32_t off = base + (uint32_t)__popc(peers & lt);
+      if (i & 1) offp[i >> 1] |= off << 16;
+      else offp[i >> 1] = off;
+    }
+    __syncthreads();
+    // exclusive scan of the counts in (digit, warp) order: thread t owns digit t / GPD and the
+    // warps 8 * (t % GPD) .. + 7
+    const int sdg = t / GPD, sw0 = (t % GPD) * 8;
+    uint32_t tot = 0;
+#pragma unroll
+    for (int j = 0; j < 8; ++j) tot += hist[(sw0 + j) * kHistStride + sdg];
+    uint32_t inc = tot;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t y = __shfl_up_sync(GCR_FULL, inc, o);
+      if (lane >= o) inc += y;
+    }
+    if (lane == 31) wsum[w] = inc;
+    __syncthreads();
+    uint32_t run = inc - tot;
+    for (int v = 0; v < w; ++v) run += wsum[v];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {  // each thread rewrites only its own counts
+      const uint32_t cj = hist[(sw0 + j) * kHistStride + sdg];
+      hist[(sw0 + j) * kHistStride + sdg] = run;
+      run += cj;
+    }
+    __syncthreads();
+    // scatter keys and indices to their destinations, then reload the keys warp-striped
+#pragma unroll
+    for (int i = 0; i < IPT; ++i) {
+      const uint32_t off = (i & 1) ? (offp[i >> 1] >> 16) : (offp[i >> 1] & 0xffffu);
+      const uint32_t dst = hw[(key[i] >> shift) & 255u] + off;
+      sk[dst] = key[i];
+      dstb[dst] = src[e0 + 32 * i];
+    }
+    __syncthreads();
+#pragma unroll
+    for (int i = 0; i < IPT; ++i) key[i] = sk[e0 + 32 * i];
+    uint16_t* tmp = src;
+    src = dstb;
+    dstb = tmp;
+    __syncthreads();
+  }
+  // registers hold ranks e0 + 32*i in order: coalesced output of the first K
+#pragma unroll
+  for (int i = 0; i < IPT; ++i) {
+    const int e = e0 + 32 * i;
+    if (e < K) {
+      idx_out[(size_t)q * K + e] = (int32_t)src[e];
+      dist_out[(size_t)q * K + e] = ordered_to_float(key[i]);
+    }
+  }
+}
+
+template <int NT, int IPT>
+cudaError_t launch_radix(const float* D, int nq, int ng, int K, int32_t* idx_out, float* dist_out,
+                         cudaStream_t st) {
+  const size_t smem = (size_t)NT * IPT * (sizeof(uint32_t) + 2 * sizeof(uint16_t)) +
+                      (size_t)(NT / 32) * kHistStride * sizeof(uint32_t);
+  cudaError_t e = cudaFuncSetAttribute(rank_rows_radix_kernel<NT, IPT>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  rank_rows_radix_kernel<NT, IPT><<<nq, NT, smem, st>>>(D, ng, K, idx_out, dist_out);
+  return cudaGetLastError();
+}
+
 }  // namespace
 
 cudaError_t launch_rank_rows(const float* D, int nq, int ng, int K, int32_t* idx_out, float* dist_out,
                              cudaStream_t st) {
   if (ng > kMaxSeg) return cudaErrorInvalidValue;
+  if (ng > 8192) return launch_radix<1024, 16>(D, nq, ng, K, idx_out, dist_out, st);
+  if (ng > 4096) return launch_radix<512, 16>(D, nq, ng, K, idx_out, dist_out, st);
+  if (ng >= 2048) return launch_radix<256, 16>(D, nq, ng, K, idx_out, dist_out, st);
   int N = 64;
   while (N < ng) N <<= 1;
   const int E = N >= 512 ? 16 : (N >= 128 ? 4 : 2);

@@ -1,11 +1,13 @@
-// BF16 similarity GEMM on the 5th-generation tensor cores (tcgen05), sm_103a.
+// Similarity GEMM on the 5th-generation tensor cores (tcgen05), sm_103a.
 //
-// S = A . B^T with A, B row-major BF16 (K = d contiguous, "K-major"): A holds 128 rows of X,
-// B 256 rows. Per CTA:
-//   warp 0        TMA producer: 64-wide K blocks of A (128 x 64) and B (256 x 64) into a
-//                 3-stage shared-memory ring (128-byte swizzle), mbarrier transaction counts;
+// S = A . B^T with A, B row-major (K = d contiguous, "K-major"), either BF16 or FP32 rows
+// rounded to TF32: A holds 128 rows of X, B 256 rows. Per CTA:
+//   warp 0        TMA producer: 128-byte K blocks (64 BF16 or 32 TF32 elements) of A (128 rows)
+//                 and B (256 rows) into a 3-stage shared-memory ring (128-byte swizzle),
+//                 mbarrier transaction counts;
 //   warp 1        allocates 512 TMEM columns (two 128 x 256 FP32 accumulators) and, from one
-//                 thread, issues tcgen05.mma.kind::f16 (M=128, N=256, K=16) for each K block,
+//                 thread, issues tcgen05.mma (kind::f16 with K=16, or kind::tf32 with K=8;
+//                 M=128, N=256) for each K block,
 //                 committing stage releases and "accumulator full" to mbarriers;
 //   warps 2..5    epilogue for the global graph, warps 6..9 for the cross-camera graph:
 //                 tcgen05.ld.32x32b gives each thread one accumulator row (32 columns per
@@ -30,10 +32,10 @@ namespace {
 
 constexpr int BM = 128;            // rows of A per tile (UMMA M)
 constexpr int BN = 256;            // rows of B per tile (UMMA N)
-constexpr int BK = 64;             // K elements per stage (128 bytes of BF16: one swizzle row)
+constexpr int BKB = 128;           // K bytes per stage (one swizzle row): 64 BF16 / 32 TF32
 constexpr int NST = 3;             // pipeline stages
-constexpr int A_BYTES = BM * BK * 2;
-constexpr int B_BYTES = BN * BK * 2;
+constexpr int A_BYTES = BM * BKB;
+constexpr int B_BYTES = BN * BKB;
 constexpr int STAGE_BYTES = A_BYTES + B_BYTES;
 constexpr uint32_t TMEM_COLS = 512;
 constexpr unsigned long long kTimeoutNs = 2000000000ull;
@@ -105,21 +107,29 @@ __device__ __forceinline__ uint64_t smem_desc(uint32_t saddr) {
   d |= (uint64_t)2 << 61;                          // layout: 128-byte swizzle
   return d;
 }
-// Instruction descriptor, kind::f16: D = F32, A = B = BF16, both K-major, N = 256, M = 128.
-constexpr uint32_t kIdesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(BN >> 3) << 17) |
-                            ((uint32_t)(BM >> 4) << 24);
+// Instruction descriptors: D = F32 (bits 4-5 = 1), A and B formats (bits 7-9, 10-12: BF16 = 1
+// under kind::f16, TF32 = 2 under kind::tf32), both K-major, N >> 3 (bits 17-22), M >> 4
+// (bits 24-28); N = 256, M = 128.
+constexpr uint32_t kIdescShape = ((uint32_t)(BN >> 3) << 17) | ((uint32_t)(BM >> 4) << 24);
+constexpr uint32_t kIdescBf16 = (1u << 4) | (1u << 7) | (1u << 10) | kIdescShape;
+constexpr uint32_t kIdescTf32 = (1u << 4) | (2u << 7) | (2u << 10) | kIdescShape;
 
 __device__ __forceinline__ void umma_bf16(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc, uint32_t accum) {
   asm volatile(
       "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n"
-      ::"r"(tmem_d), "l"(adesc), "l"(bdesc), "r"(kIdesc), "r"(accum));
+      ::"r"(tmem_d), "l"(adesc), "l"(bdesc), "r"(kIdescBf16), "r"(accum));
+}
+__device__ __forceinline__ void umma_tf32(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc, uint32_t accum) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n"
+      ::"r"(tmem_d), "l"(adesc), "l"(bdesc), "r"(kIdescTf32), "r"(accum));
 }
 __device__ __forceinline__ void umma_commit(uint64_t* bar) {
   asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
                : "memory");
 }
-__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
-  uint32_t r[32];
+// Asynchronous TMEM load of 32 columns (one accumulator row per thread) ...
+__device__ __forceinline__ void tmem_ld32_async(uint32_t taddr, uint32_t (&r)[32]) {
   asm volatile(
       "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
       "%15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
@@ -128,7 +138,23 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
         "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
         "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
       : "r"(taddr));
-  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+// ... and the wait for it; the registers are passed through the wait so that no use of them
+// can be scheduled before the load has landed.
+__device__ __forceinline__ void tmem_wait32(uint32_t (&r)[32]) {
+  asm volatile("tcgen05.wait::ld.sync.aligned;"
+               : "+r"(r[0]), "+r"(r[1]), "+r"(r[2]), "+r"(r[3]), "+r"(r[4]), "+r"(r[5]), "+r"(r[6]), "+r"(r[7]),
+                 "+r"(r[8]), "+r"(r[9]), "+r"(r[10]), "+r"(r[11]), "+r"(r[12]), "+r"(r[13]), "+r"(r[14]),
+                 "+r"(r[15]), "+r"(r[16]), "+r"(r[17]), "+r"(r[18]), "+r"(r[19]), "+r"(r[20]), "+r"(r[21]),
+                 "+r"(r[22]), "+r"(r[23]), "+r"(r[24]), "+r"(r[25]), "+r"(r[26]), "+r"(r[27]), "+r"(r[28]),
+                 "+r"(r[29]), "+r"(r[30]), "+r"(r[31])
+               :
+               : "memory");
+}
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
+  uint32_t r[32];
+  tmem_ld32_async(taddr, r);
+  tmem_wait32(r);
 #pragma unroll
   for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
 }
@@ -136,6 +162,7 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
 // ------------------------------------------------------------------------ kernel
 struct UmmaArgs {
   int mode;
+  int tf32;       // operands: 0 BF16 (kind::f16), 1 TF32 held as FP32 (kind::tf32)
   int n;          // rows of B (columns of S)
   int d;
   int a_rows;     // rows of A (POOL: rows owning pools; DIST: nq; BAND: band capacity)
@@ -191,12 +218,12 @@ umma_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
   extern __shared__ __align__(1024) unsigned char dyn_raw[];
   unsigned char* dyn = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(dyn_raw) + 1023) & ~uintptr_t(1023));
   unsigned char* stages = dyn;                                        // NST * STAGE_BYTES
-  float* qv = reinterpret_cast<float*>(dyn + NST * STAGE_BYTES);     // [2][BM][kQCap]
-  int* qi = reinterpret_cast<int*>(qv + 2 * BM * kQCap);
+  float2* qs = reinterpret_cast<float2*>(dyn + NST * STAGE_BYTES);   // [2][BM][kQCap] queues
   __shared__ Bars bars;
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int kb_count = (a.d + BK - 1) / BK;
+  const int bk = a.tf32 ? BKB / 4 : BKB / 2;  // K elements per stage
+  const int kb_count = (a.d + bk - 1) / bk;
 
   Tiles tl;
   if (a.mode == POOL) tl.count = max(0, min(a.tps, (a.n + BN - 1) / BN - (int)blockIdx.y * a.tps));
@@ -242,8 +269,8 @@ umma_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
           if (!mbar_wait(&bars.empty[s], (round & 1) ^ 1, abort_flag)) break;
           unsigned char* sa = stages + s * STAGE_BYTES;
           mbar_arrive_expect_tx(&bars.full[s], STAGE_BYTES);
-          tma_load_2d(sa, &tmA, &bars.full[s], kb * BK, r0);
-          tma_load_2d(sa + A_BYTES, &tmB, &bars.full[s], kb * BK, c0);
+          tma_load_2d(sa, &tmA, &bars.full[s], kb * bk, r0);
+          tma_load_2d(sa + A_BYTES, &tmB, &bars.full[s], kb * bk, c0);
         }
       }
       // in-flight loads land before the CTA can exit: wait for the last armed stages
@@ -273,9 +300,14 @@ umma_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
           tc_fence_after();
           const uint32_t sa = smem_u32(stages + s * STAGE_BYTES);
           const uint64_t ad = smem_desc(sa), bd = smem_desc(sa + A_BYTES);
+          // four MMAs per stage, +32 bytes (K=16 BF16 or K=8 TF32) inside the swizzle row
+          if (a.tf32) {
 #pragma unroll
-          for (int k = 0; k < BK / 16; ++k)  // +32 bytes per K=16 step inside the swizzle row
-            umma_bf16(dcol, ad + (uint64_t)(2 * k), bd + (uint64_t)(2 * k), (kb | k) != 0);
+            for (int k = 0; k < 4; ++k) umma_tf32(dcol, ad + (uint64_t)(2 * k), bd + (uint64_t)(2 * k), (kb | k) != 0);
+          } else {
+#pragma unroll
+            for (int k = 0; k < 4; ++k) umma_bf16(dcol, ad + (uint64_t)(2 * k), bd + (uint64_t)(2 * k), (kb | k) != 0);
+          }
           umma_commit(&bars.empty[s]);
         }
         if (ok) umma_commit(&bars.tfull[buf]);
@@ -340,9 +372,10 @@ umma_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
           if (kind == 0 || CROSS) {
             int ccam = 0;
             if (CROSS && kind == 1) ccam = (cb + lane < a.n) ? a.cam[cb + lane] : -1;
+            float2* myq = qs + qrow * kQCap;
 #pragma unroll
             for (int g = 0; g < 4; ++g) {
-              pool_make_room<KP>(8, lane, me, blockIdx.x * BM + quad * 32, kind * BM + quad * 32, qv, qi, pv, pi);
+              pool_make_room<KP>(8, lane, me, blockIdx.x * BM + quad * 32, kind * BM + quad * 32, qs, pv, pi);
 #pragma unroll
               for (int c = 0; c < 8; ++c) {
                 const int cc = g * 8 + c;
@@ -351,7 +384,7 @@ umma_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
                 const int cj = __shfl_sync(GCR_FULL, ccam, cc);
                 bool ok = j < a.n && !(a.self_excl && j == my_row);
                 if (CROSS && kind == 1) ok = ok && cj != my_cam;
-                pool_push(me, v[cc], j, ok, qv + qrow * kQCap, qi + qrow * kQCap, sw);
+                pool_push(me, v[cc], j, ok, myq, sw);
               }
             }
           }
@@ -391,7 +424,7 @@ umma_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
       if (lane == 0) mbar_arrive(&bars.tempty[buf]);
     }
     if (a.mode == POOL && (kind == 0 || CROSS) && !*abort_flag)
-      pool_flush<KP>(lane, my_row < a.a_rows, me, blockIdx.x * BM + quad * 32, kind * BM + quad * 32, qv, qi, pv, pi);
+      pool_flush<KP>(lane, my_row < a.a_rows, me, blockIdx.x * BM + quad * 32, kind * BM + quad * 32, qs, pv, pi);
   }
   tc_fence_before();
   __syncthreads();
@@ -437,16 +470,19 @@ EncodeTiledFn encode_fn() {
   return fn;
 }
 
-// Row-major BF16 matrix [rows][d] viewed as a 2-D tensor, box = 64 (K) x box_rows.
-cudaError_t make_map(CUtensorMap* m, const __nv_bfloat16* base, int rows, int d, int box_rows) {
+// Row-major matrix [rows][d] (BF16, or TF32 held as FP32) viewed as a 2-D tensor, box = 128
+// bytes of K x box_rows; K past d reads as zero.
+cudaError_t make_map(CUtensorMap* m, const void* base, Elt elt, int rows, int d, int box_rows) {
   EncodeTiledFn fn = encode_fn();
   if (!fn) return cudaErrorNotSupported;
-  if ((reinterpret_cast<uintptr_t>(base) & 15) || (d % 8)) return cudaErrorInvalidValue;
+  const size_t es = elt_bytes(elt);
+  if ((reinterpret_cast<uintptr_t>(base) & 15) || ((size_t)d * es) % 16) return cudaErrorInvalidValue;
   cuuint64_t dims[2] = {(cuuint64_t)d, (cuuint64_t)rows};
-  cuuint64_t strides[1] = {(cuuint64_t)d * 2};
-  cuuint32_t box[2] = {(cuuint32_t)BK, (cuuint32_t)box_rows};
+  cuuint64_t strides[1] = {(cuuint64_t)(d * es)};
+  cuuint32_t box[2] = {(cuuint32_t)(BKB / es), (cuuint32_t)box_rows};
   cuuint32_t estr[2] = {1, 1};
-  CUresult r = fn(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<__nv_bfloat16*>(base), dims, strides, box, estr,
+  CUresult r = fn(m, elt == Elt::TF32 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2,
+                  const_cast<void*>(base), dims, strides, box, estr,
                   CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                   CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
@@ -482,13 +518,13 @@ int umma_read_and_clear_timeouts() {
   return h;
 }
 
-cudaError_t launch_umma_pool(const __nv_bfloat16* Ab, int na, const __nv_bfloat16* Bb, int nb, int d,
+cudaError_t launch_umma_pool(const void* Ab, int na, const void* Bb, int nb, int d, Elt elt,
                              const int* cam, bool cross, int self_excl, int kp, int splits, float* pool_v,
                              int* pool_i, cudaStream_t st) {
   CUtensorMap ta, tb;
-  cudaError_t e = make_map(&ta, Ab, na, d, BM);
+  cudaError_t e = make_map(&ta, Ab, elt, na, d, BM);
   if (e != cudaSuccess) return e;
-  e = make_map(&tb, Bb, nb, d, BN);
+  e = make_map(&tb, Bb, elt, nb, d, BN);
   if (e != cudaSuccess) return e;
   const int ntiles = (nb + BN - 1) / BN;
   if (splits < 1) splits = 1;
@@ -497,6 +533,7 @@ cudaError_t launch_umma_pool(const __nv_bfloat16* Ab, int na, const __nv_bfloat1
   splits = (ntiles + tps - 1) / tps;  // no split is left without a column tile
   UmmaArgs a{};
   a.mode = POOL;
+  a.tf32 = elt == Elt::TF32;
   a.n = nb;
   a.d = d;
   a.a_rows = na;
@@ -506,22 +543,24 @@ cudaError_t launch_umma_pool(const __nv_bfloat16* Ab, int na, const __nv_bfloat1
   a.pool_v = pool_v;
   a.pool_i = pool_i;
   dim3 grid((na + BM - 1) / BM, splits);
+  if (kp == 32) return cross ? launch<32, true>(ta, tb, a, grid, st) : launch<32, false>(ta, tb, a, grid, st);
   if (kp == 64) return cross ? launch<64, true>(ta, tb, a, grid, st) : launch<64, false>(ta, tb, a, grid, st);
   if (kp == 128) return cross ? launch<128, true>(ta, tb, a, grid, st) : launch<128, false>(ta, tb, a, grid, st);
   return cudaErrorInvalidValue;
 }
 
-cudaError_t launch_umma_band(const __nv_bfloat16* Xb, int n, int d, const int* cam, int self_excl,
-                             const __nv_bfloat16* Ab, const int* count, int cap, const int* band_row,
+cudaError_t launch_umma_band(const void* Xb, int n, int d, Elt elt, const int* cam, int self_excl,
+                             const void* Ab, const int* count, int cap, const int* band_row,
                              const int* band_kind, const float* band_thr, int bcap, int* band_cnt, float* band_v,
                              int* band_i, cudaStream_t st) {
   CUtensorMap ta, tb;
-  cudaError_t e = make_map(&ta, Ab, cap, d, BM);
+  cudaError_t e = make_map(&ta, Ab, elt, cap, d, BM);
   if (e != cudaSuccess) return e;
-  e = make_map(&tb, Xb, n, d, BN);
+  e = make_map(&tb, Xb, elt, n, d, BN);
   if (e != cudaSuccess) return e;
   UmmaArgs a{};
   a.mode = BAND;
+  a.tf32 = elt == Elt::TF32;
   a.n = n;
   a.d = d;
   a.a_rows = cap;
@@ -543,9 +582,9 @@ cudaError_t launch_umma_band(const __nv_bfloat16* Xb, int n, int d, const int* c
 cudaError_t launch_umma_dist(const __nv_bfloat16* Qb, int nq, const __nv_bfloat16* Gb, int ng, int d,
                              const float* nrm_q, const float* nrm_g, float* D, cudaStream_t st) {
   CUtensorMap ta, tb;
-  cudaError_t e = make_map(&ta, Qb, nq, d, BM);
+  cudaError_t e = make_map(&ta, Qb, Elt::BF16, nq, d, BM);
   if (e != cudaSuccess) return e;
-  e = make_map(&tb, Gb, ng, d, BN);
+  e = make_map(&tb, Gb, Elt::BF16, ng, d, BN);
   if (e != cudaSuccess) return e;
   UmmaArgs a{};
   a.mode = DIST;

@@ -81,7 +81,8 @@ def test_workspace_queries(lib):
 
 
 @pytest.mark.parametrize("bad", [dict(k=-1), dict(k=32), dict(gamma=0.0), dict(gamma=-1.0),
-                                 dict(cross_camera=1, alpha=1.5), dict(precision=7), dict(pool=48), dict(pool=256),
+                                 dict(cross_camera=1, alpha=1.5), dict(precision=7), dict(precision=3), dict(pool=48),
+                                 dict(pool=256),
                                  dict(symmetric=2)])
 def test_invalid_params_rejected_on_host(lib, bad):
     p = _params(lib, **bad)
@@ -102,6 +103,26 @@ def test_unsupported_shapes(lib):
     assert lib.gcr_build_graph(ctypes.c_void_p(16), 100, 12, None, ctypes.byref(pb), ctypes.byref(g),
                                ctypes.c_void_p(16), 1 << 30, None) == 5
     assert lib.gcr_rerank_workspace_size(10, 20000, 256, ctypes.byref(p)) == 0
+    # TF32 operands: rows of d % 8 == 0 (the distance GEMM shares the compensated BF16 operands);
+    # a 32-entry pool is allowed under TF32, not under BF16
+    pt = _params(lib, k=10, precision=2)
+    assert lib.gcr_build_graph(ctypes.c_void_p(16), 100, 12, None, ctypes.byref(pt), ctypes.byref(g),
+                               ctypes.c_void_p(16), 1 << 30, None) == 5
+    assert lib.gcr_build_graph_workspace_size(100, 16, ctypes.byref(pt)) > 0
+    assert lib.gcr_rerank_workspace_size(10, 100, 12, ctypes.byref(pt)) == 0
+    pb32 = _params(lib, k=10, precision=1, pool=32)
+    assert lib.gcr_build_graph(ctypes.c_void_p(16), 100, 16, None, ctypes.byref(pb32), ctypes.byref(g),
+                               ctypes.c_void_p(16), 1 << 30, None) == 5
+    assert lib.gcr_build_graph_workspace_size(100, 16, ctypes.byref(_params(lib, k=10, precision=2, pool=32))) > 0
+
+
+def test_tf32_operand_copy_is_larger_than_bf16(lib):
+    # the rounded operand copy holds 4 bytes per element under TF32, 2 under BF16
+    pb = _params(lib, k=10, precision=1)
+    pt = _params(lib, k=10, precision=2)
+    wb = lib.gcr_build_graph_workspace_size(1000, 256, ctypes.byref(pb))
+    wt = lib.gcr_build_graph_workspace_size(1000, 256, ctypes.byref(pt))
+    assert wt - wb >= 1000 * 256 * 2
 
 
 def test_null_and_short_workspace(lib):

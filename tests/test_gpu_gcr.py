@@ -19,8 +19,9 @@ from tests import parity
 
 pytestmark = pytest.mark.gpu
 
-PRECISIONS = ["fp32", "bf16"]
-DIST_TOL = {"fp32": 1e-4, "bf16": 2e-3}
+PRECISIONS = ["fp32", "bf16", "tf32"]
+# the tensor-core modes share the compensated BF16 distance GEMM
+DIST_TOL = {"fp32": 1e-4, "bf16": 2e-3, "tf32": 2e-3}
 
 
 @pytest.fixture(scope="module")
@@ -68,12 +69,12 @@ def test_knn_plain_workload(gcr, precision):
     assert st["rows"] == w.n and st["band_failed"] == 0
 
 
-@pytest.mark.parametrize("precision", PRECISIONS)
-def test_knn_cross_camera(gcr, precision):
+@pytest.mark.parametrize("precision,pool", [(p, 0) for p in PRECISIONS] + [("tf32", 32)])
+def test_knn_cross_camera(gcr, precision, pool):
     w = workloads.crosscam(seed=3, n_query=400, n_gallery=2600, d=256, n_clusters=120)
     X0 = gcr.gcr_normalize(_dev(w.X))
     cam = _dev(w.cam, torch.int32)
-    p = gcr.default_params(k=w.k, cross_camera=1, alpha=0.7, precision=precision)
+    p = gcr.default_params(k=w.k, cross_camera=1, alpha=0.7, precision=precision, pool=pool)
     G = gcr.gcr_build_graph(X0, p, cam)
     torch.cuda.synchronize()
     X64 = X0.double().cpu().numpy()
@@ -87,7 +88,9 @@ def test_knn_cross_camera(gcr, precision):
 
 EDGE = [("fp32", 1, 8, 5), ("fp32", 5, 12, 10), ("fp32", 130, 68, 7), ("fp32", 300, 256, 0),
         ("fp32", 257, 36, 31), ("bf16", 1, 8, 5), ("bf16", 5, 16, 10), ("bf16", 130, 72, 7),
-        ("bf16", 300, 256, 0), ("bf16", 257, 40, 31), ("bf16", 600, 200, 63)]
+        ("bf16", 300, 256, 0), ("bf16", 257, 40, 31), ("bf16", 600, 200, 63), ("tf32", 1, 8, 5),
+        ("tf32", 129, 24, 10), ("tf32", 130, 72, 7), ("tf32", 300, 256, 0), ("tf32", 257, 40, 31),
+        ("tf32", 600, 200, 63)]
 
 
 @pytest.mark.parametrize("precision,n,d,k", EDGE)
@@ -95,7 +98,7 @@ def test_knn_edge_shapes(gcr, precision, n, d, k):
     X, cam = workloads.random_unit_like(n, n, d, cams=3)
     X0 = gcr.gcr_normalize(_dev(X))
     p = gcr.default_params(k=k, cross_camera=1, alpha=0.5, precision=precision)
-    if k >= 32 or precision == "bf16":
+    if k >= 32 or precision != "fp32":
         p.pool = 64
     G = gcr.gcr_build_graph(X0, p, _dev(cam, torch.int32))
     torch.cuda.synchronize()
@@ -189,6 +192,32 @@ def test_rerank_matches_oracle(gcr, precision, topk):
     sep[:, 1:] &= np.diff(o_d, axis=1) > 2 * tol
     sep[:, :-1] &= np.diff(o_d, axis=1) > 2 * tol
     assert np.all(idx[sep] == o_idx[sep])
+
+
+@pytest.mark.parametrize("ng", [2047, 2048, 3001, 4096, 4100, 8193, 16384])
+def test_rerank_sort_sizes_and_ties(gcr, ng):
+    """The full ranking across the sort's size classes (bitonic below 2048 keys, radix at and
+    above), with exact duplicates in the gallery: the returned distances are non-decreasing,
+    equal distances come in increasing gallery index, every gallery row appears once, and the
+    distances match FP64 within the FP32 bound."""
+    rng = np.random.default_rng(ng)
+    d, nq = 64, 9
+    G = rng.standard_normal((ng, d)).astype(np.float32)
+    dup = rng.choice(ng, ng // 5, replace=False)
+    G[dup] = G[rng.integers(0, ng, dup.size)]          # exact ties between gallery rows
+    Q = rng.standard_normal((nq, d)).astype(np.float32)
+    Q[0] = G[3]                                          # a query equal to a gallery row
+    Xq = gcr.gcr_normalize(_dev(Q))
+    Xg = gcr.gcr_normalize(_dev(G))
+    idx, dist = gcr.gcr_rerank(Xq, Xg, gcr.default_params(topk_out=0))
+    torch.cuda.synchronize()
+    idx, dist = idx.cpu().numpy(), dist.cpu().numpy()
+    assert np.all(np.sort(idx, axis=1) == np.arange(ng)[None, :])
+    step = np.diff(dist, axis=1)
+    assert np.all(step >= 0)
+    assert np.all(np.diff(idx, axis=1)[step == 0] > 0)
+    err, _ = parity.ranking_errors(Xq.double().cpu().numpy(), Xg.double().cpu().numpy(), idx, dist)
+    assert err < DIST_TOL["fp32"]
 
 
 @pytest.mark.parametrize("precision", PRECISIONS)

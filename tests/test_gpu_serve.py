@@ -15,7 +15,7 @@ import workloads
 
 pytestmark = pytest.mark.gpu
 
-PRECISIONS = ["fp32", "bf16"]
+PRECISIONS = ["fp32", "bf16", "tf32"]
 
 
 @pytest.fixture(scope="module")
