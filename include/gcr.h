@@ -69,7 +69,7 @@ typedef struct {
   int32_t cross_camera; /* 1: add the cross-camera graph (Eq. 8) and mix by Eq. 9         */
   int32_t precision;    /* gcr_precision                                                  */
   int32_t pool;         /* per-row candidate pool of the streaming kNN search: 32, 64 or
-                           128; 0 picks 32 for FP32 and 64 for BF16 and TF32 (BF16
+                           128; 0 picks 32 for FP32 and TF32, 64 for BF16 (BF16
                            needs >= 64);
                            must exceed k. A larger pool certifies more rows without the
                            threshold rescan at the cost of a busier GEMM epilogue.        */

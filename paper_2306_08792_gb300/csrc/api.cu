@@ -73,7 +73,7 @@ int check_params(const gcr_params* p, int64_t n, int32_t d, Resolved* r) {
   if (p->symmetric != 0 && p->symmetric != 1) return GCR_E_INVALID;
   if (p->cross_camera != 0 && p->cross_camera != 1) return GCR_E_INVALID;
   if (p->cross_camera && !(p->alpha >= 0.f && p->alpha <= 1.f)) return GCR_E_INVALID;
-  int kp = p->pool ? p->pool : (tensor_mode(p) ? 64 : 32);
+  int kp = p->pool ? p->pool : (p->precision == GCR_PREC_BF16 ? 64 : 32);
   if (kp != 32 && kp != 64 && kp != 128) return GCR_E_INVALID;
   if (p->k < 0 || p->k >= kp) return GCR_E_INVALID;
   // the BF16 rounding bound is too loose for a 32-entry pool to certify most rows
@@ -114,6 +114,7 @@ struct BuildWs {
   float* raw_val;
   int* op_cnt;
   int* scan_tmp;
+  double* inv;
   unsigned long long* stats;
   int* err;
   int* okey;
@@ -157,6 +158,7 @@ size_t carve_build(Carve& c, int64_t n, int32_t d, const gcr_params* p, const Re
   t.raw_val = c.take<float>(cap);
   t.op_cnt = c.take<int>(nn);
   t.scan_tmp = c.take<int>(nn + 1);
+  t.inv = c.take<double>((size_t)2 * kinds * nn);
   t.stats = c.take<unsigned long long>(GCR_STATS_LEN);
   t.err = c.take<int>(4);
   t.okey = c.take<int>(nn);
@@ -252,8 +254,9 @@ int build_graph_impl(const float* X, int64_t n64_, int32_t d, const int32_t* cam
   }
   ga.op_rowptr = g->op_rowptr; ga.op_len = g->op_len; ga.op_col = g->op_col; ga.op_val = g->op_val;
   ga.raw_col = w.raw_col; ga.raw_val = w.raw_val; ga.op_cnt = w.op_cnt; ga.scan_tmp = w.scan_tmp;
+  ga.inv = w.inv;
   {
-    StageScope sc_(GCR_STAGE_GRAPH, st, 4 * kinds + 3);
+    StageScope sc_(GCR_STAGE_GRAPH, st, 5 * kinds + 3);
     GCR_CUDA_TRY(launch_build_operator(ga, st));
   }
   return GCR_OK;
@@ -496,7 +499,7 @@ int split_count(int want, int ntiles) {
 
 int serve_kp_final(const gcr_params* p) {
   const int K = p->topk_out;
-  if (p->precision == GCR_PREC_FP32 && K < 32) return 32;
+  if (p->precision != GCR_PREC_BF16 && K < 32) return 32;
   return K < 64 ? 64 : 128;
 }
 

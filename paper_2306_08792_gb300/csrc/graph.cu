@@ -197,6 +197,8 @@ struct OpArgs {
   const int* tptr[2];
   const int* tsrc[2];
   const float* tw[2];
+  const double* inv_r[2];  // per graph: 1/sqrt(D_i) (Eq. 7, D the mean of row and column
+  const double* inv_c[2];  // degrees) in both, or 1/sqrt(D_r,i) and 1/sqrt(D_c,i) (Eq. 6)
   const int* rowptr;
   int* len;
   int* col;
@@ -205,8 +207,21 @@ struct OpArgs {
   float* raw_val;
 };
 
-__device__ __forceinline__ double degree_sym(const OpArgs& a, int g, int i) {
-  return 0.5 * ((double)a.deg_r[g][i] + (double)a.deg_c[g][i]);
+// Inverse square roots of the degrees, once per row and graph (FP64): every operator entry
+// is then a product, without a square root or division per entry.
+__global__ void inv_sqrt_degree_kernel(int n, int symmetric, const float* __restrict__ deg_r,
+                                       const float* __restrict__ deg_c, double* __restrict__ inv_r,
+                                       double* __restrict__ inv_c) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  if (symmetric) {
+    const double r = 1.0 / sqrt(0.5 * ((double)deg_r[i] + (double)deg_c[i]));
+    inv_r[i] = r;
+    inv_c[i] = r;
+  } else {
+    inv_r[i] = 1.0 / sqrt((double)deg_r[i]);
+    inv_c[i] = 1.0 / sqrt((double)deg_c[i]);
+  }
 }
 
 __global__ void op_count_kernel(OpArgs a, int* __restrict__ cnt) {
@@ -224,16 +239,15 @@ __global__ void op_count_kernel(OpArgs a, int* __restrict__ cnt) {
 // N_i entries (rank order) and, when symmetric, its transposed entries (by source).
 __device__ __forceinline__ void gen_entry(const OpArgs& a, int i, int e, int& col, double& v) {
   // e == 0: self loop
+  // self loop: A~_ii = 1, scaled by 1/D_i (Eq. 7) or 1/sqrt(D_r,i D_c,i) (Eq. 6)
   if (e == 0) {
     double s = 0.0;
-    for (int g = 0; g < a.kinds; ++g) {
-      if (a.symmetric) s += a.coef[g] / degree_sym(a, g, i);
-      else s += a.coef[g] / sqrt((double)a.deg_r[g][i] * (double)a.deg_c[g][i]);
-    }
+    for (int g = 0; g < a.kinds; ++g) s += a.coef[g] * (a.inv_r[g][i] * a.inv_c[g][i]);
     col = i;
     v = s;
     return;
   }
+  const double half = a.symmetric ? 0.5 : 1.0;  // (A~ + A~^T) / 2 in Eq. 7
   int r = e - 1;
   for (int g = 0; g < a.kinds; ++g) {
     if (r < a.k) {
@@ -241,8 +255,7 @@ __device__ __forceinline__ void gen_entry(const OpArgs& a, int i, int e, int& co
       const double wij = a.w[g][(size_t)i * a.k + r];
       if (j < 0) { col = -1; v = 0.0; return; }
       col = j;
-      if (a.symmetric) v = a.coef[g] * 0.5 * wij / sqrt(degree_sym(a, g, i) * degree_sym(a, g, j));
-      else v = a.coef[g] * wij / sqrt((double)a.deg_r[g][i] * (double)a.deg_c[g][j]);
+      v = a.coef[g] * half * wij * (a.inv_r[g][i] * a.inv_c[g][j]);
       return;
     }
     r -= a.k;
@@ -252,7 +265,7 @@ __device__ __forceinline__ void gen_entry(const OpArgs& a, int i, int e, int& co
         const int s = a.tsrc[g][tb + r];
         const double wsi = a.tw[g][tb + r];
         col = s;
-        v = a.coef[g] * 0.5 * wsi / sqrt(degree_sym(a, g, i) * degree_sym(a, g, s));
+        v = a.coef[g] * 0.5 * wsi * (a.inv_r[g][i] * a.inv_c[g][s]);
         return;
       }
       r -= tl;
@@ -376,7 +389,13 @@ cudaError_t launch_build_operator(const GraphArgs& g, cudaStream_t st) {
     const int qq = q < g.kinds ? q : 0;
     a.nbr[q] = g.nbr[qq]; a.w[q] = g.w[qq]; a.deg_r[q] = g.deg_r[qq]; a.deg_c[q] = g.deg_c[qq];
     a.tptr[q] = g.cnt[qq]; a.tsrc[q] = g.t_src[qq]; a.tw[q] = g.t_w[qq];
+    a.inv_r[q] = g.inv + (size_t)(2 * qq) * n;
+    a.inv_c[q] = g.inv + (size_t)(2 * qq + 1) * n;
   }
+  for (int q = 0; q < g.kinds; ++q)
+    inv_sqrt_degree_kernel<<<(n + 255) / 256, 256, 0, st>>>(n, g.symmetric, g.deg_r[q], g.deg_c[q],
+                                                            g.inv + (size_t)(2 * q) * n,
+                                                            g.inv + (size_t)(2 * q + 1) * n);
   a.rowptr = g.op_rowptr; a.len = g.op_len; a.col = g.op_col; a.val = g.op_val;
   a.raw_col = g.raw_col; a.raw_val = g.raw_val;
   op_count_kernel<<<(n + 255) / 256, 256, 0, st>>>(a, g.op_cnt);

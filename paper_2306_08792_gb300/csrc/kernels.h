@@ -115,6 +115,7 @@ struct GraphArgs {
   float* raw_val;           // [op_cap] scratch
   int* op_cnt;              // [n] scratch
   int* scan_tmp;            // [n+1] scratch
+  double* inv;              // [2*kinds][n] scratch: inverse square roots of the degrees
 };
 cudaError_t launch_build_operator(const GraphArgs& g, cudaStream_t st);
 cudaError_t launch_scan(const int* in, int* out, int n, cudaStream_t st);

@@ -69,7 +69,7 @@ def test_knn_plain_workload(gcr, precision):
     assert st["rows"] == w.n and st["band_failed"] == 0
 
 
-@pytest.mark.parametrize("precision,pool", [(p, 0) for p in PRECISIONS] + [("tf32", 32)])
+@pytest.mark.parametrize("precision,pool", [(p, 0) for p in PRECISIONS] + [("tf32", 64)])
 def test_knn_cross_camera(gcr, precision, pool):
     w = workloads.crosscam(seed=3, n_query=400, n_gallery=2600, d=256, n_clusters=120)
     X0 = gcr.gcr_normalize(_dev(w.X))
