@@ -213,6 +213,21 @@ int gcr_pipeline(const float* X, int64_t n, int64_t nq, int32_t d, const int32_t
                  const gcr_params* p, float* X_final, int32_t* idx_out, float* dist_out,
                  int64_t* stats, void* ws, size_t ws_bytes, gcr_stream_t stream);
 
+/* The same re-ranking from and to host memory. X_host (float32 [n][d]) and cam_host
+ * (int32 [n], when cross_camera = 1) are copied to the device on `stream`; the ranking
+ * (idx_host int32 / dist_host float32, [nq][K] as in gcr_rerank) is copied back in up to 8
+ * chunks of queries, each chunk as soon as it is sorted, on a second stream so that the
+ * copies overlap the re-ranking of the later chunks; `stream` then waits for the last copy,
+ * so a synchronisation of `stream` covers the whole call. Host buffers should be
+ * page-locked (cudaHostAlloc / cudaHostRegister) for the copies to run asynchronously. The
+ * copy stream and its events are created on the first call per device and kept until the
+ * process exits; calls are serialised on them (a host mutex while enqueuing). stats: device
+ * pointer or NULL. No counterpart in the paper (its implementation runs on the CPU). */
+size_t gcr_pipeline_host_workspace_size(int64_t n, int64_t nq, int32_t d, const gcr_params* p);
+int gcr_pipeline_host(const float* X_host, int64_t n, int64_t nq, int32_t d, const int32_t* cam_host,
+                      const gcr_params* p, int32_t* idx_host, float* dist_host, int64_t* stats,
+                      void* ws, size_t ws_bytes, gcr_stream_t stream);
+
 /* ------------------------------------------------------------------ S8: GCRV profiles
  * Profile vectors of Sec. III-D for video re-ranking (Algorithm 2 step 1):
  *   mu_c = mean of tracklet c's L2-normalised frames                              (Eq. 10)

@@ -227,6 +227,39 @@ class Pipeline:
         return {name: int(v[i]) for i, name in enumerate(_lib.STAT_NAMES)}
 
 
+class HostPipeline:
+    """gcr_pipeline_host: the re-ranking from page-locked host inputs to page-locked host
+    outputs, the ranking's copies overlapped with the re-ranking of later query chunks."""
+
+    def __init__(self, n: int, nq: int, d: int, p: Params, device="cuda"):
+        self.n, self.nq, self.d, self.p = n, nq, d, p
+        lib = _lib.load()
+        need = lib.gcr_pipeline_host_workspace_size(n, nq, d, ctypes.byref(p))
+        if need == 0:
+            raise GcrError(_lib.GCR_E_INVALID, "gcr_pipeline_host_workspace_size")
+        ng = n - nq
+        K = min(p.topk_out, ng) if p.topk_out > 0 else ng
+        self.ws = torch.empty(need, dtype=torch.uint8, device=device)
+        self.idx = torch.empty(nq, K, dtype=torch.int32).pin_memory()
+        self.dist = torch.empty(nq, K, dtype=torch.float32).pin_memory()
+        self.stats = torch.zeros(_lib.GCR_STATS_LEN, dtype=torch.int64, device=device)
+
+    def __call__(self, X: torch.Tensor, cam: Optional[torch.Tensor] = None, stream=None):
+        """X: float32 [n, d] and cam: int32 [n] on the host (page-locked for asynchronous
+        copies). Returns the host (idx, dist) buffers, complete once `stream` is synchronised."""
+        if X.is_cuda or X.dtype != torch.float32 or X.dim() != 2 or not X.is_contiguous():
+            raise ValueError("X must be a contiguous float32 host matrix")
+        if cam is not None and (cam.is_cuda or cam.dtype != torch.int32 or not cam.is_contiguous()):
+            raise ValueError("cam must be a contiguous int32 host vector")
+        lib = _lib.load()
+        _check(lib.gcr_pipeline_host(ctypes.c_void_p(X.data_ptr()), self.n, self.nq, self.d,
+                                     ctypes.c_void_p(cam.data_ptr() if cam is not None else 0), ctypes.byref(self.p),
+                                     ctypes.c_void_p(self.idx.data_ptr()), ctypes.c_void_p(self.dist.data_ptr()),
+                                     _ptr(self.stats), _ptr(self.ws), self.ws.numel(), _stream(stream)),
+               "gcr_pipeline_host")
+        return self.idx, self.dist
+
+
 def gcr_pipeline(X: torch.Tensor, nq: int, p: Params, cam: Optional[torch.Tensor] = None, stream=None):
     """One-shot wrapper of :class:`Pipeline`; returns (idx, dist, X_T, stats)."""
     n, d = X.shape

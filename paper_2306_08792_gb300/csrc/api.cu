@@ -5,6 +5,7 @@
 // device memory or synchronises (except gcr_sync).
 #include <cmath>
 #include <cstring>
+#include <mutex>
 
 #include "common.cuh"
 #include "kernels.h"
@@ -306,8 +307,20 @@ size_t carve_rerank(Carve& c, int64_t nq, int64_t ng, int32_t d, bool bf, Rerank
   return c.off;
 }
 
+// Optional delivery of the ranking to host memory in query chunks: after each chunk is
+// sorted, its rows are copied on a second stream while the next chunks are computed.
+struct HostDelivery {
+  int32_t* idx_host;
+  float* dist_host;
+  int chunk_rows;         // queries per chunk (a multiple of the GEMM's 128-row tile)
+  cudaStream_t copy;      // copy stream
+  cudaEvent_t* ready;     // one event per chunk
+  int n_events;
+};
+
 int rerank_impl(const float* Xq, int64_t nq, const float* Xg, int64_t ng, int32_t d, const gcr_params* p,
-                int32_t* idx_out, float* dist_out, const RerankWs& w, cudaStream_t st) {
+                int32_t* idx_out, float* dist_out, const RerankWs& w, cudaStream_t st,
+                const HostDelivery* hd = nullptr) {
   // the distance GEMM of both tensor-core modes runs on compensated BF16 operands
   const bool bf = tensor_mode(p);
   const int K = p->topk_out > 0 ? (int)std::min<int64_t>(p->topk_out, ng) : (int)ng;
@@ -323,17 +336,34 @@ int rerank_impl(const float* Xq, int64_t nq, const float* Xg, int64_t ng, int32_
     }
   }
   if (bf) GCR_CUDA_TRY(cudaMemsetAsync(w.err, 0, sizeof(int) * 4, st));
-  {
-    StageScope sc_(GCR_STAGE_DIST_GEMM, st);
-    if (bf) {
-    GCR_CUDA_TRY(launch_umma_dist(w.qb, (int)nq, w.gb, (int)ng, 3 * d, w.nq, w.ng, w.D, st));
-  } else {
-    GCR_CUDA_TRY(launch_sgemm_dist(Xq, (int)nq, Xg, (int)ng, d, w.nq, w.ng, w.D, st));
-  }
-  }
-  {
-    StageScope sc_(GCR_STAGE_SORT, st);
-    GCR_CUDA_TRY(launch_rank_rows(w.D, (int)nq, (int)ng, K, idx_out, dist_out, st));
+  const int64_t chunk = hd ? hd->chunk_rows : nq;
+  for (int64_t q0 = 0, c = 0; q0 < nq; q0 += chunk, ++c) {
+    const int nc = (int)std::min<int64_t>(chunk, nq - q0);
+    {
+      StageScope sc_(GCR_STAGE_DIST_GEMM, st);
+      if (bf) {
+        GCR_CUDA_TRY(launch_umma_dist(w.qb + (size_t)q0 * 3 * d, nc, w.gb, (int)ng, 3 * d, w.nq + q0, w.ng,
+                                      w.D + (size_t)q0 * ng, st));
+      } else {
+        GCR_CUDA_TRY(launch_sgemm_dist(Xq + (size_t)q0 * d, nc, Xg, (int)ng, d, w.nq + q0, w.ng,
+                                       w.D + (size_t)q0 * ng, st));
+      }
+    }
+    {
+      StageScope sc_(GCR_STAGE_SORT, st);
+      GCR_CUDA_TRY(launch_rank_rows(w.D + (size_t)q0 * ng, nc, (int)ng, K, idx_out + (size_t)q0 * K,
+                                    dist_out + (size_t)q0 * K, st));
+    }
+    if (hd) {
+      if (c >= hd->n_events) return GCR_E_INVALID;
+      const size_t off = (size_t)q0 * K, cnt = (size_t)nc * K;
+      GCR_CUDA_TRY(cudaEventRecord(hd->ready[c], st));
+      GCR_CUDA_TRY(cudaStreamWaitEvent(hd->copy, hd->ready[c], 0));
+      GCR_CUDA_TRY(cudaMemcpyAsync(hd->idx_host + off, idx_out + off, cnt * sizeof(int32_t), cudaMemcpyDeviceToHost,
+                                   hd->copy));
+      GCR_CUDA_TRY(cudaMemcpyAsync(hd->dist_host + off, dist_out + off, cnt * sizeof(float), cudaMemcpyDeviceToHost,
+                                   hd->copy));
+    }
   }
   return GCR_OK;
 }
@@ -650,6 +680,75 @@ int topk_rerank_impl(const float* Xq, int64_t nq, const float* Xg, int64_t ng, i
                    dist_out, st);
 }
 
+// The whole re-ranking on device buffers (gcr_pipeline); hd (may be NULL) delivers the
+// ranking of the full-sort path to host memory chunk by chunk.
+int pipeline_impl(const float* X, int64_t n, int64_t nq, int32_t d, const int32_t* cam, const gcr_params* p,
+                  const Resolved& r, float* X_final, int32_t* idx_out, float* dist_out, int64_t* stats,
+                  PipeWs& w, cudaStream_t st, const HostDelivery* hd) {
+  int s = GCR_OK;
+  w.g.stats = stats;
+  {
+    StageScope sc_(GCR_STAGE_NORMALIZE, st);
+    GCR_CUDA_TRY(launch_normalize(X, w.Xa, n, d, st));
+  }
+  float* cur = w.Xa;
+  float* nxt = w.Xb;
+  for (int t = 0; t < p->T; ++t) {
+    Carve cb(w.inner, w.inner_bytes);
+    BuildWs bw;
+    carve_build(cb, n, d, p, r, &bw);
+    s = build_graph_impl(cur, n, d, cam, p, r, &w.g, bw, st);
+    if (s != GCR_OK) return s;
+    {
+      StageScope sc_(GCR_STAGE_PROPAGATE, st);
+      GCR_CUDA_TRY(launch_propagate(w.g.op_rowptr, w.g.op_len, w.g.op_col, w.g.op_val, cur, nxt, (int)n, d,
+                                    p->k > 0 ? w.g.row_order : nullptr, st));
+    }
+    float* tmp = cur; cur = nxt; nxt = tmp;
+  }
+  Carve cr(w.inner, w.inner_bytes);
+  if (rerank_uses_pool(p, n - nq)) {
+    TopkRerankWs tw;
+    carve_topk_rerank(cr, nq, n - nq, d, p, &tw);
+    s = topk_rerank_impl(cur, nq, cur + (size_t)nq * d, n - nq, d, p, idx_out, dist_out, tw, st);
+  } else {
+    RerankWs rw;
+    carve_rerank(cr, nq, n - nq, d, tensor_mode(p), &rw);
+    s = rerank_impl(cur, nq, cur + (size_t)nq * d, n - nq, d, p, idx_out, dist_out, rw, st, hd);
+  }
+  if (s != GCR_OK) return s;
+  if (X_final) GCR_CUDA_TRY(cudaMemcpyAsync(X_final, cur, sizeof(float) * n * d, cudaMemcpyDeviceToDevice, st));
+  return GCR_OK;
+}
+
+// Device staging of gcr_pipeline_host: camera ids and the ranking.
+struct HostStaging {
+  int32_t* cam;
+  int32_t* idx;
+  float* dist;
+};
+size_t carve_host_staging(Carve& c, int64_t n, int64_t nq, const gcr_params* p, HostStaging* h) {
+  const int64_t ng = n - nq;
+  const int64_t K = p->topk_out > 0 ? std::min<int64_t>(p->topk_out, ng) : ng;
+  HostStaging t;
+  t.cam = c.take<int32_t>((size_t)n);
+  t.idx = c.take<int32_t>((size_t)nq * K);
+  t.dist = c.take<float>((size_t)nq * K);
+  if (h) *h = t;
+  return c.off;
+}
+
+// Per-device copy stream and events of gcr_pipeline_host, created on first use and kept.
+constexpr int kHostChunks = 8;
+constexpr int kMaxDevices = 64;
+struct HostCopyState {
+  bool ready = false;
+  cudaStream_t copy = nullptr;
+  cudaEvent_t ev[kHostChunks + 1];
+};
+std::mutex g_copy_mu;
+HostCopyState g_copy[kMaxDevices];
+
 }  // namespace
 
 extern "C" {
@@ -940,40 +1039,76 @@ int gcr_pipeline(const float* X, int64_t n, int64_t nq, int32_t d, const int32_t
   Carve c(ws, ws_bytes);
   PipeWs w;
   if (carve_pipe(c, n, nq, d, p, r, &w) > ws_bytes) return GCR_E_WORKSPACE;
-  cudaStream_t st = (cudaStream_t)stream;
-  w.g.stats = stats;
-  {
-    StageScope sc_(GCR_STAGE_NORMALIZE, st);
-    GCR_CUDA_TRY(launch_normalize(X, w.Xa, n, d, st));
-  }
-  float* cur = w.Xa;
-  float* nxt = w.Xb;
-  for (int t = 0; t < p->T; ++t) {
-    Carve cb(w.inner, w.inner_bytes);
-    BuildWs bw;
-    carve_build(cb, n, d, p, r, &bw);
-    s = build_graph_impl(cur, n, d, cam, p, r, &w.g, bw, st);
-    if (s != GCR_OK) return s;
-    {
-      StageScope sc_(GCR_STAGE_PROPAGATE, st);
-      GCR_CUDA_TRY(launch_propagate(w.g.op_rowptr, w.g.op_len, w.g.op_col, w.g.op_val, cur, nxt, (int)n, d,
-                                    p->k > 0 ? w.g.row_order : nullptr, st));
-    }
-    float* tmp = cur; cur = nxt; nxt = tmp;
-  }
-  Carve cr(w.inner, w.inner_bytes);
-  if (rerank_uses_pool(p, n - nq)) {
-    TopkRerankWs tw;
-    carve_topk_rerank(cr, nq, n - nq, d, p, &tw);
-    s = topk_rerank_impl(cur, nq, cur + (size_t)nq * d, n - nq, d, p, idx_out, dist_out, tw, st);
-  } else {
-    RerankWs rw;
-    carve_rerank(cr, nq, n - nq, d, tensor_mode(p), &rw);
-    s = rerank_impl(cur, nq, cur + (size_t)nq * d, n - nq, d, p, idx_out, dist_out, rw, st);
-  }
+  return pipeline_impl(X, n, nq, d, cam, p, r, X_final, idx_out, dist_out, stats, w, (cudaStream_t)stream, nullptr);
+}
+
+size_t gcr_pipeline_host_workspace_size(int64_t n, int64_t nq, int32_t d, const gcr_params* p) {
+  Resolved r;
+  if (check_params(p, n, d, &r) != GCR_OK) return 0;
+  if (nq < 1 || nq >= n || check_rerank(nq, n - nq, d, p) != GCR_OK) return 0;
+  Carve c(nullptr, 0);
+  carve_pipe(c, n, nq, d, p, r, nullptr);
+  HostStaging h;
+  return carve_host_staging(c, n, nq, p, &h) + 256;
+}
+
+int gcr_pipeline_host(const float* X_host, int64_t n, int64_t nq, int32_t d, const int32_t* cam_host,
+                      const gcr_params* p, int32_t* idx_host, float* dist_host, int64_t* stats, void* ws,
+                      size_t ws_bytes, gcr_stream_t stream) {
+  Resolved r;
+  int s = check_params(p, n, d, &r);
   if (s != GCR_OK) return s;
-  if (X_final) GCR_CUDA_TRY(cudaMemcpyAsync(X_final, cur, sizeof(float) * n * d, cudaMemcpyDeviceToDevice, st));
+  if (nq < 1 || nq >= n) return GCR_E_INVALID;
+  s = check_rerank(nq, n - nq, d, p);
+  if (s != GCR_OK) return s;
+  if (!X_host || !idx_host || !dist_host || (p->cross_camera && !cam_host) || p->T < 0) return GCR_E_INVALID;
+  if (!ws) return GCR_E_WORKSPACE;
+  Carve c(ws, ws_bytes);
+  PipeWs w;
+  carve_pipe(c, n, nq, d, p, r, &w);
+  HostStaging h;
+  if (carve_host_staging(c, n, nq, p, &h) > ws_bytes) return GCR_E_WORKSPACE;
+  cudaStream_t st = (cudaStream_t)stream;
+  int dev = 0;
+  GCR_CUDA_TRY(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= kMaxDevices) return GCR_E_UNSUPPORTED;
+  std::lock_guard<std::mutex> lock(g_copy_mu);
+  HostCopyState& cs = g_copy[dev];
+  if (!cs.ready) {
+    GCR_CUDA_TRY(cudaStreamCreateWithFlags(&cs.copy, cudaStreamNonBlocking));
+    for (int e = 0; e <= kHostChunks; ++e) GCR_CUDA_TRY(cudaEventCreateWithFlags(&cs.ev[e], cudaEventDisableTiming));
+    cs.ready = true;
+  }
+  // the input rows land in the second feature buffer, which the pipeline only overwrites
+  // after normalising them into the first
+  GCR_CUDA_TRY(cudaMemcpyAsync(w.Xb, X_host, sizeof(float) * n * d, cudaMemcpyHostToDevice, st));
+  if (p->cross_camera) GCR_CUDA_TRY(cudaMemcpyAsync(h.cam, cam_host, sizeof(int32_t) * n, cudaMemcpyHostToDevice, st));
+  const int64_t ng = n - nq;
+  const int64_t K = p->topk_out > 0 ? std::min<int64_t>(p->topk_out, ng) : ng;
+  HostDelivery hd;
+  hd.idx_host = idx_host;
+  hd.dist_host = dist_host;
+  const int64_t tiles = (nq + 127) / 128;
+  const int64_t per = (tiles + kHostChunks - 1) / kHostChunks;
+  hd.chunk_rows = (int)(per * 128);
+  hd.copy = cs.copy;
+  hd.ready = cs.ev;
+  hd.n_events = kHostChunks;
+  s = pipeline_impl(w.Xb, n, nq, d, p->cross_camera ? h.cam : nullptr, p, r, nullptr, h.idx, h.dist, stats, w, st,
+                    &hd);
+  if (s != GCR_OK) return s;
+  if (rerank_uses_pool(p, ng)) {
+    // the certified top-K search returns all rows at once: copy them after it
+    GCR_CUDA_TRY(cudaEventRecord(cs.ev[0], st));
+    GCR_CUDA_TRY(cudaStreamWaitEvent(cs.copy, cs.ev[0], 0));
+    GCR_CUDA_TRY(cudaMemcpyAsync(idx_host, h.idx, sizeof(int32_t) * nq * K, cudaMemcpyDeviceToHost, cs.copy));
+    GCR_CUDA_TRY(cudaMemcpyAsync(dist_host, h.dist, sizeof(float) * nq * K, cudaMemcpyDeviceToHost, cs.copy));
+  }
+  // the caller's stream completes only after the last copy
+  GCR_CUDA_TRY(cudaEventRecord(cs.ev[kHostChunks], cs.copy));
+  GCR_CUDA_TRY(cudaStreamWaitEvent(st, cs.ev[kHostChunks], 0));
   return GCR_OK;
 }
+
 
 }  // extern "C"

@@ -238,6 +238,26 @@ def test_pipeline_end_to_end_plain(gcr, precision):
     assert st["band_failed"] == 0
 
 
+@pytest.mark.parametrize("precision", ["fp32", "tf32"])
+@pytest.mark.parametrize("topk", [0, 20])
+def test_pipeline_host_buffers_match_device(gcr, precision, topk):
+    """gcr_pipeline_host (host inputs, ranking copied back in query chunks on a second stream)
+    returns exactly the ranking of gcr_pipeline on device buffers."""
+    w = workloads.crosscam(seed=5, n_query=1100, n_gallery=2500, d=256, n_clusters=150)
+    p = gcr.default_params(k=w.k, T=2, cross_camera=1, alpha=0.7, precision=precision, topk_out=topk)
+    dev = gcr.Pipeline(w.n, w.n_query, w.d, p)
+    idx_d, dist_d = dev(_dev(w.X), _dev(w.cam, torch.int32), keep_features=False)
+    hp = gcr.HostPipeline(w.n, w.n_query, w.d, p)
+    Xh = torch.from_numpy(w.X).pin_memory()
+    camh = torch.from_numpy(w.cam.astype(np.int32)).pin_memory()
+    for _ in range(2):  # twice: the copy stream and its events are reused
+        hp.idx.fill_(-7)
+        idx_h, dist_h = hp(Xh, camh)
+        torch.cuda.synchronize()
+        assert np.array_equal(idx_h.numpy(), idx_d.cpu().numpy())
+        assert np.array_equal(dist_h.numpy(), dist_d.cpu().numpy())
+
+
 @pytest.mark.parametrize("precision", PRECISIONS)
 def test_pipeline_determinism(gcr, precision):
     w = workloads.crosscam(seed=11, n_query=300, n_gallery=1700, d=192, n_clusters=80)
