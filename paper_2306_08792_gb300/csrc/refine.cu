@@ -395,16 +395,46 @@ __global__ void __launch_bounds__(256) refine_pool_kernel(RefineArgs a) {
   finalize<VPL, P>(a, xi, L, r, kk, eps, row, kind, lane);
 }
 
-// One warp per uncertified (row, kind): every band entry (score >= threshold) is re-scored.
+// The kk-th largest of the cnt (<= 512) band scores bv[0..cnt): an MSB-first radix select on
+// their order-preserving 32-bit images, one bit per step (the same value on every lane).
+__device__ __forceinline__ float band_kth(const float* __restrict__ bv, int cnt, int kk, int lane) {
+  uint32_t key[16];
+#pragma unroll
+  for (int i = 0; i < 16; ++i) {
+    const int e = i * 32 + lane;
+    key[i] = e < cnt ? float_to_ordered(bv[e]) : 0u;
+  }
+  uint32_t prefix = 0, mask = 0;
+  int need = kk;
+  for (int b = 31; b >= 0; --b) {
+    const uint32_t bit = 1u << b, cand = prefix | bit;
+    int c = 0;
+#pragma unroll
+    for (int i = 0; i < 16; ++i) c += (i * 32 + lane < cnt && (key[i] & (mask | bit)) == cand) ? 1 : 0;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(GCR_FULL, c, o);
+    if (c >= need) prefix = cand;
+    else need -= c;
+    mask |= bit;
+  }
+  return ordered_to_float(prefix);
+}
+
+// One warp per uncertified (row, kind). The band holds every column whose approximate score
+// reaches the row's threshold; of those, only the entries within 2 delta (plus the spread of
+// ||x_j||^2 / 2) of the kk-th best approximate score can be among the kk nearest (the same
+// rule as the pool refinement), and only they are re-scored.
 template <int VPL, int P>
 __global__ void __launch_bounds__(256) refine_band_kernel(RefineArgs a) {
+  __shared__ int sel_ids[8][64];
   const int lane = threadIdx.x & 31;
+  int* sb = sel_ids[threadIdx.x >> 5];
   const int U = *a.unc_count;
   const int nw = gridDim.x * 8;
   for (int u = blockIdx.x * 8 + (threadIdx.x >> 5); u < U; u += nw) {
     const int row = a.unc_row[u], kind = a.unc_kind[u];
     const int cnt = u < a.band_rows ? a.band_cnt[u] : a.bcap + 1;
-    if (cnt > a.bcap) {
+    if (cnt > a.bcap || cnt > 512) {
       if (lane == 0 && a.stats) atomicAdd(&a.stats[GCR_STAT_BAND_FAILED], 1ull);
       continue;
     }
@@ -417,18 +447,44 @@ __global__ void __launch_bounds__(256) refine_band_kernel(RefineArgs a) {
 #pragma unroll
     for (int p = 0; p < P; ++p) { L.sig[p] = -CUDART_INF; L.id[p] = 0x7fffffff; L.val[p] = 0.0; }
     const int* bi = a.band_i + (size_t)u * a.bcap;
-    for (int c0 = 0; c0 < cnt; c0 += 32) {
-      WList<1> C;
-      C.id[0] = (c0 + lane < cnt) ? bi[c0 + lane] : -1;
-      C.sig[0] = -CUDART_INF;
-      C.val[0] = 0.0;
-      rescore<VPL, 1>(a, xi, C, min(32, cnt - c0), lane);
-      if (C.id[0] < 0) C.id[0] = 0x7fffffff;
-      sort32_d(C.sig[0], C.id[0], C.val[0], lane);
-      wl_merge<P>(L, C.sig[0], C.id[0], C.val[0], lane);
+    const float* bv = a.band_v + (size_t)u * a.bcap;
+    const int kb = min(a.k, cnt);
+    const double thr = kb > 0 ? (double)band_kth(bv, cnt, kb, lane) - 2.0 * delta - 0.5 * (sc.nmax - sc.nmin)
+                              : -CUDART_INF;
+    // selected entries are staged per warp (at most 31 left over + 32 new) and re-scored 32 at
+    // a time
+    int nsel = 0, total = 0;
+    for (int c0 = 0; c0 < cnt || nsel > 0; c0 += 32) {
+      if (c0 < cnt) {
+        const int e = c0 + lane;
+        const bool s = e < cnt && (double)bv[e] >= thr;
+        const unsigned m = __ballot_sync(GCR_FULL, s);
+        if (s) sb[nsel + __popc(m & ((1u << lane) - 1u))] = bi[e];
+        nsel += __popc(m);
+        __syncwarp();
+      }
+      const bool last = c0 + 32 >= cnt;
+      while (nsel >= 32 || (last && nsel > 0)) {
+        const int take = min(nsel, 32);
+        WList<1> C;
+        C.id[0] = lane < take ? sb[lane] : -1;
+        C.sig[0] = -CUDART_INF;
+        C.val[0] = 0.0;
+        rescore<VPL, 1>(a, xi, C, take, lane);
+        if (C.id[0] < 0) C.id[0] = 0x7fffffff;
+        sort32_d(C.sig[0], C.id[0], C.val[0], lane);
+        wl_merge<P>(L, C.sig[0], C.id[0], C.val[0], lane);
+        total += take;
+        const int rem = nsel - take;
+        const int v = lane < rem ? sb[take + lane] : 0;
+        __syncwarp();
+        if (lane < rem) sb[lane] = v;
+        __syncwarp();
+        nsel = rem;
+      }
     }
-    if (lane == 0 && a.stats) atomicAdd(&a.stats[GCR_STAT_RESCORED], (unsigned long long)cnt);
-    const int r = min(cnt, 32 * P);
+    if (lane == 0 && a.stats) atomicAdd(&a.stats[GCR_STAT_RESCORED], (unsigned long long)total);
+    const int r = min(total, 32 * P);
     const int kk = min(a.k, r);
     finalize<VPL, P>(a, xi, L, r, kk, eps, row, kind, lane);
   }

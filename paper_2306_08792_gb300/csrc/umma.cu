@@ -17,6 +17,7 @@
 // tile j. Every mbarrier wait is bounded (2 s of %globaltimer); on a timeout the CTA raises a
 // shared abort flag that every role polls, waits (bounded) for its in-flight MMAs, frees TMEM
 // and returns; the timeout is counted in a device word that gcr_sync reports.
+#include <algorithm>
 #include <cuda.h>
 #include <cuda_bf16.h>
 
@@ -203,7 +204,7 @@ struct Tiles {
   int count;
   __device__ int row0(const UmmaArgs& a, int t) const {
     if (a.mode == POOL) return blockIdx.x * BM;
-    if (a.mode == BAND) return t * BM;
+    if (a.mode == BAND) return (blockIdx.y + t * gridDim.y) * BM;  // row tiles strided over grid.y
     return blockIdx.y * BM;
   }
   __device__ int col0(const UmmaArgs& a, int t) const {
@@ -229,7 +230,8 @@ umma_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
   if (a.mode == POOL) tl.count = max(0, min(a.tps, (a.n + BN - 1) / BN - (int)blockIdx.y * a.tps));
   else if (a.mode == BAND) {
     const int U = min(*a.count, a.cap);
-    tl.count = (U + BM - 1) / BM;
+    const int tiles = (U + BM - 1) / BM;
+    tl.count = max(0, (tiles - (int)blockIdx.y + (int)gridDim.y - 1) / (int)gridDim.y);
   } else tl.count = 1;
 
   if (threadIdx.x == 0) {
@@ -575,7 +577,11 @@ cudaError_t launch_umma_band(const void* Xb, int n, int d, Elt elt, const int* c
   a.band_cnt = band_cnt;
   a.band_v = band_v;
   a.band_i = band_i;
-  dim3 grid((n + BN - 1) / BN);
+  // the row tiles (known only on the device) are strided over grid.y so that the grid covers
+  // the GPU about twice even when the columns give few tiles
+  const int gx = (n + BN - 1) / BN;
+  const int gy = std::max(1, std::min(8, (2 * 152 + gx - 1) / gx));
+  dim3 grid(gx, gy);
   return launch<64, false>(ta, tb, a, grid, st);
 }
 
