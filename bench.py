@@ -374,7 +374,7 @@ def run_ours(a):
     ms = max_over_ranks(R["ms"], dist, "cuda")
     value = job_throughput(world, w.n_query, ms)
 
-    e2e_ms, e2e_mean, h2d, d2h, hp = time_e2e(gcr, torch, w, Xh, camh, R["params"], max(7, a.steps), 2)
+    e2e_ms, e2e_mean, h2d, d2h, hp = time_e2e(gcr, torch, w, Xh, camh, R["params"], max(7, a.steps), 3)
     e2e_ms = max_over_ranks(e2e_ms, dist, "cuda")
     # one more untimed run that keeps the features, for the sampled error check
     R["pipeline"](X, cam, keep_features=True)
