@@ -47,6 +47,7 @@ def _args():
     ap.add_argument("--precision", choices=["auto", "tf32", "bf16", "fp32"], default="auto")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-serving", action="store_true")
+    ap.add_argument("--no-zipf", action="store_true", help="skip the 200,000-row Zipf workload")
     ap.add_argument("--serving-requests", type=int, default=800)
     ap.add_argument("--pool", type=int, default=0, help="candidate pool per row (0: library default)")
     return ap.parse_args()
@@ -310,6 +311,60 @@ def serving_bench(gcr, torch, precision, n_requests):
             "launches": rt["launches"]}
 
 
+def zipf_bench(gcr, torch, precision, steps, warmup):
+    """Large-scale workload: 1,000 queries + 200,000 gallery, d = 512, 10,000 Zipf(1.1)-sized
+    clusters, k = 30, T = 3, top-100 re-ranking (the certified top-K search; the full ranking of
+    200,000 rows per query is outside the segmented sort). Step time, stage times and the HBM
+    roofline of the propagation kernel (algorithmic bytes per layer = 2*n*d*4 + nnz*8)."""
+    import workloads
+    from paper_2306_08792_gb300 import _lib
+    import ctypes
+    w = workloads.zipf()
+    p = gcr.default_params(k=w.k, T=w.T, precision=precision, topk_out=100)
+    X = torch.from_numpy(w.X).cuda()
+    pl = gcr.Pipeline(w.n, w.n_query, w.d, p)
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device="cuda")
+    for _ in range(warmup):
+        pl(X, None, keep_features=False)
+    torch.cuda.synchronize()
+    lib = _lib.load()
+    S = _lib.GCR_STAGES
+    ms_arr, la, ca = (ctypes.c_double * S)(), (ctypes.c_int64 * S)(), (ctypes.c_int64 * S)()
+    lib.gcr_profile_enable(1)
+    stream = torch.cuda.current_stream()
+    per = []
+    for _ in range(steps):
+        flush.zero_()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        pl(X, None, keep_features=False)
+        b.record(stream)
+        b.synchronize()
+        per.append(a.elapsed_time(b))
+    lib.gcr_profile_read(ms_arr, la, ca, S)
+    lib.gcr_profile_enable(0)
+    stages = {name: round(ms_arr[i] / steps, 4) for i, name in enumerate(_lib.STAGE_NAMES)}
+    # operator entries of one layer's graph (layer 1), for the propagation's algorithmic bytes
+    X0 = gcr.gcr_normalize(X)
+    G = gcr.gcr_build_graph(X0, p)
+    nnz = int(G.op_len.sum().item())
+    bytes_layer = 2.0 * w.n * w.d * 4 + nnz * 8.0
+    prop_ms = stages["propagate"] / w.T
+    peaks, psrc = _peaks()
+    gbs = bytes_layer / (prop_ms / 1e3) / 1e9
+    ms = statistics.mean(per)
+    del pl, G, X0, X
+    torch.cuda.empty_cache()
+    return {"workload": "zipf: 1,000 queries + 200,000 gallery, d=512, 10,000 Zipf(1.1) clusters, k=30, T=3, "
+                        "top-100 re-ranking",
+            "precision": precision, "steps": steps, "warmup": warmup, "ms_per_step": ms,
+            "queries_per_s": w.n_query / (ms / 1e3), "stages_ms": stages,
+            "propagate_roofline": {"bound": "hbm", "achieved": gbs, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                                   "frac": gbs / peaks["hbm_gbs"], "peak_source": f"hbm_gbs of {psrc}",
+                                   "bytes_per_layer": bytes_layer, "nnz": nnz, "ms_per_layer": prop_ms},
+            "sim_gemm_tflops": 2.0 * w.n * w.n * w.d / (stages["sim_gemm"] / w.T / 1e3) / 1e12}
+
+
 def max_over_ranks(value: float, dist, device=None) -> float:
     """Largest value over all ranks (the slowest replica sets the job's time)."""
     if dist is None:
@@ -434,6 +489,11 @@ def run_ours(a):
                 line["speedup_vs_" + prec] = o["ms"] / R["ms"]
             else:
                 line[f"{prec}_path"] = o
+    if rank == 0 and world == 1 and not a.no_zipf:
+        try:
+            line["zipf"] = zipf_bench(gcr, torch, primary if primary != "fp32" else "tf32", 3, 3)
+        except gcr.GcrError as e:
+            line["zipf"] = {"error": str(e)}
     if rank == 0 and world == 1 and not a.no_serving:
         serving = {}
         for prec in prec_order:

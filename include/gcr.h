@@ -69,8 +69,9 @@ typedef struct {
   int32_t cross_camera; /* 1: add the cross-camera graph (Eq. 8) and mix by Eq. 9         */
   int32_t precision;    /* gcr_precision                                                  */
   int32_t pool;         /* per-row candidate pool of the streaming kNN search: 32, 64 or
-                           128; 0 picks 32 for FP32 and TF32, 64 for BF16 (BF16
-                           needs >= 64);
+                           128; 0 picks the smallest of these that holds k plus a
+                           margin of max(12, k/2) (32 for k <= 20), at least 64 under
+                           BF16 (which needs >= 64);
                            must exceed k. A larger pool certifies more rows without the
                            threshold rescan at the cost of a busier GEMM epilogue.        */
   int32_t topk_out;     /* gcr_rerank: results per query; 0 = the whole gallery           */
@@ -82,12 +83,19 @@ enum {
   GCR_STAT_ROWS = 0,          /* (row, graph) pairs searched                               */
   GCR_STAT_UNCERTIFIED = 1,   /* pairs whose candidate pool could not certify the k-th
                                  neighbour and went through the threshold (band) rescan  */
-  GCR_STAT_BAND_FAILED = 2,   /* pairs whose band rescan overflowed; their sets are the
-                                 best available, not certified                            */
+  GCR_STAT_BAND_FAILED = 2,   /* pairs whose band rescan found more than 512 columns
+                                 within the certified margin of the k-th (a dense
+                                 boundary): they keep the pool's exact top k, whose
+                                 exact scores are within 2*delta of the exact k-th score
+                                 (delta = the certified bound of the GEMM)               */
   GCR_STAT_FP64_ROWS = 3,     /* pairs whose k-th / (k+1)-th boundary needed FP64          */
   GCR_STAT_FP64_DOTS = 4,     /* FP64 dot products computed for those boundaries           */
   GCR_STAT_CLAMPED = 5,       /* pairs with fewer than k eligible samples                  */
   GCR_STAT_RESCORED = 6,      /* FP32 re-scored candidates                                 */
+  GCR_STAT_SATURATED = 7,     /* uncertified pairs whose pool is saturated with near-ties:
+                                 the density of its lower half predicts more than 512
+                                 band entries, so the rescan is skipped; the same 2*delta
+                                 guarantee as GCR_STAT_BAND_FAILED                        */
   GCR_STATS_LEN = 8
 };
 

@@ -14,7 +14,7 @@ GCR_PREC_FP32, GCR_PREC_BF16, GCR_PREC_TF32 = 0, 1, 2
 STAGE_NAMES = ["normalize", "prep", "sim_gemm", "refine", "band", "graph", "propagate", "dist_gemm", "sort",
                "gcrv"]
 GCR_STAGES = 12
-STAT_NAMES = ["rows", "uncertified", "band_failed", "fp64_rows", "fp64_dots", "clamped", "rescored", "reserved"]
+STAT_NAMES = ["rows", "uncertified", "band_failed", "fp64_rows", "fp64_dots", "clamped", "rescored", "saturated"]
 GCR_STATS_LEN = 8
 
 

@@ -43,7 +43,6 @@ struct StageScope {
 };
 
 constexpr int kBandCap = 512;        // band entries kept per rescanned (row, graph)
-constexpr int kBandRowsMax = 32768;  // (row, graph) pairs a band rescan can hold
 constexpr int kMaxD = 4096;
 
 struct Resolved {
@@ -64,6 +63,15 @@ int check_precision(const gcr_params* p, int32_t d) {
   return GCR_OK;
 }
 
+// Default candidate pool: room for a margin of max(12, k/2) candidates past the k-th, which
+// the certification needs when the k-th neighbour sits in a dense region; BF16 at least 64.
+int default_pool(const gcr_params* p) {
+  const int want = p->k + std::max(12, p->k / 2);
+  int kp = want <= 32 ? 32 : (want <= 64 ? 64 : 128);
+  if (p->precision == GCR_PREC_BF16) kp = std::max(kp, 64);
+  return kp;
+}
+
 int check_params(const gcr_params* p, int64_t n, int32_t d, Resolved* r) {
   if (!p || n < 1 || n > (1 << 24)) return GCR_E_INVALID;
   if (d < 4 || d > kMaxD) return GCR_E_INVALID;
@@ -74,7 +82,7 @@ int check_params(const gcr_params* p, int64_t n, int32_t d, Resolved* r) {
   if (p->symmetric != 0 && p->symmetric != 1) return GCR_E_INVALID;
   if (p->cross_camera != 0 && p->cross_camera != 1) return GCR_E_INVALID;
   if (p->cross_camera && !(p->alpha >= 0.f && p->alpha <= 1.f)) return GCR_E_INVALID;
-  int kp = p->pool ? p->pool : (p->precision == GCR_PREC_BF16 ? 64 : 32);
+  int kp = p->pool ? p->pool : default_pool(p);
   if (kp != 32 && kp != 64 && kp != 128) return GCR_E_INVALID;
   if (p->k < 0 || p->k >= kp) return GCR_E_INVALID;
   // the BF16 rounding bound is too loose for a 32-entry pool to certify most rows
@@ -116,6 +124,8 @@ struct BuildWs {
   int* op_cnt;
   int* scan_tmp;
   double* inv;
+  int* long_list;
+  int* long_count;
   unsigned long long* stats;
   int* err;
   int* okey;
@@ -131,7 +141,8 @@ size_t carve_build(Carve& c, int64_t n, int32_t d, const gcr_params* p, const Re
   const int kinds = r.kinds;
   const bool bf = tensor_mode(p);
   const size_t es = elt_size(p);
-  const int band_rows = (int)std::min<int64_t>((int64_t)kinds * n, kBandRowsMax);
+  // every (row, graph) pair fits in the band buffers, so no uncertified pair goes unrescanned
+  const int band_rows = (int)((int64_t)kinds * n);
   const size_t cap = op_capacity(n, p, kinds);
   BuildWs t;
   t.n64 = c.take<double>(nn);
@@ -160,6 +171,8 @@ size_t carve_build(Carve& c, int64_t n, int32_t d, const gcr_params* p, const Re
   t.op_cnt = c.take<int>(nn);
   t.scan_tmp = c.take<int>(nn + 1);
   t.inv = c.take<double>((size_t)2 * kinds * nn);
+  t.long_list = c.take<int>(nn);
+  t.long_count = c.take<int>(4);
   t.stats = c.take<unsigned long long>(GCR_STATS_LEN);
   t.err = c.take<int>(4);
   t.okey = c.take<int>(nn);
@@ -255,9 +268,9 @@ int build_graph_impl(const float* X, int64_t n64_, int32_t d, const int32_t* cam
   }
   ga.op_rowptr = g->op_rowptr; ga.op_len = g->op_len; ga.op_col = g->op_col; ga.op_val = g->op_val;
   ga.raw_col = w.raw_col; ga.raw_val = w.raw_val; ga.op_cnt = w.op_cnt; ga.scan_tmp = w.scan_tmp;
-  ga.inv = w.inv;
+  ga.inv = w.inv; ga.long_list = w.long_list; ga.long_count = w.long_count;
   {
-    StageScope sc_(GCR_STAGE_GRAPH, st, 5 * kinds + 3);
+    StageScope sc_(GCR_STAGE_GRAPH, st, 7 * kinds + 3);
     GCR_CUDA_TRY(launch_build_operator(ga, st));
   }
   return GCR_OK;

@@ -157,6 +157,8 @@ __device__ void tseg_sort_regs(int beg, int len, const int* __restrict__ src_tmp
   }
 }
 
+constexpr int kLongSeg = 256;  // longer transposed segments (in-degree hubs) go to tsort_long_kernel
+
 // One warp per transposed row j: sort its entries by source, then D_c(j) = 1 + sum.
 __global__ void tsort_kernel(int n, const int* __restrict__ tptr, const int* __restrict__ src_tmp,
                              const float* __restrict__ w_tmp, int* __restrict__ src, float* __restrict__ tw,
@@ -168,22 +170,126 @@ __global__ void tsort_kernel(int n, const int* __restrict__ tptr, const int* __r
   if (len <= 32) tseg_sort_regs<1>(beg, len, src_tmp, w_tmp, src, tw, lane);
   else if (len <= 64) tseg_sort_regs<2>(beg, len, src_tmp, w_tmp, src, tw, lane);
   else if (len <= 128) tseg_sort_regs<4>(beg, len, src_tmp, w_tmp, src, tw, lane);
-  else if (len <= 256) tseg_sort_regs<8>(beg, len, src_tmp, w_tmp, src, tw, lane);
-  else {
-    // long segment (hub): rank sort, sources within a segment are distinct
-    for (int e = lane; e < len; e += 32) {
-      const int me = src_tmp[beg + e];
-      int rank = 0;
-      for (int f = 0; f < len; ++f) rank += src_tmp[beg + f] < me;
-      src[beg + rank] = me;
-      tw[beg + rank] = w_tmp[beg + e];
-    }
-  }
+  else if (len <= kLongSeg) tseg_sort_regs<8>(beg, len, src_tmp, w_tmp, src, tw, lane);
+  else return;  // a hub's long segment: tsort_long_kernel sorts it and sets its D_c
   __syncwarp();
   if (lane == 0) {
     float acc = 1.0f;  // A~_jj = 1
     for (int e = 0; e < len; ++e) acc += tw[beg + e];
     deg_c[j] = acc;
+  }
+}
+
+// Transposed rows longer than kLongSeg, listed in arbitrary order (each is processed on its own).
+__global__ void long_list_kernel(int n, const int* __restrict__ tptr, int* __restrict__ list, int* __restrict__ count) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= n) return;
+  if (tptr[j + 1] - tptr[j] > kLongSeg) list[atomicAdd(count, 1)] = j;
+}
+
+// One CTA per long transposed segment (a persistent loop over the list): a stable LSD radix
+// sort of the segment by source row (8-bit digits, nbits = bits of the largest row index),
+// chunk by chunk through global memory in segment order, so the work is linear in the
+// segment's length (an in-degree hub can hold tens of thousands of entries). Within a chunk
+// each warp ranks its keys slot by slot with __match_any_sync; a running per-digit offset
+// carries the order from chunk to chunk. The weights follow their keys. Then D_c(j) = 1 + sum
+// of the weights, reduced in a fixed order.
+template <int IPT>
+__global__ void __launch_bounds__(256) tsort_long_kernel(const int* __restrict__ tptr, int* src_tmp, float* w_tmp,
+                                                         int* src, float* tw, float* __restrict__ deg_c,
+                                                         const int* __restrict__ list, const int* __restrict__ count,
+                                                         int nbits) {
+  constexpr int NT = 256, NW = NT / 32, CH = NT * IPT;
+  __shared__ uint32_t dbase[256];       // running offset of each digit in the segment
+  __shared__ uint32_t wcnt[NW][257];    // per-warp digit counts of a chunk (column 256: past the end)
+  __shared__ float red[NW];
+  const int t = threadIdx.x, lane = t & 31, w = t >> 5;
+  const unsigned lt = (1u << lane) - 1u;
+  const int total = *count;
+  for (int li = blockIdx.x; li < total; li += gridDim.x) {
+    const int j = list[li];
+    const int beg = tptr[j], L = tptr[j + 1] - beg;
+    int* ka = src_tmp + beg;
+    float* va = w_tmp + beg;
+    int* kb = src + beg;
+    float* vb = tw + beg;
+    for (int shift = 0; shift < nbits; shift += 8) {
+      for (int v = t; v < 256; v += NT) dbase[v] = 0;
+      __syncthreads();
+      for (int e = t; e < L; e += NT) atomicAdd(&dbase[((uint32_t)ka[e] >> shift) & 255u], 1u);
+      __syncthreads();
+      if (w == 0) {  // exclusive scan of the 256 digit counts
+        uint32_t c[8], sum = 0;
+#pragma unroll
+        for (int q = 0; q < 8; ++q) { c[q] = dbase[lane * 8 + q]; sum += c[q]; }
+        uint32_t inc = sum;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+          const uint32_t y = __shfl_up_sync(GCR_FULL, inc, o);
+          if (lane >= o) inc += y;
+        }
+        uint32_t run = inc - sum;
+#pragma unroll
+        for (int q = 0; q < 8; ++q) { dbase[lane * 8 + q] = run; run += c[q]; }
+      }
+      __syncthreads();
+      for (int c0 = 0; c0 < L; c0 += CH) {
+        for (int v = t; v < NW * 257; v += NT) (&wcnt[0][0])[v] = 0;
+        __syncthreads();
+        uint32_t key[IPT], off[IPT], dg[IPT];
+#pragma unroll
+        for (int i = 0; i < IPT; ++i) {
+          const int e = c0 + w * 32 * IPT + i * 32 + lane;
+          key[i] = e < L ? (uint32_t)ka[e] : 0u;
+          dg[i] = e < L ? ((key[i] >> shift) & 255u) : 256u;
+          const unsigned peers = __match_any_sync(GCR_FULL, dg[i]);
+          const uint32_t base = wcnt[w][dg[i]];
+          __syncwarp();
+          if ((peers & lt) == 0) wcnt[w][dg[i]] = base + (uint32_t)__popc(peers);  // the lowest peer updates
+          __syncwarp();
+          off[i] = base + (uint32_t)__popc(peers & lt);
+        }
+        __syncthreads();
+        {  // digit t: offsets of each warp's keys in (digit, warp) order, then the running base
+          uint32_t run = dbase[t];
+#pragma unroll
+          for (int ww = 0; ww < NW; ++ww) {
+            const uint32_t cc = wcnt[ww][t];
+            wcnt[ww][t] = run;
+            run += cc;
+          }
+          dbase[t] = run;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int i = 0; i < IPT; ++i) {
+          const int e = c0 + w * 32 * IPT + i * 32 + lane;
+          if (e < L) {
+            const uint32_t dst = wcnt[w][dg[i]] + off[i];
+            kb[dst] = (int)key[i];
+            vb[dst] = va[e];
+          }
+        }
+        __syncthreads();
+      }
+      int* tk = ka; ka = kb; kb = tk;
+      float* tv = va; va = vb; vb = tv;
+    }
+    if (ka != src + beg) {  // an even number of passes leaves the result in the scratch
+      for (int e = t; e < L; e += NT) { src[beg + e] = ka[e]; tw[beg + e] = va[e]; }
+      __syncthreads();
+    }
+    float sum = 0.f;
+    for (int e = t; e < L; e += NT) sum += tw[beg + e];
+    sum = warp_sum(sum);
+    if (lane == 0) red[w] = sum;
+    __syncthreads();
+    if (t == 0) {
+      float acc = 1.0f;  // A~_jj = 1
+      for (int ww = 0; ww < NW; ++ww) acc += red[ww];
+      deg_c[j] = acc;
+    }
+    __syncthreads();
   }
 }
 
@@ -377,6 +483,13 @@ cudaError_t launch_build_operator(const GraphArgs& g, cudaStream_t st) {
           n, k, g.nbr[q], g.w[q], g.cnt[q], g.fill[q], g.op_col, g.op_val);
     }
     tsort_kernel<<<(n + 7) / 8, 256, 0, st>>>(n, g.cnt[q], g.op_col, g.op_val, g.t_src[q], g.t_w[q], g.deg_c[q]);
+    e = cudaMemsetAsync(g.long_count, 0, sizeof(int), st);
+    if (e != cudaSuccess) return e;
+    long_list_kernel<<<(n + 255) / 256, 256, 0, st>>>(n, g.cnt[q], g.long_list, g.long_count);
+    int nbits = 0;
+    while (nbits < 31 && ((long)1 << nbits) < (long)n) ++nbits;
+    tsort_long_kernel<8><<<2 * 152, 256, 0, st>>>(g.cnt[q], g.op_col, g.op_val, g.t_src[q], g.t_w[q], g.deg_c[q],
+                                                  g.long_list, g.long_count, nbits);
   }
   e = cudaGetLastError();
   if (e != cudaSuccess) return e;

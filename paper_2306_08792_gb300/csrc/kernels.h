@@ -116,6 +116,8 @@ struct GraphArgs {
   int* op_cnt;              // [n] scratch
   int* scan_tmp;            // [n+1] scratch
   double* inv;              // [2*kinds][n] scratch: inverse square roots of the degrees
+  int* long_list;           // [n] scratch: transposed rows of a hub's length
+  int* long_count;          // [1] scratch
 };
 cudaError_t launch_build_operator(const GraphArgs& g, cudaStream_t st);
 cudaError_t launch_scan(const int* in, int* out, int n, cudaStream_t st);

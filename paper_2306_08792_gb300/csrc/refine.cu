@@ -384,12 +384,25 @@ __global__ void __launch_bounds__(256) refine_pool_kernel(RefineArgs a) {
   const double sig_k = wl_sig(L, kk - 1);
   if (mvalid == KP) {
     const bool cert = (sig_k - eps) > ((double)tau + delta - 0.5 * sc.nmin);
+    // Saturated pool: the density of the pool's lower half, extrapolated over the band's
+    // window below tau (about 2*delta wide), predicts more than 512 band entries, so the
+    // rescan would overflow; it is skipped. Either way the pool's exact top k is within
+    // 2*delta of the exact k-th score: every column outside the pool has s <= tau + delta,
+    // every pool entry s >= tau - delta.
+    const float mid = pool_at(KP / 2);
+    const double dens = (KP / 2) / fmax((double)mid - (double)tau, 1e-30);
+    const double below = fmax(0.0, 2.0 * delta + 0.5 * (sc.nmax - sc.nmin) - ((double)s_k - (double)tau));
+    const bool saturated = KP + dens * below > 512.0;
     if (!cert && lane == 0) {
-      const int u = atomicAdd(a.unc_count, 1);
-      a.unc_row[u] = row;
-      a.unc_kind[u] = kind;
-      a.unc_thr[u] = __double2float_rd(sig_k - eps + 0.5 * sc.nmin - delta);
       if (a.stats) atomicAdd(&a.stats[GCR_STAT_UNCERTIFIED], 1ull);
+      if (saturated) {
+        if (a.stats) atomicAdd(&a.stats[GCR_STAT_SATURATED], 1ull);
+      } else {
+        const int u = atomicAdd(a.unc_count, 1);
+        a.unc_row[u] = row;
+        a.unc_kind[u] = kind;
+        a.unc_thr[u] = __double2float_rd(sig_k - eps + 0.5 * sc.nmin - delta);
+      }
     }
   }
   finalize<VPL, P>(a, xi, L, r, kk, eps, row, kind, lane);

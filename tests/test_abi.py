@@ -80,7 +80,7 @@ def test_workspace_queries(lib):
     assert lib.gcr_pipeline_workspace_size(1000, 100, 256, ctypes.byref(p)) > a
 
 
-@pytest.mark.parametrize("bad", [dict(k=-1), dict(k=32), dict(gamma=0.0), dict(gamma=-1.0),
+@pytest.mark.parametrize("bad", [dict(k=-1), dict(k=128), dict(k=32, pool=32), dict(gamma=0.0), dict(gamma=-1.0),
                                  dict(cross_camera=1, alpha=1.5), dict(precision=7), dict(precision=3), dict(pool=48),
                                  dict(pool=256),
                                  dict(symmetric=2)])
@@ -114,6 +114,17 @@ def test_unsupported_shapes(lib):
     assert lib.gcr_build_graph(ctypes.c_void_p(16), 100, 16, None, ctypes.byref(pb32), ctypes.byref(g),
                                ctypes.c_void_p(16), 1 << 30, None) == 5
     assert lib.gcr_build_graph_workspace_size(100, 16, ctypes.byref(_params(lib, k=10, precision=2, pool=32))) > 0
+
+
+def test_default_pool_leaves_a_margin_past_k(lib):
+    # the default pool holds k plus max(12, k/2) candidates: k = 20 fits in 32, k = 30 needs 64,
+    # k = 100 needs 128 (visible through the workspace, which scales with the pool)
+    def ws(k, **kw):
+        return lib.gcr_build_graph_workspace_size(1000, 256, ctypes.byref(_params(lib, k=k, **kw)))
+    assert ws(20) == ws(20, pool=32)
+    assert ws(30) == ws(30, pool=64)
+    assert ws(100) == ws(100, pool=128)
+    assert ws(10, precision=1) == ws(10, precision=1, pool=64)
 
 
 def test_tf32_operand_copy_is_larger_than_bf16(lib):
