@@ -187,6 +187,10 @@ struct UmmaArgs {
   const float* nrm_q;
   const float* nrm_g;
   float* D;
+  int dist_nrb;    // row tiles of the distance matrix
+  int dist_tiles;  // all tiles; CTA b takes tiles b, b + grid, ... in column-major tile order,
+                   // so the CTAs at work share the (small) query blocks and stream each gallery
+                   // column tile once
 };
 
 struct __align__(8) Bars {
@@ -205,11 +209,12 @@ struct Tiles {
   __device__ int row0(const UmmaArgs& a, int t) const {
     if (a.mode == POOL) return blockIdx.x * BM;
     if (a.mode == BAND) return (blockIdx.y + t * gridDim.y) * BM;  // row tiles strided over grid.y
-    return blockIdx.y * BM;
+    return (((int)blockIdx.x + t * (int)gridDim.x) % a.dist_nrb) * BM;
   }
   __device__ int col0(const UmmaArgs& a, int t) const {
     if (a.mode == POOL) return (blockIdx.y * a.tps + t) * BN;
-    return blockIdx.x * BN;
+    if (a.mode == BAND) return blockIdx.x * BN;
+    return (((int)blockIdx.x + t * (int)gridDim.x) / a.dist_nrb) * BN;
   }
 };
 
@@ -232,7 +237,9 @@ umma_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
     const int U = min(*a.count, a.cap);
     const int tiles = (U + BM - 1) / BM;
     tl.count = max(0, (tiles - (int)blockIdx.y + (int)gridDim.y - 1) / (int)gridDim.y);
-  } else tl.count = 1;
+  } else {
+    tl.count = max(0, (a.dist_tiles - (int)blockIdx.x + (int)gridDim.x - 1) / (int)gridDim.x);
+  }
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < NST; ++s) {
@@ -600,7 +607,11 @@ cudaError_t launch_umma_dist(const __nv_bfloat16* Qb, int nq, const __nv_bfloat1
   a.nrm_q = nrm_q;
   a.nrm_g = nrm_g;
   a.D = D;
-  dim3 grid((ng + BN - 1) / BN, (nq + BM - 1) / BM);
+  // persistent: one CTA per SM walks its tiles, so the MMAs of a tile overlap the epilogue of
+  // the previous one (double-buffered accumulators)
+  a.dist_nrb = (nq + BM - 1) / BM;
+  a.dist_tiles = a.dist_nrb * ((ng + BN - 1) / BN);
+  dim3 grid((unsigned)std::max(1, std::min(a.dist_tiles, 152)));
   return launch<64, false>(ta, tb, a, grid, st);
 }
 
