@@ -48,6 +48,7 @@ def _args():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-serving", action="store_true")
     ap.add_argument("--no-zipf", action="store_true", help="skip the 200,000-row Zipf workload")
+    ap.add_argument("--no-video", action="store_true", help="skip the GCRV video workload")
     ap.add_argument("--serving-requests", type=int, default=800)
     ap.add_argument("--pool", type=int, default=0, help="candidate pool per row (0: library default)")
     return ap.parse_args()
@@ -365,6 +366,54 @@ def zipf_bench(gcr, torch, precision, steps, warmup):
             "sim_gemm_tflops": 2.0 * w.n * w.n * w.d / (stages["sim_gemm"] / w.T / 1e3) / 1e12}
 
 
+def video_bench(gcr, torch, precision, steps, warmup):
+    """GCRV video workload (Algorithm 2): 1,980 query + 11,310 gallery tracklets of 2-100 frames
+    (about 678k frames of d = 2048), 6 cameras, lambda = 10: the profile vectors of Eq. 17, then
+    GCR with the global and cross-camera graphs on them (k = 20, T = 2, full ranking). Times the
+    profiles and the re-ranking separately and together."""
+    import workloads
+    w = workloads.video()
+    frames = torch.from_numpy(w.frames).cuda()
+    off = torch.from_numpy(w.trk_off).cuda()
+    cam = torch.from_numpy(w.trk_cam.astype("int32")).cuda()
+    C = int(w.trk_cam.shape[0])
+    ncam = int(w.trk_cam.max()) + 1
+    p = gcr.default_params(k=w.k, T=w.T, cross_camera=1, alpha=0.7, precision=precision)
+    pl = gcr.Pipeline(C, w.n_query, frames.shape[1], p)
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device="cuda")
+    stream = torch.cuda.current_stream()
+
+    def one(ev):
+        ev[0].record(stream)
+        W = gcr.gcrv_profiles(frames, off, cam, ncam, w.lam)
+        ev[1].record(stream)
+        pl(W, cam, keep_features=False)
+        ev[2].record(stream)
+
+    for _ in range(warmup):
+        one([torch.cuda.Event(enable_timing=True) for _ in range(3)])
+    torch.cuda.synchronize()
+    prof, rr = [], []
+    for _ in range(steps):
+        flush.zero_()
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+        one(ev)
+        ev[2].synchronize()
+        prof.append(ev[0].elapsed_time(ev[1]))
+        rr.append(ev[1].elapsed_time(ev[2]))
+    F, d = frames.shape
+    ms = statistics.mean(prof) + statistics.mean(rr)
+    del pl, frames
+    torch.cuda.empty_cache()
+    return {"workload": f"video: {w.n_query:,} query + {C - w.n_query:,} gallery tracklets, {F:,} frames of "
+                        f"d={d}, 6 cameras, lambda={w.lam}; GCR k={w.k}, T={w.T}, cross-camera, full ranking",
+            "precision": precision, "steps": steps, "warmup": warmup, "ms_per_step": ms,
+            "queries_per_s": w.n_query / (ms / 1e3), "profiles_ms": statistics.mean(prof),
+            "rerank_ms": statistics.mean(rr),
+            "frames_gb_per_s": F * d * 4 / (statistics.mean(prof) / 1e3) / 1e9,
+            "gram_tflops": 2.0 * d * d * F / (statistics.mean(prof) / 1e3) / 1e12}
+
+
 def max_over_ranks(value: float, dist, device=None) -> float:
     """Largest value over all ranks (the slowest replica sets the job's time)."""
     if dist is None:
@@ -494,6 +543,11 @@ def run_ours(a):
             line["zipf"] = zipf_bench(gcr, torch, primary if primary != "fp32" else "tf32", 3, 3)
         except gcr.GcrError as e:
             line["zipf"] = {"error": str(e)}
+    if rank == 0 and world == 1 and not a.no_video:
+        try:
+            line["video"] = video_bench(gcr, torch, primary if primary != "fp32" else "tf32", 3, 3)
+        except gcr.GcrError as e:
+            line["video"] = {"error": str(e)}
     if rank == 0 and world == 1 and not a.no_serving:
         serving = {}
         for prec in prec_order:

@@ -31,6 +31,38 @@ struct Carve {
   }
 };
 
+// Float-float accumulation of sums of squares or products without FP64 arithmetic (GB300's FP64
+// rate is 1/64 of FP32): each product is split exactly (a*b = p + pe with an FMA), each addition
+// is an exact TwoSum into (hi, lo); the result is accurate to about 2^-46 relative (for sums
+// without cancellation), well below the 1e-12 the FP64 tie-break needs from the squared norms.
+struct FF {
+  float hi = 0.f, lo = 0.f;
+  __device__ __forceinline__ void add_sq(float x) {
+    const float p = x * x;
+    const float pe = fmaf(x, x, -p);
+    const float s = hi + p;
+    const float bp = s - hi;
+    lo += (hi - (s - bp)) + (p - bp) + pe;
+    hi = s;
+  }
+  __device__ __forceinline__ void add_prod(float a, float b) {
+    const float p = a * b;
+    const float pe = fmaf(a, b, -p);
+    const float s = hi + p;
+    const float bp = s - hi;
+    lo += (hi - (s - bp)) + (p - bp) + pe;
+    hi = s;
+  }
+  __device__ __forceinline__ double value() const { return (double)hi + (double)lo; }
+};
+
+// Rounding of an FP32 value to TF32 (10 explicit mantissa bits): round to nearest, ties away
+// from zero, by adding half a unit of the 13th bit to the magnitude and clearing the low 13
+// bits (a carry into the exponent gives the next power of two). Finite inputs only.
+__device__ __forceinline__ float round_tf32(float x) {
+  return __uint_as_float((__float_as_uint(x) + 0x1000u) & 0xFFFFE000u);
+}
+
 // Strict total order used by every top-k structure: larger value first, then smaller index.
 __device__ __forceinline__ bool better(float a, int ai, float b, int bi) {
   return a > b || (a == b && ai < bi);

@@ -11,23 +11,26 @@
 //   2. one block orders the tracklets by camera (stable), pads each camera's block of rows to
 //      a multiple of 128 and lays out its frames contiguously in a frame index list;
 //   3. tracklet means and camera means;
-//   4. per-camera Gram G_s on CUDA cores (upper-triangle 128 x 128 tiles, mirrored), K = the
-//      camera's frames, gathered through the frame list;
+//   4. per-camera Gram G_s on the tcgen05 tensor cores: the camera's normalised frames are
+//      written transposed (features x frames, camera blocks padded to 64 frames) as BF16
+//      hi + lo, and G_s = hi.hi^T + hi.lo^T + lo.hi^T is accumulated in FP32 (error about
+//      2^-16 relative, against 2^-11 for TF32 operands), plus lambda n_s on the diagonal; only
+//      the tiles on or above the diagonal are computed, the lower triangle is mirrored;
 //   5. conjugate gradients for all right-hand sides at once: each iteration is one
-//      (rows of P) x G_s product per camera plus one row-wise update. Since every frame has
+//      (rows of P) x G_s product per camera (tensor cores, TF32 hi + lo operands) plus one
+//      row-wise update. Since every frame has
 //      unit norm, the eigenvalues of G_s lie in [0, n_s], so cond(G_s + lambda n_s I) <=
 //      1 + 1/lambda and the iteration count needed for a relative error of 1e-7 follows
 //      from the standard CG bound 2 ((sqrt(k)-1)/(sqrt(k)+1))^m.
 #include <cmath>
 
+#include <cuda_bf16.h>
+
 #include "common.cuh"
 #include "kernels.h"
-#include "sgemm_tile.cuh"
 
 namespace gcr {
 namespace {
-
-using namespace simt;
 
 constexpr int kMaxCams = 64;
 
@@ -36,12 +39,12 @@ __global__ void frame_inv_norm_kernel(const float* __restrict__ F, int64_t nf, i
   const int64_t f = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
   if (f >= nf) return;
   const float4* x = reinterpret_cast<const float4*>(F + f * d);
-  double ss = 0.0;
+  FF acc;  // float-float: FP64 arithmetic runs at 1/64 of the FP32 rate on this GPU
   for (int v = lane; v < (d >> 2); v += 32) {
     const float4 a = x[v];
-    ss += (double)a.x * a.x + (double)a.y * a.y + (double)a.z * a.z + (double)a.w * a.w;
+    acc.add_sq(a.x); acc.add_sq(a.y); acc.add_sq(a.z); acc.add_sq(a.w);
   }
-  ss = warp_sum_d(ss);
+  const double ss = warp_sum_d(acc.value());
   if (lane == 0) inv[f] = ss > 0.0 ? (float)(1.0 / sqrt(ss)) : 0.f;
 }
 
@@ -142,6 +145,84 @@ __global__ void frame_list_kernel(const int64_t* __restrict__ off, int C, const 
   for (int64_t t = threadIdx.x; t < m; t += blockDim.x) flist[s + t] = (int)(b + t);
 }
 
+// Column blocks (64 frames each) of every camera in the transposed frame matrix Z:
+// camera s owns blocks [kstart[s], kstart[s] + knum[s]), knum[s] = ceil(n_s / 64).
+__global__ void zt_blocks_kernel(const int64_t* __restrict__ cam_nf, int ncam, int64_t* __restrict__ kstart,
+                                 int64_t* __restrict__ knum) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  int64_t b = 0;
+  for (int s = 0; s < ncam; ++s) {
+    kstart[s] = b;
+    knum[s] = (cam_nf[s] + 63) / 64;
+    b += knum[s];
+  }
+}
+
+// Z^T in BF16 hi + lo for the tensor-core Gram: column q of camera s's block range holds the
+// camera's q-th frame (frame-list order), normalised; hi = bf16(x), lo = bf16(x - hi), so that
+// hi.hi + hi.lo + lo.hi reproduces x.x' to about 2^-16 relative. Columns past n_s are zero. One
+// block per 64 columns x 64 features, transposed through shared memory.
+__global__ void __launch_bounds__(256) zt_split_kernel(const float* __restrict__ F, int d, const float* __restrict__ inv,
+                                                       const int* __restrict__ flist, const int64_t* __restrict__ foff,
+                                                       const int64_t* __restrict__ cam_nf,
+                                                       const int64_t* __restrict__ kstart,
+                                                       const int64_t* __restrict__ knum, int ncam, int64_t cols,
+                                                       __nv_bfloat16* __restrict__ zt_hi,
+                                                       __nv_bfloat16* __restrict__ zt_lo) {
+  __shared__ float tile[64][65];
+  const int64_t cb = blockIdx.x;  // column block
+  const int a0 = blockIdx.y * 64;
+  int s = -1;
+  for (int t = 0; t < ncam; ++t)
+    if (cb >= kstart[t] && cb < kstart[t] + knum[t]) s = t;
+  if (s < 0) return;  // past the last camera's blocks
+  const int64_t q0 = (cb - kstart[s]) * 64, ns = cam_nf[s];
+  // load 64 frames x 64 features (4 floats per thread per step)
+  for (int e = threadIdx.x; e < 64 * 16; e += blockDim.x) {
+    const int fr = e / 16, c4 = (e % 16) * 4;
+    float4 x = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (q0 + fr < ns && a0 + c4 < d) {
+      const int f = flist[foff[s] + q0 + fr];
+      const float sc = inv[f];
+      x = *reinterpret_cast<const float4*>(F + (size_t)f * d + a0 + c4);
+      x.x *= sc; x.y *= sc; x.z *= sc; x.w *= sc;
+    }
+    tile[fr][c4] = x.x; tile[fr][c4 + 1] = x.y; tile[fr][c4 + 2] = x.z; tile[fr][c4 + 3] = x.w;
+  }
+  __syncthreads();
+  // write 64 feature rows x 64 frame columns, two columns per thread per step
+  for (int e = threadIdx.x; e < 64 * 32; e += blockDim.x) {
+    const int a = e / 32, q = (e % 32) * 2;
+    if (a0 + a >= d) continue;
+    const float x0 = tile[q][a], x1 = tile[q + 1][a];
+    const __nv_bfloat16 h0 = __float2bfloat16_rn(x0), h1 = __float2bfloat16_rn(x1);
+    const __nv_bfloat16 l0 = __float2bfloat16_rn(x0 - __bfloat162float(h0));
+    const __nv_bfloat16 l1 = __float2bfloat16_rn(x1 - __bfloat162float(h1));
+    const size_t o = (size_t)(a0 + a) * cols + cb * 64 + q;
+    *reinterpret_cast<__nv_bfloat162*>(zt_hi + o) = __halves2bfloat162(h0, h1);
+    *reinterpret_cast<__nv_bfloat162*>(zt_lo + o) = __halves2bfloat162(l0, l1);
+  }
+}
+
+// The tensor-core Gram computes the tiles on or above the diagonal; the strictly lower
+// triangle is then copied from the upper one (32 x 32 tiles through shared memory), so G_s is
+// exactly symmetric. grid = (d/32, d/32, ncam), block (32, 8).
+__global__ void gram_mirror_kernel(float* __restrict__ G, int d) {
+  __shared__ float t[32][33];
+  const int bx = blockIdx.x, by = blockIdx.y;  // lower tile: rows by*32.., cols bx*32..
+  if (by < bx) return;
+  float* Gs = G + (size_t)blockIdx.z * d * d;
+  for (int r = threadIdx.y; r < 32; r += 8) {  // read the upper tile (rows bx*32.., cols by*32..)
+    const int a = bx * 32 + r, b = by * 32 + threadIdx.x;
+    if (a < d && b < d) t[r][threadIdx.x] = Gs[(size_t)a * d + b];
+  }
+  __syncthreads();
+  for (int r = threadIdx.y; r < 32; r += 8) {
+    const int a = by * 32 + r, b = bx * 32 + threadIdx.x;
+    if (a < d && b < d && a > b) Gs[(size_t)a * d + b] = t[threadIdx.x][r];
+  }
+}
+
 // mu[row] = mean of the tracklet's normalised frames (Eq. 10); padded rows are zero.
 __global__ void means_kernel(const float* __restrict__ F, int d, const int64_t* __restrict__ off,
                              const float* __restrict__ inv, const int* __restrict__ perm, float* __restrict__ mu) {
@@ -181,83 +262,6 @@ __global__ void cam_means_kernel(const float* __restrict__ mu, int d, const int6
   mu_cam[(size_t)s * d + a] = nf > 0 ? (float)(acc / (double)nf) : 0.f;
 }
 
-// G_s = sum over the camera's frames of x^ x^^T, upper-triangle tiles mirrored, plus
-// lambda n_s on the diagonal. grid = (d/128 tiles a, d/128 tiles b, camera).
-__global__ void __launch_bounds__(256) gram_kernel(const float* __restrict__ F, int d, const float* __restrict__ inv,
-                                                   const int* __restrict__ flist, Layout L, float lambda,
-                                                   float* __restrict__ G) {
-  const int ta = blockIdx.x, tb = blockIdx.y, s = blockIdx.z;
-  if (tb < ta) return;
-  __shared__ TileSmem sm;
-  const int tid = threadIdx.x, ty = tid >> 4, tx = tid & 15;
-  const int a0 = ta * BM, b0 = tb * BN;
-  const int64_t f0 = L.foff[s], nf = L.cam_nf[s];
-  float acc[8][8];
-#pragma unroll
-  for (int i = 0; i < 8; ++i)
-#pragma unroll
-    for (int j = 0; j < 8; ++j) acc[i][j] = 0.f;
-  // slice loader: 8 frames x 128 features; thread t -> frame t/32, features 4*(t%32)
-  auto load = [&](int64_t k0, int col0) {
-    const int kk = tid >> 5, cc = (tid & 31) * 4;
-    float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
-    if (k0 + kk < nf && col0 + cc < d) {
-      const int f = flist[f0 + k0 + kk];
-      const float sc = inv[f];
-      v = *reinterpret_cast<const float4*>(F + (size_t)f * d + col0 + cc);
-      v.x *= sc; v.y *= sc; v.z *= sc; v.w *= sc;
-    }
-    return v;
-  };
-  auto store = [&](float (*S)[PITCH], float4 v) {
-    const int kk = tid >> 5, cc = (tid & 31) * 4;
-    *reinterpret_cast<float4*>(&S[kk][cc]) = v;
-  };
-  float4 ra = load(0, a0), rb = load(0, b0);
-  store(sm.As[0], ra);
-  store(sm.Bs[0], rb);
-  __syncthreads();
-  int buf = 0;
-  for (int64_t k0 = 0; k0 < nf; k0 += BK) {
-    const bool more = k0 + BK < nf;
-    if (more) { ra = load(k0 + BK, a0); rb = load(k0 + BK, b0); }
-#pragma unroll
-    for (int kk = 0; kk < BK; ++kk) {
-      const float4 x0 = *reinterpret_cast<const float4*>(&sm.As[buf][kk][ty * 4]);
-      const float4 x1 = *reinterpret_cast<const float4*>(&sm.As[buf][kk][64 + ty * 4]);
-      const float4 y0 = *reinterpret_cast<const float4*>(&sm.Bs[buf][kk][tx * 4]);
-      const float4 y1 = *reinterpret_cast<const float4*>(&sm.Bs[buf][kk][64 + tx * 4]);
-      const float av[8] = {x0.x, x0.y, x0.z, x0.w, x1.x, x1.y, x1.z, x1.w};
-      const float bv[8] = {y0.x, y0.y, y0.z, y0.w, y1.x, y1.y, y1.z, y1.w};
-#pragma unroll
-      for (int i = 0; i < 8; ++i)
-#pragma unroll
-        for (int j = 0; j < 8; ++j) acc[i][j] = fmaf(av[i], bv[j], acc[i][j]);
-    }
-    if (more) {
-      store(sm.As[buf ^ 1], ra);
-      store(sm.Bs[buf ^ 1], rb);
-      __syncthreads();
-      buf ^= 1;
-    }
-  }
-  float* Gs = G + (size_t)s * d * d;
-  const float lam_n = lambda * (float)nf;
-#pragma unroll
-  for (int i = 0; i < 8; ++i) {
-    const int a = a0 + acc_row(ty, i);
-    if (a >= d) continue;
-#pragma unroll
-    for (int j = 0; j < 8; ++j) {
-      const int b = b0 + acc_col(tx, j);
-      if (b >= d) continue;
-      const float v = acc[i][j] + (a == b ? lam_n : 0.f);
-      Gs[(size_t)a * d + b] = v;
-      if (ta != tb) Gs[(size_t)b * d + a] = v;
-    }
-  }
-}
-
 // R = mu_c - mu_s, X = 0, P = R, rr = R.R (one warp per padded row).
 __global__ void cg_init_kernel(const float* __restrict__ mu, const float* __restrict__ mu_cam, int d,
                                const int* __restrict__ perm, const int* __restrict__ row_cam, int rows,
@@ -285,25 +289,15 @@ __global__ void cg_init_kernel(const float* __restrict__ mu, const float* __rest
   if (lane == 0) rr[r] = acc;
 }
 
-// Q = P (G_s + lambda n_s I) for each camera's 128-row blocks (G_s symmetric, so this is
-// the tile product P . G_s^T). grid = (d/128, row blocks).
-__global__ void __launch_bounds__(256) cg_apply_kernel(const float* __restrict__ P, const float* __restrict__ G, int d,
-                                                       const int* __restrict__ row_cam, float* __restrict__ Q) {
-  const int s = row_cam[blockIdx.y];
-  if (s < 0) return;
-  __shared__ TileSmem sm;
-  const int tid = threadIdx.x, ty = tid >> 4, tx = tid & 15;
-  const int r0 = blockIdx.y * BM, c0 = blockIdx.x * BN;
-  float acc[8][8];
-  tile_mma(sm, P + (size_t)r0 * d, BM, nullptr, G + (size_t)s * d * d + (size_t)c0 * d, min(BN, d - c0), d, acc);
-#pragma unroll
-  for (int i = 0; i < 8; ++i) {
-    const int r = r0 + acc_row(ty, i);
-#pragma unroll
-    for (int j = 0; j < 8; ++j) {
-      const int c = c0 + acc_col(tx, j);
-      if (c < d) Q[(size_t)r * d + c] = acc[i][j];
-    }
+// x = hi + lo with hi = tf32(x), lo = tf32(x - hi): hi.hi + hi.lo + lo.hi reproduces products to
+// about 2^-21 relative on the tensor cores.
+__global__ void split_tf32_kernel(const float* __restrict__ x, int64_t n, float* __restrict__ hi,
+                                  float* __restrict__ lo) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const float v = x[i];
+    const float h = round_tf32(v);
+    hi[i] = h;
+    lo[i] = round_tf32(v - h);
   }
 }
 
@@ -319,20 +313,21 @@ __global__ void __launch_bounds__(256) cg_update_kernel(float* __restrict__ Xs, 
   const double rr0 = rr[r];
   if (!(rr0 > 0.0)) return;
   float4 p[VPL], q[VPL];
-  double pq = 0.0;
+  FF pqa;  // float-float: FP64 arithmetic is slow on this GPU
 #pragma unroll
   for (int v = 0; v < VPL; ++v) {
     const int a = v * 128 + lane * 4;
     if (a < d) {
       p[v] = *reinterpret_cast<const float4*>(P + (size_t)r * d + a);
       q[v] = *reinterpret_cast<const float4*>(Q + (size_t)r * d + a);
-      pq += (double)p[v].x * q[v].x + (double)p[v].y * q[v].y + (double)p[v].z * q[v].z + (double)p[v].w * q[v].w;
+      pqa.add_prod(p[v].x, q[v].x); pqa.add_prod(p[v].y, q[v].y);
+      pqa.add_prod(p[v].z, q[v].z); pqa.add_prod(p[v].w, q[v].w);
     }
   }
-  pq = warp_sum_d(pq);
+  const double pq = warp_sum_d(pqa.value());
   if (!(pq > 0.0)) return;
   const float alpha = (float)(rr0 / pq);
-  double rr1 = 0.0;
+  FF rra;
   float4 rv[VPL];
 #pragma unroll
   for (int v = 0; v < VPL; ++v) {
@@ -347,10 +342,10 @@ __global__ void __launch_bounds__(256) cg_update_kernel(float* __restrict__ Xs, 
       *reinterpret_cast<float4*>(Xs + (size_t)r * d + a) = x;
       *reinterpret_cast<float4*>(R + (size_t)r * d + a) = rt;
       rv[v] = rt;
-      rr1 += (double)rt.x * rt.x + (double)rt.y * rt.y + (double)rt.z * rt.z + (double)rt.w * rt.w;
+      rra.add_sq(rt.x); rra.add_sq(rt.y); rra.add_sq(rt.z); rra.add_sq(rt.w);
     }
   }
-  rr1 = warp_sum_d(rr1);
+  const double rr1 = warp_sum_d(rra.value());
   const float beta = (float)(rr1 / rr0);
 #pragma unroll
   for (int v = 0; v < VPL; ++v) {
@@ -404,6 +399,15 @@ size_t gcrv_carve(Carve& c, int64_t F, int d, int C, int ncam, GcrvWs* w) {
   t.mu = c.take<float>((size_t)rows_cap * d);
   t.mu_cam = c.take<float>((size_t)ncam * d);
   t.G = c.take<float>((size_t)ncam * d * d);
+  t.g_hi = c.take<float>((size_t)ncam * d * d);
+  t.g_lo = c.take<float>((size_t)ncam * d * d);
+  t.p_hi = c.take<float>((size_t)rows_cap * d);
+  t.p_lo = c.take<float>((size_t)rows_cap * d);
+  t.zt_cols = (F + 63) / 64 * 64 + 64 * (int64_t)ncam;  // camera blocks padded to 64 frames
+  t.zt_hi = c.take<__nv_bfloat16>((size_t)d * t.zt_cols);
+  t.zt_lo = c.take<__nv_bfloat16>((size_t)d * t.zt_cols);
+  t.kstart = c.take<int64_t>(kMaxCams);
+  t.knum = c.take<int64_t>(kMaxCams);
   t.X = c.take<float>((size_t)rows_cap * d);
   t.R = c.take<float>((size_t)rows_cap * d);
   t.P = c.take<float>((size_t)rows_cap * d);
@@ -421,14 +425,24 @@ cudaError_t launch_gcrv(const float* frames, int64_t F, int d, const int64_t* of
   frame_list_kernel<<<C, 128, 0, st>>>(off, C, w.fstart, w.flist);
   means_kernel<<<w.rows_cap, 256, 0, st>>>(frames, d, off, w.inv, w.perm, w.mu);
   cam_means_kernel<<<dim3((d + 255) / 256, ncam), 256, 0, st>>>(w.mu, d, off, w.perm, L, w.mu_cam);
-  const int td = (d + BM - 1) / BM;
-  gram_kernel<<<dim3(td, td, ncam), 256, 0, st>>>(frames, d, w.inv, w.flist, L, lambda, w.G);
+  // G_s on the tensor cores: compensated BF16 operands of the transposed normalised frames
+  zt_blocks_kernel<<<1, 32, 0, st>>>(w.cam_nf, ncam, w.kstart, w.knum);
+  zt_split_kernel<<<dim3((unsigned)(w.zt_cols / 64), (unsigned)((d + 63) / 64)), 256, 0, st>>>(
+      frames, d, w.inv, w.flist, w.foff, w.cam_nf, w.kstart, w.knum, ncam, w.zt_cols, w.zt_hi, w.zt_lo);
+  cudaError_t e = launch_umma_gram(w.zt_hi, w.zt_lo, d, w.zt_cols, w.kstart, w.knum, w.cam_nf, ncam, lambda, w.G,
+                                   st);
+  if (e != cudaSuccess) return e;
+  gram_mirror_kernel<<<dim3((d + 31) / 32, (d + 31) / 32, ncam), dim3(32, 8), 0, st>>>(w.G, d);
   const int rows = w.rows_cap;
   cg_init_kernel<<<(rows + 7) / 8, 256, 0, st>>>(w.mu, w.mu_cam, d, w.perm, w.row_cam, rows, w.X, w.R, w.P, w.rr);
   const int iters = gcrv_iterations(lambda);
   const int vpl = (d + 127) / 128;
+  split_tf32_kernel<<<152 * 8, 256, 0, st>>>(w.G, (int64_t)ncam * d * d, w.g_hi, w.g_lo);
   for (int it = 0; it < iters; ++it) {
-    cg_apply_kernel<<<dim3(td, rows / 128), 256, 0, st>>>(w.P, w.G, d, w.row_cam, w.Q);
+    // Q = P (G_s + lambda n_s I) per camera block, on the tensor cores (TF32 hi + lo operands)
+    split_tf32_kernel<<<152 * 8, 256, 0, st>>>(w.P, (int64_t)rows * d, w.p_hi, w.p_lo);
+    e = launch_umma_mul(w.p_hi, w.p_lo, rows, w.g_hi, w.g_lo, ncam, d, w.row_cam, w.Q, st);
+    if (e != cudaSuccess) return e;
     if (vpl <= 2) cg_update_kernel<2><<<(rows + 7) / 8, 256, 0, st>>>(w.X, w.R, w.P, w.Q, w.rr, w.perm, rows, d);
     else if (vpl <= 4) cg_update_kernel<4><<<(rows + 7) / 8, 256, 0, st>>>(w.X, w.R, w.P, w.Q, w.rr, w.perm, rows, d);
     else if (vpl <= 8) cg_update_kernel<8><<<(rows + 7) / 8, 256, 0, st>>>(w.X, w.R, w.P, w.Q, w.rr, w.perm, rows, d);

@@ -53,6 +53,17 @@ cudaError_t launch_umma_band(const void* Xb, int n, int d, Elt elt, const int* c
                              int* band_i, cudaStream_t st);
 cudaError_t launch_umma_dist(const __nv_bfloat16* Qb, int nq, const __nv_bfloat16* Gb, int ng, int d,
                              const float* nrm_q, const float* nrm_g, float* D, cudaStream_t st);
+// G_s = Z_s Z_s^T + lambda n_s I for every camera s (d x d, FP32, [ncam][d][d]), Z the
+// transposed normalised frames (d rows, cols columns), split hi + lo in BF16 (hi.hi + hi.lo +
+// lo.hi); camera s owns the column blocks of 64 [kstart[s], kstart[s] + knum[s]).
+cudaError_t launch_umma_gram(const __nv_bfloat16* zt_hi, const __nv_bfloat16* zt_lo, int d, int64_t cols,
+                             const int64_t* kstart, const int64_t* knum, const int64_t* nf, int ncam, float lambda,
+                             float* G, cudaStream_t st);
+// Q = P G_s for each 128-row block of P (camera s = rowcam[block]; blocks with s < 0 are
+// skipped), TF32 operands split hi + lo (hi.hi + hi.lo + lo.hi); G stacked as ncam*d rows of d
+// (symmetric, so its rows are the K-major B operand).
+cudaError_t launch_umma_mul(const float* p_hi, const float* p_lo, int rows, const float* g_hi, const float* g_lo,
+                            int ncam, int d, const int* rowcam, float* Q, cudaStream_t st);
 int umma_read_and_clear_timeouts();
 cudaError_t launch_wait_probe(unsigned long long limit_ns, cudaStream_t st);  // bounded waits that ran out since the last call (-1: error)
 
@@ -143,6 +154,15 @@ struct GcrvWs {
   float* mu;
   float* mu_cam;
   float* G;
+  __nv_bfloat16* zt_hi;     // [d][cols] transposed normalised frames, camera blocks padded to 64
+  __nv_bfloat16* zt_lo;
+  int64_t zt_cols;
+  float* g_hi;              // [ncam][d][d] G in TF32 hi + lo
+  float* g_lo;
+  float* p_hi;              // [rows_cap][d] the CG direction in TF32 hi + lo
+  float* p_lo;
+  int64_t* kstart;          // [kMaxCams] first 64-column block of each camera
+  int64_t* knum;            // [kMaxCams] 64-column blocks of each camera
   float* X;
   float* R;
   float* P;

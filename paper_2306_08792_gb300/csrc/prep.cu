@@ -6,23 +6,6 @@
 
 namespace gcr {
 
-// Float-float accumulation of sum x^2 without FP64 arithmetic (GB300's FP64 rate is low):
-// each product is split exactly (x*x = p + pe with an FMA), each addition is an exact TwoSum
-// into (hi, lo); the result is accurate to about 2^-46 relative, well below the 1e-12 the
-// FP64 tie-break needs from the squared norms.
-struct FF {
-  float hi = 0.f, lo = 0.f;
-  __device__ __forceinline__ void add_sq(float x) {
-    const float p = x * x;
-    const float pe = fmaf(x, x, -p);
-    const float s = hi + p;
-    const float bp = s - hi;
-    lo += (hi - (s - bp)) + (p - bp) + pe;
-    hi = s;
-  }
-  __device__ __forceinline__ double value() const { return (double)hi + (double)lo; }
-};
-
 // X_out[i] = X_in[i] / ||X_in[i]||: the squared norm is accumulated exactly (float-float,
 // combined in FP64 once per row) and 1/||x|| is formed in FP64, so each output element is the
 // FP32 rounding of x * fl32(1/||x||), within one ulp of the exact quotient. One warp per row.
@@ -45,13 +28,6 @@ __global__ void normalize_kernel(const float* __restrict__ X_in, float* __restri
     float4 x = src[v];
     dst[v] = make_float4(x.x * inv, x.y * inv, x.z * inv, x.w * inv);
   }
-}
-
-// Rounding of an FP32 value to TF32 (10 explicit mantissa bits): round to nearest, ties away
-// from zero, by adding half a unit of the 13th bit to the magnitude and clearing the low 13
-// bits (a carry into the exponent gives the next power of two). Finite inputs only.
-__device__ __forceinline__ float round_tf32(float x) {
-  return __uint_as_float((__float_as_uint(x) + 0x1000u) & 0xFFFFE000u);
 }
 
 // n64[i] = ||x_i||^2 (float-float accumulation, combined in FP64), n32[i] = its FP32 rounding;

@@ -41,7 +41,7 @@ constexpr int STAGE_BYTES = A_BYTES + B_BYTES;
 constexpr uint32_t TMEM_COLS = 512;
 constexpr unsigned long long kTimeoutNs = 2000000000ull;
 
-enum Mode { POOL = 0, BAND = 1, DIST = 2 };
+enum Mode { POOL = 0, BAND = 1, DIST = 2, GRAM = 3, MUL = 4 };
 
 // ------------------------------------------------------------------------ PTX wrappers
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
@@ -187,6 +187,17 @@ struct UmmaArgs {
   const float* nrm_q;
   const float* nrm_g;
   float* D;
+  // GRAM: G_s = Z_s Z_s^T + lambda n_s I per camera s = blockIdx.z, Z = the transposed,
+  // normalised frames (feature rows, frame columns) split as hi + lo in BF16; K blocks of 64
+  // frames [gram_kstart[s], + gram_knum[s]) run three times: hi.hi, hi.lo, lo.hi
+  const int64_t* gram_kstart;
+  const int64_t* gram_knum;
+  const int64_t* gram_nf;  // n_s
+  float gram_lambda;
+  float* G;                // [ncam][d][d]
+  // MUL: Q = P G_s for each 128-row block of P (camera s = mul_rowcam[block], < 0: skipped);
+  // TF32 operands split hi + lo (hi.hi + hi.lo + lo.hi); G stacked as ncam * d rows of d
+  const int* mul_rowcam;
   int dist_nrb;    // row tiles of the distance matrix
   int dist_tiles;  // all tiles; CTA b takes tiles b, b + grid, ... in column-major tile order,
                    // so the CTAs at work share the (small) query blocks and stream each gallery
@@ -208,11 +219,13 @@ struct Tiles {
   int count;
   __device__ int row0(const UmmaArgs& a, int t) const {
     if (a.mode == POOL) return blockIdx.x * BM;
+    if (a.mode == GRAM || a.mode == MUL) return blockIdx.y * BM;
     if (a.mode == BAND) return (blockIdx.y + t * gridDim.y) * BM;  // row tiles strided over grid.y
     return (((int)blockIdx.x + t * (int)gridDim.x) % a.dist_nrb) * BM;
   }
   __device__ int col0(const UmmaArgs& a, int t) const {
     if (a.mode == POOL) return (blockIdx.y * a.tps + t) * BN;
+    if (a.mode == GRAM || a.mode == MUL) return blockIdx.x * BN;
     if (a.mode == BAND) return blockIdx.x * BN;
     return (((int)blockIdx.x + t * (int)gridDim.x) / a.dist_nrb) * BN;
   }
@@ -220,7 +233,8 @@ struct Tiles {
 
 template <int KP, bool CROSS>
 __global__ void __launch_bounds__(320, 1)
-umma_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, UmmaArgs a) {
+umma_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
+            const __grid_constant__ CUtensorMap tmA2, const __grid_constant__ CUtensorMap tmB2, UmmaArgs a) {
   extern __shared__ __align__(1024) unsigned char dyn_raw[];
   unsigned char* dyn = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(dyn_raw) + 1023) & ~uintptr_t(1023));
   unsigned char* stages = dyn;                                        // NST * STAGE_BYTES
@@ -229,7 +243,11 @@ umma_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int bk = a.tf32 ? BKB / 4 : BKB / 2;  // K elements per stage
-  const int kb_count = (a.d + bk - 1) / bk;
+  // K blocks per tile (GRAM: three passes over the camera's frame blocks)
+  const int gram_kn = a.mode == GRAM ? (int)a.gram_knum[blockIdx.z] : (a.d + bk - 1) / bk;
+  const int kb_count = (a.mode == GRAM || a.mode == MUL) ? 3 * gram_kn : (a.d + bk - 1) / bk;
+  // MUL: rows of camera s's G_s in the stacked G
+  const int mul_b0 = a.mode == MUL ? max(0, a.mul_rowcam[blockIdx.y]) * a.n : 0;
 
   Tiles tl;
   if (a.mode == POOL) tl.count = max(0, min(a.tps, (a.n + BN - 1) / BN - (int)blockIdx.y * a.tps));
@@ -237,6 +255,11 @@ umma_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
     const int U = min(*a.count, a.cap);
     const int tiles = (U + BM - 1) / BM;
     tl.count = max(0, (tiles - (int)blockIdx.y + (int)gridDim.y - 1) / (int)gridDim.y);
+  } else if (a.mode == GRAM) {
+    // G_s is symmetric: tiles wholly below the diagonal (every column < every row) are mirrored
+    tl.count = ((int)blockIdx.x + 1) * BN <= (int)blockIdx.y * BM ? 0 : 1;
+  } else if (a.mode == MUL) {
+    tl.count = a.mul_rowcam[blockIdx.y] >= 0 ? 1 : 0;
   } else {
     tl.count = max(0, (a.dist_tiles - (int)blockIdx.x + (int)gridDim.x - 1) / (int)gridDim.x);
   }
@@ -278,8 +301,20 @@ umma_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
           if (!mbar_wait(&bars.empty[s], (round & 1) ^ 1, abort_flag)) break;
           unsigned char* sa = stages + s * STAGE_BYTES;
           mbar_arrive_expect_tx(&bars.full[s], STAGE_BYTES);
-          tma_load_2d(sa, &tmA, &bars.full[s], kb * bk, r0);
-          tma_load_2d(sa + A_BYTES, &tmB, &bars.full[s], kb * bk, c0);
+          if (a.mode == GRAM) {
+            const int pass = kb / gram_kn;
+            const int x = (int)((a.gram_kstart[blockIdx.z] + kb % gram_kn) * bk);
+            tma_load_2d(sa, pass == 2 ? &tmA2 : &tmA, &bars.full[s], x, r0);
+            tma_load_2d(sa + A_BYTES, pass == 1 ? &tmB2 : &tmB, &bars.full[s], x, c0);
+          } else if (a.mode == MUL) {
+            const int pass = kb / gram_kn;
+            const int x = (kb % gram_kn) * bk;
+            tma_load_2d(sa, pass == 2 ? &tmA2 : &tmA, &bars.full[s], x, r0);
+            tma_load_2d(sa + A_BYTES, pass == 1 ? &tmB2 : &tmB, &bars.full[s], x, mul_b0 + c0);
+          } else {
+            tma_load_2d(sa, &tmA, &bars.full[s], kb * bk, r0);
+            tma_load_2d(sa + A_BYTES, &tmB, &bars.full[s], kb * bk, c0);
+          }
         }
       }
       // in-flight loads land before the CTA can exit: wait for the last armed stages
@@ -370,6 +405,11 @@ umma_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
       } else if (a.mode == DIST) {
         my_row = r0 + r;
         my_nq = my_row < a.a_rows ? a.nrm_q[my_row] : 0.f;
+      } else if (a.mode == MUL) {
+        my_row = r0 + r;
+      } else if (a.mode == GRAM) {
+        my_row = r0 + r;
+        my_nq = a.gram_lambda * (float)a.gram_nf[blockIdx.z];  // lambda n_s, added on the diagonal
       }
       const int ncol = min(BN, a.n - c0);
       for (int ch = 0; ch < BN / 32; ++ch) {
@@ -414,6 +454,21 @@ umma_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
                 a.band_i[(size_t)u * a.bcap + pos] = j;
               }
             }
+          }
+        } else if (a.mode == MUL) {
+          if (kind == 0 && my_row < a.a_rows) {
+            float* out = a.D + (size_t)my_row * a.n + cb;
+#pragma unroll
+            for (int cc = 0; cc < 32; ++cc)
+              if (cb + cc < a.n) out[cc] = v[cc];
+          }
+        } else if (a.mode == GRAM) {
+          if (kind == 0 && my_row < a.a_rows) {
+            float* out = a.G + ((size_t)blockIdx.z * a.a_rows + my_row) * a.n + cb;
+            const bool none = gram_kn == 0;  // a camera without frames: no MMA wrote the accumulator
+#pragma unroll
+            for (int cc = 0; cc < 32; ++cc)
+              if (cb + cc < a.n) out[cc] = (none ? 0.f : v[cc]) + (cb + cc == my_row ? my_nq : 0.f);
           }
         } else {
           if (kind == 0) {
@@ -504,12 +559,13 @@ size_t smem_bytes(int mode) {
 }
 
 template <int KP, bool CROSS>
-cudaError_t launch(const CUtensorMap& ta, const CUtensorMap& tb, const UmmaArgs& a, dim3 grid, cudaStream_t st) {
+cudaError_t launch(const CUtensorMap& ta, const CUtensorMap& tb, const UmmaArgs& a, dim3 grid, cudaStream_t st,
+                   const CUtensorMap* ta2 = nullptr, const CUtensorMap* tb2 = nullptr) {
   auto fn = umma_kernel<KP, CROSS>;
   const size_t smem = smem_bytes(a.mode);
   cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  fn<<<grid, CROSS ? 320 : 192, smem, st>>>(ta, tb, a);
+  fn<<<grid, CROSS ? 320 : 192, smem, st>>>(ta, tb, ta2 ? *ta2 : ta, tb2 ? *tb2 : tb, a);
   return cudaGetLastError();
 }
 
@@ -613,6 +669,56 @@ cudaError_t launch_umma_dist(const __nv_bfloat16* Qb, int nq, const __nv_bfloat1
   a.dist_tiles = a.dist_nrb * ((ng + BN - 1) / BN);
   dim3 grid((unsigned)std::max(1, std::min(a.dist_tiles, 152)));
   return launch<64, false>(ta, tb, a, grid, st);
+}
+
+cudaError_t launch_umma_gram(const __nv_bfloat16* zt_hi, const __nv_bfloat16* zt_lo, int d, int64_t cols,
+                             const int64_t* kstart, const int64_t* knum, const int64_t* nf, int ncam, float lambda,
+                             float* G, cudaStream_t st) {
+  if (cols > INT32_MAX || cols % 8) return cudaErrorInvalidValue;
+  CUtensorMap ta, tb, ta2, tb2;
+  cudaError_t e = make_map(&ta, zt_hi, Elt::BF16, d, (int)cols, BM);
+  if (e != cudaSuccess) return e;
+  e = make_map(&tb, zt_hi, Elt::BF16, d, (int)cols, BN);
+  if (e != cudaSuccess) return e;
+  e = make_map(&ta2, zt_lo, Elt::BF16, d, (int)cols, BM);
+  if (e != cudaSuccess) return e;
+  e = make_map(&tb2, zt_lo, Elt::BF16, d, (int)cols, BN);
+  if (e != cudaSuccess) return e;
+  UmmaArgs a{};
+  a.mode = GRAM;
+  a.n = d;
+  a.d = 64;  // unused: the K extent of a tile comes from gram_knum
+  a.a_rows = d;
+  a.gram_kstart = kstart;
+  a.gram_knum = knum;
+  a.gram_nf = nf;
+  a.gram_lambda = lambda;
+  a.G = G;
+  dim3 grid((d + BN - 1) / BN, (d + BM - 1) / BM, ncam);
+  return launch<64, false>(ta, tb, a, grid, st, &ta2, &tb2);
+}
+
+cudaError_t launch_umma_mul(const float* p_hi, const float* p_lo, int rows, const float* g_hi, const float* g_lo,
+                            int ncam, int d, const int* rowcam, float* Q, cudaStream_t st) {
+  CUtensorMap ta, tb, ta2, tb2;
+  cudaError_t e = make_map(&ta, p_hi, Elt::TF32, rows, d, BM);
+  if (e != cudaSuccess) return e;
+  e = make_map(&ta2, p_lo, Elt::TF32, rows, d, BM);
+  if (e != cudaSuccess) return e;
+  e = make_map(&tb, g_hi, Elt::TF32, ncam * d, d, BN);
+  if (e != cudaSuccess) return e;
+  e = make_map(&tb2, g_lo, Elt::TF32, ncam * d, d, BN);
+  if (e != cudaSuccess) return e;
+  UmmaArgs a{};
+  a.mode = MUL;
+  a.tf32 = 1;
+  a.n = d;
+  a.d = d;
+  a.a_rows = rows;
+  a.mul_rowcam = rowcam;
+  a.D = Q;
+  dim3 grid((d + BN - 1) / BN, (rows + BM - 1) / BM);
+  return launch<64, false>(ta, tb, a, grid, st, &ta2, &tb2);
 }
 
 }  // namespace gcr
