@@ -299,6 +299,22 @@ def serving_bench(gcr, torch, precision, n_requests):
     t0 = time.perf_counter()
     G = Gallery(torch.from_numpy(w.gallery).cuda(), p)
     build_s = time.perf_counter() - t0
+    # device time of one gcr_serve call per batch size (CUDA events, after warm-up)
+    per_batch = {}
+    for b in (1, 8, 64, 512):
+        q = torch.from_numpy(w.queries_of(b)).cuda()
+        for _ in range(3):
+            G.query(q)
+        torch.cuda.synchronize()
+        ts = []
+        for _ in range(10):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            G.query(q)
+            e1.record()
+            e1.synchronize()
+            ts.append(e0.elapsed_time(e1))
+        per_batch[str(b)] = round(statistics.median(ts), 3)
     srv = Server(G, n_slots=4, max_batch=512)
     srv.warmup()
     rt = srv.run(make_requests(w, n_requests))
@@ -309,6 +325,7 @@ def serving_bench(gcr, torch, precision, n_requests):
             "offered_requests_per_s": 200.0, "requests": n_requests,
             "p50_ms": rt["p50_ms"], "p99_ms": rt["p99_ms"], "queries_per_s": rt["queries_per_s"],
             "saturation_queries_per_s": sat["queries_per_s"], "saturation_p99_ms": sat["p99_ms"],
+            "batch_device_ms": per_batch,
             "launches": rt["launches"]}
 
 

@@ -179,6 +179,14 @@ class ServingWorkload:
     batch: np.ndarray            # int32 [R] queries per request
     seed: int
 
+    def queries_of(self, b: int, tag: int = 1 << 30) -> np.ndarray:
+        """b query rows drawn like a request's (seeded by b and a tag outside request indices)."""
+        rng = np.random.default_rng((self.seed, tag, b))
+        cl = rng.integers(0, self.centroids.shape[0], size=b)
+        q = self.centroids[cl] + np.float32(self.sigma) * rng.standard_normal(
+            (b, self.centroids.shape[1]), dtype=np.float32)
+        return q.astype(np.float32)
+
     def queries(self, r: int) -> np.ndarray:
         """Query features of request r (seeded by the request index)."""
         rng = np.random.default_rng((self.seed, r))
