@@ -73,10 +73,10 @@ sgemm_pool_kernel(const float* __restrict__ A, int na, const float* __restrict__
     if (CROSS && tid < BN) cam_tile[tid] = (col0 + tid < nb) ? cam[col0 + tid] : -1;
     __syncthreads();
     if (kind == 0 || CROSS) {
-      for (int c0 = 0; c0 < brows; c0 += 8) {
-        pool_make_room<KP>(8, lane, me, warp_row0, warp_qrow0, q, pv, pi);
+      for (int c0 = 0; c0 < brows; c0 += 4) {  // queues fill to 28 of 32 before a merge
+        pool_make_room<KP>(4, lane, me, warp_row0, warp_qrow0, q, pv, pi);
 #pragma unroll
-        for (int c = 0; c < 8; ++c) {
+        for (int c = 0; c < 4; ++c) {
           const int cc = c0 + c;
           const int j = col0 + cc;
           float v = S[r][cc];
