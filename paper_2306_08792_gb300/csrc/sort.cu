@@ -4,8 +4,9 @@
 // index, and the first K (index, distance) pairs are written out. One CTA per query sorts the
 // whole segment (up to 16384 keys):
 //  * segments of 2048 keys and more: a stable LSD radix sort of the order-preserving 32-bit
-//    images of the distances, four 8-bit digit passes (a pass whose digit is the same for
-//    every key of the segment is skipped). Keys start in gallery-index order and every pass is
+//    images of the distances taken relative to the segment's smallest, in 8-bit digit passes
+//    over the bits that range needs, or three 9-bit passes when it needs 25 to 27 bits (the
+//    usual case for one query's distances). Keys start in gallery-index order and every pass is
 //    stable, so equal distances stay in index order. Each thread keeps 16 keys in registers in
 //    a warp-striped layout (key e = (warp*16 + slot)*32 + lane); per pass a warp ranks its keys
 //    slot by slot with __match_any_sync (peers with the same digit, ranked by lane), per-warp
@@ -129,7 +130,7 @@ __global__ void __launch_bounds__(1024) rank_rows_kernel(const float* __restrict
 
 
 // ---------------------------------------------------------------------------- radix sort
-constexpr int kHistStride = 257;  // per-warp digit counts, padded against bank conflicts in the scan
+constexpr int kHistStride = 513;  // per-warp digit counts (up to 9-bit digits), padded against bank conflicts
 
 // NT threads (NW = NT/32 warps, a multiple of 8), IPT keys per thread (even), segment <= NT*IPT.
 // Keys live in registers; the gallery indices live in shared memory (two buffers, swapped per
@@ -139,7 +140,6 @@ __global__ void __launch_bounds__(NT, 1)
 rank_rows_radix_kernel(const float* __restrict__ D, int ng, int K, int32_t* __restrict__ idx_out,
                        float* __restrict__ dist_out) {
   constexpr int NW = NT / 32;
-  constexpr int GPD = NW / 8;  // scan threads per digit (8 warp counts each)
   constexpr int N = NT * IPT;
   static_assert(NW % 8 == 0 && IPT % 2 == 0, "warps: a multiple of 8; keys per thread: even");
   static_assert(N <= 65536, "gallery indices are held in 16 bits");
@@ -148,7 +148,7 @@ rank_rows_radix_kernel(const float* __restrict__ D, int ng, int K, int32_t* __re
   uint16_t* si0 = reinterpret_cast<uint16_t*>(sk + N);            // [N] gallery indices
   uint16_t* si1 = si0 + N;                                        // [N] (second buffer)
   uint32_t* hist = reinterpret_cast<uint32_t*>(si1 + N);          // [NW][kHistStride]
-  __shared__ uint32_t red_and[NW], red_or[NW], wsum[NW];
+  __shared__ uint32_t red_min[NW], red_max[NW], wsum[NW];
 
   const int q = blockIdx.x;
   const int t = threadIdx.x, lane = t & 31, w = t >> 5;
@@ -157,44 +157,51 @@ rank_rows_radix_kernel(const float* __restrict__ D, int ng, int K, int32_t* __re
   const float* row = D + (size_t)q * ng;
   uint32_t key[IPT];
   uint32_t offp[IPT / 2];
-  uint32_t kand = 0xffffffffu, kor = 0u;
+  uint32_t kmin = 0xffffffffu, kmax = 0u;
 #pragma unroll
   for (int i = 0; i < IPT; ++i) {
     const int e = e0 + 32 * i;
-    key[i] = e < ng ? float_to_ordered(row[e]) : 0xffffffffu;  // padding sorts last (larger index)
+    key[i] = e < ng ? float_to_ordered(row[e]) : 0xffffffffu;
     si0[e] = (uint16_t)e;
     if (e < ng) {
-      kand &= key[i];
-      kor |= key[i];
+      kmin = min(kmin, key[i]);
+      kmax = max(kmax, key[i]);
     }
   }
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) {
-    kand &= __shfl_xor_sync(GCR_FULL, kand, o);
-    kor |= __shfl_xor_sync(GCR_FULL, kor, o);
+    kmin = min(kmin, __shfl_xor_sync(GCR_FULL, kmin, o));
+    kmax = max(kmax, __shfl_xor_sync(GCR_FULL, kmax, o));
   }
-  if (lane == 0) { red_and[w] = kand; red_or[w] = kor; }
+  if (lane == 0) { red_min[w] = kmin; red_max[w] = kmax; }
   __syncthreads();
-  // the bits in which the real keys differ: a digit they all share needs no pass (the padding
-  // keys are all ones, so they stay after every real key on the remaining digits)
-  uint32_t diff;
-  {
-    uint32_t a = 0xffffffffu, o = 0u;
-    for (int v = 0; v < NW; ++v) { a &= red_and[v]; o |= red_or[v]; }
-    diff = a ^ o;
-  }
+  for (int v = 0; v < NW; ++v) { kmin = min(kmin, red_min[v]); kmax = max(kmax, red_max[v]); }
+  // Keys relative to the smallest (order-preserving): their range needs nb bits, usually far
+  // fewer than 32 (distances of one query span a narrow band), so three 9-bit digit passes
+  // often suffice where four 8-bit ones would be needed. Padding keys are all ones and stay
+  // after every real key (on ties the stable passes keep their larger positions last).
+  const uint32_t range = kmax - kmin;
+  const int nb = range == 0 ? 0 : 32 - __clz((int)range);
+  int W = 8, passes = (nb + 7) / 8;
+  if (NT >= 512 && nb > 24 && nb <= 27) { W = 9; passes = 3; }  // a scan thread per digit at least
+  const uint32_t B = 1u << W, mask = B - 1u;
+#pragma unroll
+  for (int i = 0; i < IPT; ++i)
+    if (e0 + 32 * i < ng) key[i] -= kmin;
+  const int TPD = NT / (int)B;       // scan threads per digit
+  const int WPT = NW / TPD;          // warp counts per scan thread
 
   uint32_t* hw = hist + w * kHistStride;
   uint16_t* src = si0;
   uint16_t* dstb = si1;
-  for (int shift = 0; shift < 32; shift += 8) {
-    if (((diff >> shift) & 255u) == 0) continue;  // block-uniform
+  for (int pass = 0; pass < passes; ++pass) {  // block-uniform
+    const int shift = pass * W;
     for (int v = t; v < NW * kHistStride; v += NT) hist[v] = 0;
     __syncthreads();
     // per-warp stable ranking, slot by slot (slot order = key order inside the warp)
 #pragma unroll
     for (int i = 0; i < IPT; ++i) {
-      const uint32_t dg = (key[i] >> shift) & 255u;
+      const uint32_t dg = (key[i] >> shift) & mask;
       const unsigned peers = __match_any_sync(GCR_FULL, dg);
       const uint32_t base = hw[dg];
       __syncwarp();
@@ -205,12 +212,11 @@ rank_rows_radix_kernel(const float* __restrict__ D, int ng, int K, int32_t* __re
       else offp[i >> 1] = off;
     }
     __syncthreads();
-    // exclusive scan of the counts in (digit, warp) order: thread t owns digit t / GPD and the
-    // warps 8 * (t % GPD) .. + 7
-    const int sdg = t / GPD, sw0 = (t % GPD) * 8;
+    // exclusive scan of the counts in (digit, warp) order: thread t owns digit t / TPD and the
+    // warps WPT * (t % TPD) .. + WPT - 1
+    const int sdg = t / TPD, sw0 = (t % TPD) * WPT;
     uint32_t tot = 0;
-#pragma unroll
-    for (int j = 0; j < 8; ++j) tot += hist[(sw0 + j) * kHistStride + sdg];
+    for (int j = 0; j < WPT; ++j) tot += hist[(sw0 + j) * kHistStride + sdg];
     uint32_t inc = tot;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
@@ -221,8 +227,7 @@ rank_rows_radix_kernel(const float* __restrict__ D, int ng, int K, int32_t* __re
     __syncthreads();
     uint32_t run = inc - tot;
     for (int v = 0; v < w; ++v) run += wsum[v];
-#pragma unroll
-    for (int j = 0; j < 8; ++j) {  // each thread rewrites only its own counts
+    for (int j = 0; j < WPT; ++j) {  // each thread rewrites only its own counts
       const uint32_t cj = hist[(sw0 + j) * kHistStride + sdg];
       hist[(sw0 + j) * kHistStride + sdg] = run;
       run += cj;
@@ -232,7 +237,7 @@ rank_rows_radix_kernel(const float* __restrict__ D, int ng, int K, int32_t* __re
 #pragma unroll
     for (int i = 0; i < IPT; ++i) {
       const uint32_t off = (i & 1) ? (offp[i >> 1] >> 16) : (offp[i >> 1] & 0xffffu);
-      const uint32_t dst = hw[(key[i] >> shift) & 255u] + off;
+      const uint32_t dst = hw[(key[i] >> shift) & mask] + off;
       sk[dst] = key[i];
       dstb[dst] = src[e0 + 32 * i];
     }
@@ -250,7 +255,7 @@ rank_rows_radix_kernel(const float* __restrict__ D, int ng, int K, int32_t* __re
     const int e = e0 + 32 * i;
     if (e < K) {
       idx_out[(size_t)q * K + e] = (int32_t)src[e];
-      dist_out[(size_t)q * K + e] = ordered_to_float(key[i]);
+      dist_out[(size_t)q * K + e] = ordered_to_float(key[i] + kmin);
     }
   }
 }
