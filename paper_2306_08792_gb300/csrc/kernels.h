@@ -14,7 +14,7 @@ inline size_t elt_bytes(Elt e) { return e == Elt::TF32 ? 4 : 2; }
 // Per-call scalars reduced over the rows of X (device memory).
 struct RowScalars {
   double nmin, nmax;   // min / max of ||x_j||^2
-  double bmax;         // max ||x_j||
+  double bmax;         // max ||x_j||: formed by the reader from nmax
   double emax;         // max ||round(x_j) - x_j||   (tensor-core paths)
   double amax;         // max ||round(x_j)||         (tensor-core paths)
 };

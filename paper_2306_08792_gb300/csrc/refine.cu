@@ -313,6 +313,7 @@ template <int P>
 __device__ __forceinline__ void bounds(const RefineArgs& a, int row, int vpl, double& delta, double& eps,
                                        RowScalars& sc) {
   sc = *a.sc;
+  sc.bmax = sqrt(sc.nmax) * (1.0 + 1e-12);  // max ||x_j||, rounded up
   const double b_i = sqrt(a.n64[row]);
   if (a.precision == GCR_PREC_FP32) {
     delta = gamma_n((double)a.d, kU32) * b_i * sc.bmax;
