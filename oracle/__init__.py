@@ -8,3 +8,4 @@ code with the CUDA path.
 from .gcr_oracle import *  # noqa: F401,F403
 from .pvg_oracle import *  # noqa: F401,F403
 from .serve_oracle import *  # noqa: F401,F403
+from .dsfp_oracle import *  # noqa: F401,F403
