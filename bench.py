@@ -49,6 +49,7 @@ def _args():
     ap.add_argument("--no-serving", action="store_true")
     ap.add_argument("--no-zipf", action="store_true", help="skip the 200,000-row Zipf workload")
     ap.add_argument("--no-video", action="store_true", help="skip the GCRV video workload")
+    ap.add_argument("--no-local", action="store_true", help="skip the DSFP (Algorithm 1) comparison")
     ap.add_argument("--serving-requests", type=int, default=800)
     ap.add_argument("--pool", type=int, default=0, help="candidate pool per row (0: library default)")
     return ap.parse_args()
@@ -431,6 +432,73 @@ def video_bench(gcr, torch, precision, steps, warmup):
             "gram_tflops": 2.0 * d * d * F / (statistics.mean(prof) / 1e3) / 1e12}
 
 
+def local_bench(gcr, torch, w, X, precision, steps, warmup):
+    """DSFP (Algorithm 1, "GCR_Local" of the paper's timing table) against global GCR with the
+    same plain graph, on the crosscam features (19,281 x 2048, no camera graph), k = 20,
+    T = 2, gamma = 0.2, full ranking: one step = the feature update plus the re-ranking
+    (gcr_dsfp then gcr_rerank, against gcr_pipeline). Stage times from the stage profiler."""
+    from paper_2306_08792_gb300 import _lib
+    import ctypes
+    p = gcr.default_params(k=w.k, T=w.T, gamma=w.gamma, cross_camera=0, precision=precision)
+    ds = gcr.Dsfp(w.n, w.d, p)
+    pl = gcr.Pipeline(w.n, w.n_query, w.d, p)
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device="cuda")
+    stream = torch.cuda.current_stream()
+    nq = w.n_query
+
+    def dsfp_step():
+        out = ds(X)
+        gcr.gcr_rerank(out[:nq], out[nq:], p)
+
+    def gcr_step():
+        pl(X, None, keep_features=False)
+
+    lib = _lib.load()
+    S = _lib.GCR_STAGES
+    res = {}
+    for name, fn in (("dsfp", dsfp_step), ("gcr_plain", gcr_step)):
+        for _ in range(warmup):
+            fn()
+        torch.cuda.synchronize()
+        lib.gcr_profile_enable(1)
+        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+        for s in range(steps):
+            flush.zero_()
+            evs[s][0].record(stream)
+            fn()
+            evs[s][1].record(stream)
+        torch.cuda.synchronize()
+        ms_arr = (ctypes.c_double * S)()
+        la = (ctypes.c_int64 * S)()
+        ca = (ctypes.c_int64 * S)()
+        lib.gcr_profile_read(ms_arr, la, ca, S)
+        lib.gcr_profile_enable(0)
+        res[name] = {"ms": statistics.mean([a.elapsed_time(b) for a, b in evs]),
+                     "stages": {nm: round(ms_arr[i] / steps, 4) for i, nm in enumerate(_lib.STAGE_NAMES)}}
+    m = w.k + 1
+    # the local kernel (stage "propagate" of gcr_dsfp): m(m+1)/2 Gram dot products and the
+    # m-term output row per image, 2 FLOP per multiply-add
+    flops = w.n * (m * (m + 1) / 2 + m) * w.d * 2.0
+    kms = res["dsfp"]["stages"]["propagate"]
+    peaks, psrc = _peaks()
+    alu = N_SMS * FP32_LANES_PER_SM * 2 * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
+    del ds, pl
+    torch.cuda.empty_cache()
+    return {"workload": f"crosscam features ({w.n:,} x {w.d}) with the plain graph (no camera graph), k={w.k}, "
+                        f"T={w.T}, gamma={w.gamma}, full ranking",
+            "precision": precision, "steps": steps, "warmup": warmup,
+            "dsfp_ms_per_step": res["dsfp"]["ms"], "dsfp_queries_per_s": nq / (res["dsfp"]["ms"] / 1e3),
+            "gcr_plain_ms_per_step": res["gcr_plain"]["ms"],
+            "gcr_plain_queries_per_s": nq / (res["gcr_plain"]["ms"] / 1e3),
+            "speedup_dsfp_vs_gcr": res["gcr_plain"]["ms"] / res["dsfp"]["ms"],
+            "dsfp_stages_ms": res["dsfp"]["stages"], "gcr_plain_stages_ms": res["gcr_plain"]["stages"],
+            "local_kernel": {"kernel": "dsfp_kernel", "bound": "alu", "ms": kms, "flops": flops,
+                             "achieved_tflops": flops / (kms / 1e3) / 1e12 if kms > 0 else None, "peak": alu,
+                             "frac": flops / (kms / 1e3) / 1e12 / alu if kms > 0 else None,
+                             "peak_source": f"FP32 FMA: 152 SMs x 128 lanes x 2 x sm_max_mhz of {psrc}"},
+            "paper": "Sec. IV-F timing table (24-core CPU, Market-1501): GCR 24 s, GCR_Local 10 s"}
+
+
 def max_over_ranks(value: float, dist, device=None) -> float:
     """Largest value over all ranks (the slowest replica sets the job's time)."""
     if dist is None:
@@ -560,6 +628,11 @@ def run_ours(a):
             line["zipf"] = zipf_bench(gcr, torch, primary if primary != "fp32" else "tf32", 3, 3)
         except gcr.GcrError as e:
             line["zipf"] = {"error": str(e)}
+    if rank == 0 and world == 1 and not a.no_local:
+        try:
+            line["local"] = local_bench(gcr, torch, w, X, primary if primary != "fp32" else "tf32", 5, 3)
+        except gcr.GcrError as e:
+            line["local"] = {"error": str(e)}
     if rank == 0 and world == 1 and not a.no_video:
         try:
             line["video"] = video_bench(gcr, torch, primary if primary != "fp32" else "tf32", 3, 3)

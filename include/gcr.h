@@ -9,7 +9,9 @@
  *   caller owns every buffer; the library never allocates, frees or retains memory.
  * - Feature matrices are row-major float32, one sample per row: X[i*d + c].
  *   d must be a multiple of 4 (16-byte rows) and at most 4096; the BF16 tensor-core
- *   path additionally needs d % 8 == 0.
+ *   path additionally needs d % 8 == 0. Device feature matrices must start on a 16-byte
+ *   boundary (every cudaMalloc or PyTorch allocation does; so does any row of one):
+ *   a misaligned one is GCR_E_INVALID.
  * - Every call is asynchronous on the caller's stream (a cudaStream_t passed as
  *   gcr_stream_t; NULL is the legacy default stream) and returns a gcr_status code.
  *   Arguments are validated on the host before anything is launched; on a non-zero
@@ -283,6 +285,37 @@ size_t gcr_serve_workspace_size(int64_t b, int64_t ng, int32_t d, const gcr_para
 int gcr_serve(const void* state, size_t state_bytes, int64_t ng, const float* Xq, int64_t b,
               int32_t d, const gcr_params* p, int32_t* idx_out, float* dist_out, int64_t* stats,
               void* ws, size_t ws_bytes, gcr_stream_t stream);
+
+/* ------------------------------------------------------------------ DSFP (local propagation)
+ * Decentralized and synchronous feature propagation, Algorithm 1 (Sec. III-B; "GCR_Local"
+ * in Sec. IV-F): every image i is updated from its own local graph only. Its node set is
+ * {i} u N_i (N_i its k nearest samples on the input features, i excluded, ties to the
+ * smaller index, found by the same certified search as gcr_build_graph); over every pair
+ * (u, v) of that set A_uv = exp(-||x_u - x_v||^2 / gamma) (A_uu = 1), D_u = sum_v A_uv, and
+ * the (k+1) x d local features run T iterations of X <- normalise(D^{-1/2} A D^{-1/2} X).
+ * Row i of X_out is i's own row after the T-th iteration (T = 0: the normalised input).
+ * The local graph is built once, from the input (Algorithm 1 has no rebuild step), and the
+ * rows are L2-normalised on input and after every iteration, as in the global method.
+ *
+ * gcr_dsfp: X device float32 [n][d], raw (normalised first). Uses p->k (0..64, < pool),
+ * p->gamma, p->precision, p->pool and p->T; p->cross_camera must be 0 (Algorithm 1 is
+ * stated for the plain graph); p->symmetric, alpha and topk_out are not used. X_out:
+ * device float32 [n][d], must not alias X. nbr_out (may be NULL): device int32 [n][k]
+ * receives N_i (-1 where fewer than k samples exist). stats: as gcr_graph.stats.
+ * Errors: GCR_E_INVALID (null X / X_out, X_out == X, cross_camera = 1, T < 0, and every
+ * gcr_build_graph parameter error), GCR_E_UNSUPPORTED (k > 64, d % 4, the precision rules of
+ * gcr_build_graph), GCR_E_WORKSPACE.
+ *
+ * gcr_dsfp_propagate: the local propagation alone (no kNN search) on given neighbour lists.
+ * X: device float32 [n][d], unit rows; nbr: device int32 [n][k], entries in [0, n) or < 0
+ * (absent; skipped), trusted (not re-validated on the device); 0 <= k <= 64; gamma > 0;
+ * T >= 0; X_out: device float32 [n][d], must not alias X. No workspace.
+ * Errors: GCR_E_INVALID, GCR_E_UNSUPPORTED (k > 64, d % 4). */
+size_t gcr_dsfp_workspace_size(int64_t n, int32_t d, const gcr_params* p);
+int gcr_dsfp(const float* X, int64_t n, int32_t d, const gcr_params* p, float* X_out, int32_t* nbr_out,
+             int64_t* stats, void* ws, size_t ws_bytes, gcr_stream_t stream);
+int gcr_dsfp_propagate(const float* X, int64_t n, int32_t d, const int32_t* nbr, int32_t k, float gamma,
+                       int32_t T, float* X_out, gcr_stream_t stream);
 
 /* ------------------------------------------------------------------ stage profiler
  * Process-wide, for measurement only (not thread-safe). While enabled, every entry point

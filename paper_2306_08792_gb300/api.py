@@ -195,6 +195,53 @@ def gcrv_profiles(frames: torch.Tensor, trk_off: torch.Tensor, trk_cam: torch.Te
     return W
 
 
+class Dsfp:
+    """gcr_dsfp (Algorithm 1, the local propagation) with a reusable workspace."""
+
+    def __init__(self, n: int, d: int, p: Params, device="cuda"):
+        self.n, self.d, self.p = n, d, p
+        lib = _lib.load()
+        need = lib.gcr_dsfp_workspace_size(n, d, ctypes.byref(p))
+        if need == 0:
+            raise GcrError(_lib.GCR_E_INVALID, "gcr_dsfp_workspace_size")
+        self.ws = torch.empty(need, dtype=torch.uint8, device=device)
+        self.out = torch.empty(n, d, dtype=torch.float32, device=device)
+        self.nbr = torch.empty(n, max(p.k, 1), dtype=torch.int32, device=device)
+        self.stats = torch.zeros(_lib.GCR_STATS_LEN, dtype=torch.int64, device=device)
+
+    def __call__(self, X: torch.Tensor, stream=None) -> torch.Tensor:
+        """X: raw float32 [n, d] on the device. Returns X_T (the kNN lists are in self.nbr)."""
+        X = _dev_f32(X, "X")
+        if tuple(X.shape) != (self.n, self.d):
+            raise ValueError("X has the wrong shape")
+        _check(_lib.load().gcr_dsfp(_ptr(X), self.n, self.d, ctypes.byref(self.p), _ptr(self.out),
+                                    _ptr(self.nbr) if self.p.k > 0 else None, _ptr(self.stats), _ptr(self.ws),
+                                    self.ws.numel(), _stream(stream)), "gcr_dsfp")
+        return self.out
+
+
+def gcr_dsfp(X: torch.Tensor, p: Params, stream=None):
+    """One-shot Algorithm 1: returns (X_T, N_i lists int32 [n, k])."""
+    n, d = X.shape
+    ds = Dsfp(n, d, p, device=X.device)
+    out = ds(X, stream=stream)
+    return out, ds.nbr[:, :p.k]
+
+
+def gcr_dsfp_propagate(X: torch.Tensor, nbr: torch.Tensor, gamma: float, T: int,
+                       out: Optional[torch.Tensor] = None, stream=None) -> torch.Tensor:
+    """The local propagation of Algorithm 1 on given neighbour lists (X: unit rows)."""
+    X = _dev_f32(X, "X")
+    if not (nbr.is_cuda and nbr.dtype == torch.int32 and nbr.dim() == 2 and nbr.is_contiguous()):
+        raise ValueError("nbr must be a contiguous int32 CUDA matrix")
+    n, d = X.shape
+    k = nbr.shape[1]
+    out = torch.empty_like(X) if out is None else out
+    _check(_lib.load().gcr_dsfp_propagate(_ptr(X), n, d, _ptr(nbr) if k > 0 else None, k, ctypes.c_float(gamma),
+                                          T, _ptr(out), _stream(stream)), "gcr_dsfp_propagate")
+    return out
+
+
 class Pipeline:
     """Whole re-ranking (normalise, T x (graph, propagate), re-rank) with reusable buffers."""
 

@@ -43,7 +43,6 @@ struct StageScope {
 };
 
 constexpr int kBandCap = 512;        // band entries kept per rescanned (row, graph)
-constexpr int kMaxD = 4096;
 
 struct Resolved {
   int kp;
@@ -71,6 +70,10 @@ int default_pool(const gcr_params* p) {
   if (p->precision == GCR_PREC_BF16) kp = std::max(kp, 64);
   return kp;
 }
+
+// Feature matrices are read and written as 16-byte vectors: their base must be 16-byte aligned
+// (rows then are too, d being a multiple of 4).
+bool misaligned(const void* q) { return (reinterpret_cast<uintptr_t>(q) & 15) != 0; }
 
 int check_params(const gcr_params* p, int64_t n, int32_t d, Resolved* r) {
   if (!p || n < 1 || n > (1 << 24)) return GCR_E_INVALID;
@@ -185,8 +188,10 @@ size_t carve_build(Carve& c, int64_t n, int32_t d, const gcr_params* p, const Re
   return c.off;
 }
 
-int build_graph_impl(const float* X, int64_t n64_, int32_t d, const int32_t* cam, const gcr_params* p,
-                     const Resolved& r, gcr_graph* g, const BuildWs& w, cudaStream_t st) {
+// The certified kNN search of Eq. 4 / Eq. 8 (S1-S3): writes g->nbr / nbr_d2 (and the
+// cross-camera lists), g->row_order when given, and the search counters.
+int knn_impl(const float* X, int64_t n64_, int32_t d, const int32_t* cam, const gcr_params* p, const Resolved& r,
+             gcr_graph* g, const BuildWs& w, cudaStream_t st) {
   const int n = (int)n64_;
   const int kinds = r.kinds;
   const bool bf = tensor_mode(p);
@@ -250,6 +255,15 @@ int build_graph_impl(const float* X, int64_t n64_, int32_t d, const int32_t* cam
     }
     GCR_CUDA_TRY(launch_refine_band(ra, st));
   }
+  return GCR_OK;
+}
+
+int build_graph_impl(const float* X, int64_t n64_, int32_t d, const int32_t* cam, const gcr_params* p,
+                     const Resolved& r, gcr_graph* g, const BuildWs& w, cudaStream_t st) {
+  const int n = (int)n64_;
+  const int kinds = r.kinds;
+  const int s = knn_impl(X, n64_, d, cam, p, r, g, w, st);
+  if (s != GCR_OK) return s;
 
   GraphArgs ga;
   std::memset(&ga, 0, sizeof(ga));
@@ -762,6 +776,32 @@ struct HostCopyState {
 std::mutex g_copy_mu;
 HostCopyState g_copy[kMaxDevices];
 
+// Workspace of gcr_dsfp: the normalised input, the kNN lists and the kNN search's own.
+struct DsfpWs {
+  float* Xn;
+  int32_t* nbr;
+  float* d2;
+  BuildWs bw;
+};
+
+size_t carve_dsfp(Carve& c, int64_t n, int32_t d, const gcr_params* p, const Resolved& r, DsfpWs* w) {
+  DsfpWs t;
+  t.Xn = c.take<float>((size_t)n * d);
+  t.nbr = c.take<int32_t>((size_t)n * p->k);
+  t.d2 = c.take<float>((size_t)n * p->k);
+  carve_build(c, n, d, p, r, &t.bw);
+  if (w) *w = t;
+  return c.off;
+}
+
+int check_dsfp(const gcr_params* p, int64_t n, int32_t d, Resolved* r) {
+  const int s = check_params(p, n, d, r);
+  if (s != GCR_OK) return s;
+  if (p->cross_camera || p->T < 0) return GCR_E_INVALID;
+  if (p->k > kDsfpMaxK) return GCR_E_UNSUPPORTED;
+  return GCR_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -842,7 +882,7 @@ int gcr_selftest_wait_timeout(int64_t limit_us, gcr_stream_t stream) {
 }
 
 int gcr_normalize(const float* X_in, float* X_out, int64_t n, int32_t d, gcr_stream_t stream) {
-  if (!X_in || !X_out || n < 1 || d < 4 || d > kMaxD) return GCR_E_INVALID;
+  if (!X_in || !X_out || n < 1 || d < 4 || d > kMaxD || misaligned(X_in) || misaligned(X_out)) return GCR_E_INVALID;
   if (d % 4 != 0) return GCR_E_UNSUPPORTED;
   StageScope sc_(GCR_STAGE_NORMALIZE, (cudaStream_t)stream);
   GCR_CUDA_TRY(launch_normalize(X_in, X_out, n, d, (cudaStream_t)stream));
@@ -866,7 +906,7 @@ int gcr_build_graph(const float* X, int64_t n, int32_t d, const int32_t* cam, co
   Resolved r;
   int s = check_params(p, n, d, &r);
   if (s != GCR_OK) return s;
-  if (!X || (p->cross_camera && !cam)) return GCR_E_INVALID;
+  if (!X || misaligned(X) || (p->cross_camera && !cam)) return GCR_E_INVALID;
   s = check_graph(g, r.kinds, p->k);
   if (s != GCR_OK) return s;
   if (!ws) return GCR_E_WORKSPACE;
@@ -879,6 +919,7 @@ int gcr_build_graph(const float* X, int64_t n, int32_t d, const int32_t* cam, co
 int gcr_propagate(const gcr_graph* g, const float* X_in, float* X_out, int64_t n, int32_t d, gcr_stream_t stream) {
   if (!g || !g->op_rowptr || !g->op_len || !g->op_col || !g->op_val || !X_in || !X_out) return GCR_E_INVALID;
   if (X_in == X_out || n < 1 || n > (1 << 24) || d < 4 || d > kMaxD) return GCR_E_INVALID;
+  if (misaligned(X_in) || misaligned(X_out)) return GCR_E_INVALID;
   if (d % 4 != 0) return GCR_E_UNSUPPORTED;
   StageScope sc_(GCR_STAGE_PROPAGATE, (cudaStream_t)stream);
   GCR_CUDA_TRY(launch_propagate(g->op_rowptr, g->op_len, g->op_col, g->op_val, X_in, X_out, (int)n, d,
@@ -897,7 +938,7 @@ int gcr_rerank(const float* Xq, int64_t nq, const float* Xg, int64_t ng, int32_t
                int32_t* idx_out, float* dist_out, void* ws, size_t ws_bytes, gcr_stream_t stream) {
   int s = check_rerank(nq, ng, d, p);
   if (s != GCR_OK) return s;
-  if (!Xq || !Xg || !idx_out || !dist_out) return GCR_E_INVALID;
+  if (!Xq || !Xg || !idx_out || !dist_out || misaligned(Xq) || misaligned(Xg)) return GCR_E_INVALID;
   if (!ws) return GCR_E_WORKSPACE;
   Carve c(ws, ws_bytes);
   if (rerank_uses_pool(p, ng)) {
@@ -919,7 +960,7 @@ size_t gcrv_profiles_workspace_size(int64_t F, int32_t d, int32_t C, int32_t n_c
 int gcrv_profiles(const float* frames, int64_t F, int32_t d, const int64_t* trk_off, const int32_t* trk_cam,
                   int32_t C, int32_t n_cams, float lambda, float* W_out, void* ws, size_t ws_bytes,
                   gcr_stream_t stream) {
-  if (!frames || !trk_off || !trk_cam || !W_out) return GCR_E_INVALID;
+  if (!frames || !trk_off || !trk_cam || !W_out || misaligned(frames) || misaligned(W_out)) return GCR_E_INVALID;
   if (F < 1 || C < 1 || n_cams < 1 || n_cams > 64 || F > (int64_t)INT32_MAX) return GCR_E_INVALID;
   if (d < 4 || d > kMaxD) return GCR_E_INVALID;
   if (d % 4 != 0) return GCR_E_UNSUPPORTED;
@@ -953,7 +994,7 @@ int gcr_gallery_build(const float* Xg, int64_t ng, int32_t d, const gcr_params* 
   Resolved r;
   int s = check_serve_params(p, ng, d, &r);
   if (s != GCR_OK) return s;
-  if (!Xg || !state) return GCR_E_INVALID;
+  if (!Xg || !state || misaligned(Xg)) return GCR_E_INVALID;
   if (!ws) return GCR_E_WORKSPACE;
   Carve cs(state, state_bytes);
   GalleryView g;
@@ -1000,7 +1041,7 @@ int gcr_serve(const void* state, size_t state_bytes, int64_t ng, const float* Xq
   Resolved r;
   int s = check_serve_params(p, ng, d, &r);
   if (s != GCR_OK) return s;
-  if (!state || !Xq || !idx_out || !dist_out || b < 1 || b > (1 << 20)) return GCR_E_INVALID;
+  if (!state || !Xq || !idx_out || !dist_out || b < 1 || b > (1 << 20) || misaligned(Xq)) return GCR_E_INVALID;
   Carve cs(const_cast<void*>(state), state_bytes);
   GalleryView g;
   if (carve_gallery(cs, ng, d, p, &g) > state_bytes) return GCR_E_WORKSPACE;
@@ -1048,6 +1089,7 @@ int gcr_pipeline(const float* X, int64_t n, int64_t nq, int32_t d, const int32_t
   s = check_rerank(nq, n - nq, d, p);
   if (s != GCR_OK) return s;
   if (!X || !idx_out || !dist_out || (p->cross_camera && !cam) || p->T < 0) return GCR_E_INVALID;
+  if (misaligned(X) || misaligned(X_final)) return GCR_E_INVALID;
   if (!ws) return GCR_E_WORKSPACE;
   Carve c(ws, ws_bytes);
   PipeWs w;
@@ -1123,5 +1165,57 @@ int gcr_pipeline_host(const float* X_host, int64_t n, int64_t nq, int32_t d, con
   return GCR_OK;
 }
 
+// ---------------------------------------------------------------- DSFP (Algorithm 1)
+size_t gcr_dsfp_workspace_size(int64_t n, int32_t d, const gcr_params* p) {
+  Resolved r;
+  if (check_dsfp(p, n, d, &r) != GCR_OK) return 0;
+  Carve c(nullptr, 0);
+  return carve_dsfp(c, n, d, p, r, nullptr) + 256;
+}
+
+int gcr_dsfp(const float* X, int64_t n, int32_t d, const gcr_params* p, float* X_out, int32_t* nbr_out,
+             int64_t* stats, void* ws, size_t ws_bytes, gcr_stream_t stream) {
+  Resolved r;
+  int s = check_dsfp(p, n, d, &r);
+  if (s != GCR_OK) return s;
+  if (!X || !X_out || X == X_out || misaligned(X) || misaligned(X_out)) return GCR_E_INVALID;
+  if (!ws) return GCR_E_WORKSPACE;
+  Carve c(ws, ws_bytes);
+  DsfpWs w;
+  if (carve_dsfp(c, n, d, p, r, &w) > ws_bytes) return GCR_E_WORKSPACE;
+  cudaStream_t st = (cudaStream_t)stream;
+  {
+    StageScope sc_(GCR_STAGE_NORMALIZE, st);
+    GCR_CUDA_TRY(launch_normalize(X, w.Xn, n, d, st));
+  }
+  int32_t* nbr = nbr_out ? nbr_out : w.nbr;
+  if (p->k > 0) {
+    // step 1 of Algorithm 1: the certified kNN search on the normalised input
+    gcr_graph g;
+    std::memset(&g, 0, sizeof(g));
+    g.nbr = nbr;
+    g.nbr_d2 = w.d2;
+    g.stats = stats;
+    s = knn_impl(w.Xn, n, d, nullptr, p, r, &g, w.bw, st);
+    if (s != GCR_OK) return s;
+  }
+  StageScope sc_(GCR_STAGE_PROPAGATE, st);
+  GCR_CUDA_TRY(launch_dsfp(w.Xn, (int)n, d, nbr, p->k, p->gamma, p->T, X_out, st));
+  return GCR_OK;
+}
+
+int gcr_dsfp_propagate(const float* X, int64_t n, int32_t d, const int32_t* nbr, int32_t k, float gamma,
+                       int32_t T, float* X_out, gcr_stream_t stream) {
+  if (!X || !X_out || X == X_out || n < 1 || n > (1 << 24) || d < 4 || d > kMaxD || k < 0 || T < 0)
+    return GCR_E_INVALID;
+  if (!(gamma > 0.f) || !std::isfinite(gamma)) return GCR_E_INVALID;
+  if (k > 0 && !nbr) return GCR_E_INVALID;
+  if (misaligned(X) || misaligned(X_out)) return GCR_E_INVALID;
+  if (k > kDsfpMaxK || d % 4) return GCR_E_UNSUPPORTED;
+  cudaStream_t st = (cudaStream_t)stream;
+  StageScope sc_(GCR_STAGE_PROPAGATE, st);
+  GCR_CUDA_TRY(launch_dsfp(X, (int)n, d, nbr, k, gamma, T, X_out, st));
+  return GCR_OK;
+}
 
 }  // extern "C"

@@ -12,6 +12,8 @@
 namespace gcr {
 
 constexpr int kMaxK = 64;          // largest k supported by the kNN search
+constexpr int kMaxD = 4096;        // largest feature dimension
+constexpr int kDsfpMaxK = 64;      // largest k of the local propagation (Algorithm 1)
 constexpr int kQCap = 32;          // survivors queued per row before a merge
 
 __host__ __device__ inline size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }

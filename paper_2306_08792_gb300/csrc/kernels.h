@@ -180,6 +180,12 @@ cudaError_t launch_query_step(const float* xq, int b, int d, const float* G, con
                               const float* d2, int k, float gamma, int symmetric, float* out, cudaStream_t st);
 cudaError_t launch_layer_degree(const float* dr, const float* dc, int n, int symmetric, float* out, cudaStream_t st);
 
+// ---- dsfp.cu
+// Local propagation of Algorithm 1 for every row of the normalised X (n x d, d % 4 == 0)
+// over its neighbour lists nbr (n x k, entries < 0 absent; k <= kDsfpMaxK); out: n x d.
+cudaError_t launch_dsfp(const float* X, int n, int d, const int32_t* nbr, int k, float gamma, int T, float* out,
+                        cudaStream_t st);
+
 // ---- sort.cu
 cudaError_t launch_rank_rows(const float* D, int nq, int ng, int K, int32_t* idx_out,
                              float* dist_out, cudaStream_t st);

@@ -189,3 +189,47 @@ def test_serving_validation_on_host(lib):
     v = ctypes.c_void_p(16)
     assert lib.gcr_serve(v, 1 << 40, 500000, v, 8, 256, ctypes.byref(p), v, v, None, None, 0, None) == 2
     assert lib.gcr_serve(None, 1 << 40, 500000, v, 8, 256, ctypes.byref(p), v, v, None, v, 1 << 40, None) == 1
+
+
+def test_dsfp_validation_on_host(lib):
+    p = _params(lib, k=20, T=2)
+    assert lib.gcr_dsfp_workspace_size(1000, 256, ctypes.byref(p)) > 1000 * 256 * 4
+    for bad in (dict(cross_camera=1), dict(T=-1), dict(k=65, pool=128), dict(gamma=0.0)):
+        kw = dict(k=20, T=2)
+        kw.update(bad)
+        q = _params(lib, **kw)
+        assert lib.gcr_dsfp_workspace_size(1000, 256, ctypes.byref(q)) == 0, bad
+    v = ctypes.c_void_p(16)
+    w = ctypes.c_void_p(4096)
+    big = 1 << 40
+    # missing or aliased buffers, then the error classes of the parameters
+    assert lib.gcr_dsfp(None, 1000, 256, ctypes.byref(p), w, None, None, v, big, None) == 1
+    assert lib.gcr_dsfp(v, 1000, 256, ctypes.byref(p), v, None, None, w, big, None) == 1
+    assert lib.gcr_dsfp(v, 1000, 256, ctypes.byref(p), w, None, None, None, 0, None) == 2
+    assert lib.gcr_dsfp(v, 1000, 256, ctypes.byref(p), w, None, None, v, 100, None) == 2
+    assert lib.gcr_dsfp(v, 1000, 256, ctypes.byref(_params(lib, k=20, T=2, cross_camera=1)), w, None, None, v,
+                        big, None) == 1
+    assert lib.gcr_dsfp(v, 1000, 256, ctypes.byref(_params(lib, k=65, T=2, pool=128)), w, None, None, v,
+                        big, None) == 5
+    assert lib.gcr_dsfp(v, 1000, 258, ctypes.byref(p), w, None, None, v, big, None) == 5
+    g = ctypes.c_float(0.2)
+    assert lib.gcr_dsfp_propagate(v, 1000, 256, v, 20, ctypes.c_float(0.0), 2, w, None) == 1
+    assert lib.gcr_dsfp_propagate(v, 1000, 256, v, 20, g, -1, w, None) == 1
+    assert lib.gcr_dsfp_propagate(v, 1000, 256, None, 20, g, 2, w, None) == 1
+    assert lib.gcr_dsfp_propagate(v, 1000, 256, v, 20, g, 2, v, None) == 1
+    assert lib.gcr_dsfp_propagate(v, 1000, 256, v, 65, g, 2, w, None) == 5
+    assert lib.gcr_dsfp_propagate(v, 1000, 258, v, 20, g, 2, w, None) == 5
+
+
+def test_misaligned_feature_matrices_rejected_on_host(lib):
+    # feature matrices are moved as 16-byte vectors: a base off the 16-byte grid is refused
+    p = _params(lib, k=10, T=2)
+    a, m = ctypes.c_void_p(4096), ctypes.c_void_p(4100)
+    assert lib.gcr_normalize(m, a, 100, 64, None) == 1
+    assert lib.gcr_normalize(a, m, 100, 64, None) == 1
+    assert lib.gcr_dsfp(m, 100, 64, ctypes.byref(p), a, None, None, a, 1 << 40, None) == 1
+    assert lib.gcr_dsfp(a, 100, 64, ctypes.byref(p), m, None, None, a, 1 << 40, None) == 1
+    assert lib.gcr_dsfp_propagate(m, 100, 64, a, 10, ctypes.c_float(0.2), 2, ctypes.c_void_p(8192), None) == 1
+    q = _params(lib, k=10, T=2, topk_out=5)
+    assert lib.gcr_rerank(m, 10, a, 90, 64, ctypes.byref(q), a, a, a, 1 << 40, None) == 1
+    assert lib.gcr_pipeline(m, 100, 10, 64, None, ctypes.byref(q), None, a, a, None, a, 1 << 40, None) == 1
