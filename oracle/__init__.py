@@ -9,3 +9,4 @@ from .gcr_oracle import *  # noqa: F401,F403
 from .pvg_oracle import *  # noqa: F401,F403
 from .serve_oracle import *  # noqa: F401,F403
 from .dsfp_oracle import *  # noqa: F401,F403
+from .eval_oracle import *  # noqa: F401,F403
