@@ -50,6 +50,7 @@ def _args():
     ap.add_argument("--no-zipf", action="store_true", help="skip the 200,000-row Zipf workload")
     ap.add_argument("--no-video", action="store_true", help="skip the GCRV video workload")
     ap.add_argument("--no-local", action="store_true", help="skip the DSFP (Algorithm 1) comparison")
+    ap.add_argument("--no-quality", action="store_true", help="skip the retrieval-quality measurements")
     ap.add_argument("--serving-requests", type=int, default=800)
     ap.add_argument("--pool", type=int, default=0, help="candidate pool per row (0: library default)")
     return ap.parse_args()
@@ -508,6 +509,61 @@ def local_bench(gcr, torch, w, X, precision, steps, warmup):
             "paper": "Sec. IV-F timing table (24-core CPU, Market-1501): GCR 24 s, GCR_Local 10 s"}
 
 
+def quality_bench(gcr, torch):
+    """Retrieval quality (mAP, Rank-1/5 under the cross-camera protocol: same-identity
+    same-camera gallery items removed) on the ``camera_bias`` workload (Market-1501 shape,
+    look-alike identities, per-camera offsets): the original features, global GCR with the
+    plain graph, GCR with the cross-camera graph (Eq. 9), and DSFP (Algorithm 1), all TF32;
+    then a sweep of k, T, gamma and alpha around the paper's defaults (GCR + cross-camera).
+    Rankings and their evaluation run on the GPU (gcr_rerank / gcr_pipeline / gcr_dsfp,
+    gcr_eval_retrieval)."""
+    import workloads
+    w = workloads.camera_bias()
+    nq = w.n_query
+    X = torch.from_numpy(w.X).cuda()
+    cam = torch.from_numpy(w.cam).cuda()
+    ql = torch.from_numpy(w.label[:nq].astype("int32")).cuda()
+    gl = torch.from_numpy(w.label[nq:].astype("int32")).cuda()
+    qc, gc = cam[:nq].contiguous(), cam[nq:].contiguous()
+
+    def score(idx):
+        ap, first = gcr.gcr_eval_retrieval(idx, ql, gl, qc, gc, protocol=1)
+        s = gcr.retrieval_summary(ap, first, ranks=(1, 5))
+        return {"mAP": round(s["mAP"], 4), "rank1": round(s["rank1"], 4), "rank5": round(s["rank5"], 4)}
+
+    t0 = time.perf_counter()
+    base = gcr.default_params(k=20, T=2, gamma=0.2, alpha=0.7, precision="tf32")
+    Xn = gcr.gcr_normalize(X)
+    out = {"original": score(gcr.gcr_rerank(Xn[:nq], Xn[nq:], base)[0])}
+
+    def run(**kw):
+        p = gcr.default_params(**{**dict(k=20, T=2, gamma=0.2, alpha=0.7, precision="tf32"), **kw})
+        c = cam if p.cross_camera else None
+        return score(gcr.gcr_pipeline(X, nq, p, c)[0])
+
+    out["gcr_global"] = run(cross_camera=0)
+    out["gcr_cross_camera"] = run(cross_camera=1)
+    XL, _ = gcr.gcr_dsfp(X, gcr.default_params(k=20, T=2, gamma=0.2, precision="tf32"))
+    out["dsfp"] = score(gcr.gcr_rerank(XL[:nq], XL[nq:], base)[0])
+    sweep = []
+    for k in (10, 15, 20, 30):
+        for T in (1, 2, 3):
+            sweep.append({"k": k, "T": T, "gamma": 0.2, "alpha": 0.7, **run(cross_camera=1, k=k, T=T)})
+    for g in (0.1, 0.5, 1.0):
+        sweep.append({"k": 20, "T": 2, "gamma": g, "alpha": 0.7, **run(cross_camera=1, gamma=g)})
+    for a in (0.0, 0.3, 0.5, 0.9, 1.0):
+        sweep.append({"k": 20, "T": 2, "gamma": 0.2, "alpha": a, **run(cross_camera=1, alpha=a)})
+    out["sweep_gcr_cross_camera"] = sweep
+    del X, Xn, XL
+    torch.cuda.empty_cache()
+    return {"workload": f"camera_bias: {nq:,} queries + {w.n - nq:,} gallery, d={w.d}, {w.params['n_clusters']} "
+                        f"identities in groups of {w.params['ids_per_group']} look-alikes, 20% distractors, "
+                        f"{w.params['n_cams']} cameras with offsets (cam_bias={w.params['cam_bias']})",
+            "protocol": "cross-camera (same identity and camera removed); mAP = mean precision at each hit",
+            "defaults": "k=20, T=2, gamma=0.2, alpha=0.7, TF32 search, full ranking", **out,
+            "wall_s": time.perf_counter() - t0}
+
+
 def max_over_ranks(value: float, dist, device=None) -> float:
     """Largest value over all ranks (the slowest replica sets the job's time)."""
     if dist is None:
@@ -642,6 +698,11 @@ def run_ours(a):
             line["local"] = local_bench(gcr, torch, w, X, primary if primary != "fp32" else "tf32", 5, 3)
         except gcr.GcrError as e:
             line["local"] = {"error": str(e)}
+    if rank == 0 and world == 1 and not a.no_quality:
+        try:
+            line["quality"] = quality_bench(gcr, torch)
+        except gcr.GcrError as e:
+            line["quality"] = {"error": str(e)}
     if rank == 0 and world == 1 and not a.no_video:
         try:
             line["video"] = video_bench(gcr, torch, primary if primary != "fp32" else "tf32", 3, 3)

@@ -317,6 +317,26 @@ int gcr_dsfp(const float* X, int64_t n, int32_t d, const gcr_params* p, float* X
 int gcr_dsfp_propagate(const float* X, int64_t n, int32_t d, const int32_t* nbr, int32_t k, float gamma,
                        int32_t T, float* X_out, gcr_stream_t stream);
 
+/* ------------------------------------------------------------------ retrieval quality
+ * Average precision and first-hit position of ranked lists, from which the mAP and CMC
+ * (Rank-k) of the paper's result tables follow, for evaluating re-ranking on labelled data
+ * (an evaluation step, not part of the re-ranking). idx: device int32 [nq][K], gallery
+ * indices by rank (entries < 0 are skipped, the others must be < ng; trusted). q_label [nq],
+ * g_label [ng]: device int32, -1 marks a distractor (relevant to no query). q_cam [nq],
+ * g_cam [ng]: device int32, required when protocol = 1, else may be NULL. A gallery item is
+ * relevant to a query with the same label (>= 0); protocol 1 (the cross-camera protocol of
+ * the re-identification benchmarks) first removes from the list every item with the query's
+ * label and camera ("junk"); protocol 0 removes nothing. With the relevant items at 0-based
+ * positions p_1 < ... < p_R of the list without junk and R counted over the whole gallery,
+ * ap_out[q] = (1/R) sum_i i / (p_i + 1) (device double [nq]; items missing from a truncated
+ * list count 0; NaN when R = 0 or the query is a distractor), first_out[q] = p_1 or -1
+ * (device int32 [nq]). mAP = mean AP over the queries with R > 0, Rank-k = the fraction of
+ * them with 0 <= first < k. Deterministic. No workspace.
+ * Errors: GCR_E_INVALID (null arrays, sizes, protocol not 0 or 1, cameras missing). */
+int gcr_eval_retrieval(const int32_t* idx, int64_t nq, int64_t K, const int32_t* q_label,
+                       const int32_t* q_cam, const int32_t* g_label, const int32_t* g_cam, int64_t ng,
+                       int32_t protocol, double* ap_out, int32_t* first_out, gcr_stream_t stream);
+
 /* ------------------------------------------------------------------ stage profiler
  * Process-wide, for measurement only (not thread-safe). While enabled, every entry point
  * records a CUDA event pair on its stream around each stage below. gcr_profile_read()

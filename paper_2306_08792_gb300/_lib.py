@@ -70,6 +70,8 @@ PROTOTYPES = {
                          c_size_t, c_void_p]),
     "gcr_dsfp_propagate": (c_int, [c_void_p, c_int64, c_int32, c_void_p, c_int32, c_float, c_int32, c_void_p,
                                    c_void_p]),
+    "gcr_eval_retrieval": (c_int, [c_void_p, c_int64, c_int64, c_void_p, c_void_p, c_void_p, c_void_p, c_int64,
+                                   c_int32, c_void_p, c_void_p, c_void_p]),
     "gcr_pipeline_host_workspace_size": (c_size_t, [c_int64, c_int64, c_int32, POINTER(Params)]),
     "gcr_pipeline_host": (c_int, [c_void_p, c_int64, c_int64, c_int32, c_void_p, POINTER(Params), c_void_p,
                                   c_void_p, c_void_p, c_void_p, c_size_t, c_void_p]),

@@ -242,6 +242,47 @@ def gcr_dsfp_propagate(X: torch.Tensor, nbr: torch.Tensor, gamma: float, T: int,
     return out
 
 
+def _dev_i32(t: Optional[torch.Tensor], name: str, n: int):
+    if t is None:
+        return None
+    if not (t.is_cuda and t.dtype == torch.int32 and t.is_contiguous() and t.numel() == n):
+        raise ValueError(f"{name} must be a contiguous int32 CUDA vector of {n} entries")
+    return t
+
+
+def gcr_eval_retrieval(idx: torch.Tensor, q_label: torch.Tensor, g_label: torch.Tensor,
+                       q_cam: Optional[torch.Tensor] = None, g_cam: Optional[torch.Tensor] = None,
+                       protocol: int = 0, stream=None):
+    """Per-query average precision (float64, NaN without relevant items) and first-hit
+    position (int32, -1 without a hit) of ranked lists idx [nq, K] (see include/gcr.h)."""
+    if not (idx.is_cuda and idx.dtype == torch.int32 and idx.dim() == 2 and idx.is_contiguous()):
+        raise ValueError("idx must be a contiguous int32 CUDA matrix")
+    nq, K = idx.shape
+    ng = g_label.numel()
+    q_label = _dev_i32(q_label, "q_label", nq)
+    g_label = _dev_i32(g_label, "g_label", ng)
+    q_cam = _dev_i32(q_cam, "q_cam", nq)
+    g_cam = _dev_i32(g_cam, "g_cam", ng)
+    ap = torch.empty(nq, dtype=torch.float64, device=idx.device)
+    first = torch.empty(nq, dtype=torch.int32, device=idx.device)
+    _check(_lib.load().gcr_eval_retrieval(_ptr(idx), nq, K, _ptr(q_label), _ptr(q_cam), _ptr(g_label), _ptr(g_cam),
+                                          ng, protocol, _ptr(ap), _ptr(first), _stream(stream)),
+           "gcr_eval_retrieval")
+    return ap, first
+
+
+def retrieval_summary(ap: torch.Tensor, first: torch.Tensor, ranks=(1, 5, 10)) -> dict:
+    """mAP and Rank-k over the queries that have relevant items (host-side averages)."""
+    ap = ap.cpu()
+    first = first.cpu().long()
+    ok = ~torch.isnan(ap)
+    out = {"mAP": float(ap[ok].mean()) if bool(ok.any()) else float("nan"), "queries": int(ok.sum())}
+    for k in ranks:
+        hit = (first[ok] >= 0) & (first[ok] < k)
+        out[f"rank{k}"] = float(hit.double().mean()) if bool(ok.any()) else float("nan")
+    return out
+
+
 class Pipeline:
     """Whole re-ranking (normalise, T x (graph, propagate), re-rank) with reusable buffers."""
 

@@ -1218,4 +1218,17 @@ int gcr_dsfp_propagate(const float* X, int64_t n, int32_t d, const int32_t* nbr,
   return GCR_OK;
 }
 
+int gcr_eval_retrieval(const int32_t* idx, int64_t nq, int64_t K, const int32_t* q_label, const int32_t* q_cam,
+                       const int32_t* g_label, const int32_t* g_cam, int64_t ng, int32_t protocol, double* ap_out,
+                       int32_t* first_out, gcr_stream_t stream) {
+  if (!idx || !q_label || !g_label || !ap_out || !first_out) return GCR_E_INVALID;
+  if (nq < 1 || nq > INT32_MAX || K < 1 || ng < 1 || ng > INT32_MAX || K > ((int64_t)1 << 40) / nq)
+    return GCR_E_INVALID;
+  if (protocol != 0 && protocol != 1) return GCR_E_INVALID;
+  if (protocol == 1 && (!q_cam || !g_cam)) return GCR_E_INVALID;
+  GCR_CUDA_TRY(launch_eval(idx, (int)nq, (long)K, q_label, q_cam, g_label, g_cam, (int)ng, protocol, ap_out,
+                           first_out, (cudaStream_t)stream));
+  return GCR_OK;
+}
+
 }  // extern "C"

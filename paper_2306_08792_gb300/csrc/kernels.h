@@ -186,6 +186,11 @@ cudaError_t launch_layer_degree(const float* dr, const float* dc, int n, int sym
 cudaError_t launch_dsfp(const float* X, int n, int d, const int32_t* nbr, int k, float gamma, int T, float* out,
                         cudaStream_t st);
 
+// ---- eval.cu
+cudaError_t launch_eval(const int32_t* idx, int nq, long K, const int32_t* q_label, const int32_t* q_cam,
+                        const int32_t* g_label, const int32_t* g_cam, int ng, int protocol, double* ap_out,
+                        int32_t* first_out, cudaStream_t st);
+
 // ---- sort.cu
 cudaError_t launch_rank_rows(const float* D, int nq, int ng, int K, int32_t* idx_out,
                              float* dist_out, cudaStream_t st);

@@ -233,3 +233,14 @@ def test_misaligned_feature_matrices_rejected_on_host(lib):
     q = _params(lib, k=10, T=2, topk_out=5)
     assert lib.gcr_rerank(m, 10, a, 90, 64, ctypes.byref(q), a, a, a, 1 << 40, None) == 1
     assert lib.gcr_pipeline(m, 100, 10, 64, None, ctypes.byref(q), None, a, a, None, a, 1 << 40, None) == 1
+
+
+def test_eval_validation_on_host(lib):
+    v = ctypes.c_void_p(16)
+    assert lib.gcr_eval_retrieval(None, 10, 5, v, v, v, v, 20, 0, v, v, None) == 1
+    assert lib.gcr_eval_retrieval(v, 0, 5, v, v, v, v, 20, 0, v, v, None) == 1
+    assert lib.gcr_eval_retrieval(v, 10, 0, v, v, v, v, 20, 0, v, v, None) == 1
+    assert lib.gcr_eval_retrieval(v, 10, 5, v, v, v, v, 0, 0, v, v, None) == 1
+    assert lib.gcr_eval_retrieval(v, 10, 5, v, v, v, v, 20, 2, v, v, None) == 1
+    assert lib.gcr_eval_retrieval(v, 10, 5, v, None, v, v, 20, 1, v, v, None) == 1
+    assert lib.gcr_eval_retrieval(v, 10, 5, v, v, v, v, 20, 0, None, v, None) == 1
