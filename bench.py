@@ -509,6 +509,34 @@ def local_bench(gcr, torch, w, X, precision, steps, warmup):
             "paper": "Sec. IV-F timing table (24-core CPU, Market-1501): GCR 24 s, GCR_Local 10 s"}
 
 
+def profile_ablation(gcr, torch):
+    """Mean profiles (Eq. 10) against the profile vectors of Eq. 17, each as is and followed by
+    GCR with both graphs (Algorithm 2), on a video set whose cameras add offsets to the frames
+    (mAP / Rank-1, cross-camera protocol on tracklets)."""
+    import workloads
+    v = workloads.video(n_query=500, n_gallery=2500, d=512, n_ids=400, max_len=40, sigma_trk=0.8, cam_bias=0.8)
+    nq = v.n_query
+    frames = torch.from_numpy(v.frames).cuda()
+    off = torch.from_numpy(v.trk_off).cuda()
+    cam = torch.from_numpy(v.trk_cam.astype("int32")).cuda()
+    lab = torch.from_numpy(v.trk_label.astype("int32")).cuda()
+    ql, gl, qc, gc = lab[:nq].contiguous(), lab[nq:].contiguous(), cam[:nq].contiguous(), cam[nq:].contiguous()
+
+    def score(idx):
+        s = gcr.retrieval_summary(*gcr.gcr_eval_retrieval(idx, ql, gl, qc, gc, protocol=1), ranks=(1,))
+        return {"mAP": round(s["mAP"], 4), "rank1": round(s["rank1"], 4)}
+
+    p = gcr.default_params(k=20, T=2, gamma=0.2, alpha=0.7, cross_camera=1, precision="tf32")
+    out = {"workload": f"video: {nq} query + {v.C - nq} gallery tracklets of 2-40 frames ({v.frames.shape[0]:,} "
+                       f"frames, d=512), 400 identities, tracklet spread 0.8, camera offsets 0.8, lambda={v.lam}"}
+    for name, W in (("mean_profile", gcr.gcrv_mean_profiles(frames, off)),
+                    ("pvg", gcr.gcrv_profiles(frames, off, cam, int(v.trk_cam.max()) + 1, v.lam))):
+        Wn = gcr.gcr_normalize(W)
+        out[name] = score(gcr.gcr_rerank(Wn[:nq], Wn[nq:], p)[0])
+        out[name + "_gcr"] = score(gcr.gcr_pipeline(W, nq, p, cam)[0])
+    return out
+
+
 def quality_bench(gcr, torch):
     """Retrieval quality (mAP, Rank-1/5 under the cross-camera protocol: same-identity
     same-camera gallery items removed) on the ``camera_bias`` workload (Market-1501 shape,
@@ -555,6 +583,7 @@ def quality_bench(gcr, torch):
         sweep.append({"k": 20, "T": 2, "gamma": 0.2, "alpha": a, **run(cross_camera=1, alpha=a)})
     out["sweep_gcr_cross_camera"] = sweep
     del X, Xn, XL
+    out["video_profiles"] = profile_ablation(gcr, torch)
     torch.cuda.empty_cache()
     return {"workload": f"camera_bias: {nq:,} queries + {w.n - nq:,} gallery, d={w.d}, {w.params['n_clusters']} "
                         f"identities in groups of {w.params['ids_per_group']} look-alikes, 20% distractors, "

@@ -259,6 +259,14 @@ int gcrv_profiles(const float* frames, int64_t F, int32_t d, const int64_t* trk_
                   const int32_t* trk_cam, int32_t C, int32_t n_cams, float lambda, float* W_out,
                   void* ws, size_t ws_bytes, gcr_stream_t stream);
 
+/* Eq. 10 alone: W_out[c] = the mean of tracklet c's L2-normalised frames (the "mean profile"
+ * that Sec. IV's ablation compares with the Eq. 17 profile vectors). frames / trk_off / C as
+ * for gcrv_profiles; W_out: device float32 [C][d], not normalised. Workspace: F floats.
+ * Errors: GCR_E_INVALID, GCR_E_UNSUPPORTED (d % 4), GCR_E_WORKSPACE. */
+size_t gcrv_mean_profiles_workspace_size(int64_t F, int32_t d, int32_t C);
+int gcrv_mean_profiles(const float* frames, int64_t F, int32_t d, const int64_t* trk_off, int32_t C,
+                       float* W_out, void* ws, size_t ws_bytes, gcr_stream_t stream);
+
 /* ------------------------------------------------------------------ S9: serving
  * Re-ranking against a resident gallery. Sec. IV-F2 notes that with the gallery's graphs
  * computed and stored in advance the cost per query falls to O(N log N); this is that form:

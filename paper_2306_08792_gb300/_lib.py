@@ -55,6 +55,9 @@ PROTOTYPES = {
     "gcrv_profiles_workspace_size": (c_size_t, [c_int64, c_int32, c_int32, c_int32]),
     "gcrv_profiles": (c_int, [c_void_p, c_int64, c_int32, c_void_p, c_void_p, c_int32, c_int32, c_float, c_void_p,
                               c_void_p, c_size_t, c_void_p]),
+    "gcrv_mean_profiles_workspace_size": (c_size_t, [c_int64, c_int32, c_int32]),
+    "gcrv_mean_profiles": (c_int, [c_void_p, c_int64, c_int32, c_void_p, c_int32, c_void_p, c_void_p, c_size_t,
+                                   c_void_p]),
     "gcr_gallery_bytes": (c_size_t, [c_int64, c_int32, POINTER(Params)]),
     "gcr_gallery_build_workspace_size": (c_size_t, [c_int64, c_int32, POINTER(Params)]),
     "gcr_gallery_build": (c_int, [c_void_p, c_int64, c_int32, POINTER(Params), c_void_p, c_size_t, c_void_p,

@@ -195,6 +195,24 @@ def gcrv_profiles(frames: torch.Tensor, trk_off: torch.Tensor, trk_cam: torch.Te
     return W
 
 
+def gcrv_mean_profiles(frames: torch.Tensor, trk_off: torch.Tensor, stream=None) -> torch.Tensor:
+    """Eq. 10 mean profiles (C x d, not normalised) of ragged tracklets of raw frames."""
+    frames = _dev_f32(frames, "frames")
+    if not (trk_off.is_cuda and trk_off.dtype == torch.int64 and trk_off.is_contiguous()):
+        raise ValueError("trk_off must be a contiguous int64 CUDA vector")
+    F, d = frames.shape
+    C = trk_off.numel() - 1
+    lib = _lib.load()
+    need = lib.gcrv_mean_profiles_workspace_size(F, d, C)
+    if need == 0:
+        raise GcrError(_lib.GCR_E_INVALID, "gcrv_mean_profiles_workspace_size")
+    ws = torch.empty(need, dtype=torch.uint8, device=frames.device)
+    W = torch.empty(C, d, dtype=torch.float32, device=frames.device)
+    _check(lib.gcrv_mean_profiles(_ptr(frames), F, d, _ptr(trk_off), C, _ptr(W), _ptr(ws), need, _stream(stream)),
+           "gcrv_mean_profiles")
+    return W
+
+
 class Dsfp:
     """gcr_dsfp (Algorithm 1, the local propagation) with a reusable workspace."""
 

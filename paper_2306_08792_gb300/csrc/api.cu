@@ -974,6 +974,24 @@ int gcrv_profiles(const float* frames, int64_t F, int32_t d, const int64_t* trk_
   return GCR_OK;
 }
 
+size_t gcrv_mean_profiles_workspace_size(int64_t F, int32_t d, int32_t C) {
+  if (F < 1 || C < 1 || F > (int64_t)INT32_MAX || d < 4 || d > kMaxD || d % 4) return 0;
+  return sizeof(float) * (size_t)F + 256;
+}
+
+int gcrv_mean_profiles(const float* frames, int64_t F, int32_t d, const int64_t* trk_off, int32_t C, float* W_out,
+                       void* ws, size_t ws_bytes, gcr_stream_t stream) {
+  if (!frames || !trk_off || !W_out || misaligned(frames) || misaligned(W_out)) return GCR_E_INVALID;
+  if (F < 1 || C < 1 || F > (int64_t)INT32_MAX || d < 4 || d > kMaxD) return GCR_E_INVALID;
+  if (d % 4 != 0) return GCR_E_UNSUPPORTED;
+  if (!ws) return GCR_E_WORKSPACE;
+  Carve c(ws, ws_bytes);
+  float* inv = c.take<float>((size_t)F);
+  if (c.off > ws_bytes) return GCR_E_WORKSPACE;
+  StageScope sc_(GCR_STAGE_GCRV, (cudaStream_t)stream);
+  GCR_CUDA_TRY(launch_gcrv_means(frames, F, d, trk_off, C, inv, W_out, (cudaStream_t)stream));
+  return GCR_OK;
+}
 
 size_t gcr_gallery_bytes(int64_t ng, int32_t d, const gcr_params* p) {
   Resolved r;

@@ -65,10 +65,9 @@ __global__ void __launch_bounds__(1024) layout_kernel(const int64_t* __restrict_
   __shared__ int cnt[kMaxCams];
   __shared__ long long nfr[kMaxCams];
   __shared__ int run[kMaxCams];
-  __shared__ long long frun[kMaxCams];
   __shared__ int wsum[32];
   const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
-  if (tid < kMaxCams) { cnt[tid] = 0; nfr[tid] = 0; run[tid] = 0; frun[tid] = 0; }
+  if (tid < kMaxCams) { cnt[tid] = 0; nfr[tid] = 0; run[tid] = 0; }
   __syncthreads();
   for (int c = tid; c < C; c += blockDim.x) {
     const int s = cam[c];
@@ -227,7 +226,7 @@ __global__ void gram_mirror_kernel(float* __restrict__ G, int d) {
 __global__ void means_kernel(const float* __restrict__ F, int d, const int64_t* __restrict__ off,
                              const float* __restrict__ inv, const int* __restrict__ perm, float* __restrict__ mu) {
   const int row = blockIdx.x;
-  const int c = perm[row];
+  const int c = perm ? perm[row] : row;  // no permutation: row r is tracklet r
   float* out = mu + (size_t)row * d;
   for (int a = threadIdx.x * 4; a < d; a += blockDim.x * 4) {
     float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
@@ -450,6 +449,13 @@ cudaError_t launch_gcrv(const float* frames, int64_t F, int d, const int64_t* of
     else cg_update_kernel<32><<<(rows + 7) / 8, 256, 0, st>>>(w.X, w.R, w.P, w.Q, w.rr, w.perm, rows, d);
   }
   gcrv_out_kernel<<<C, 256, 0, st>>>(w.X, w.mu, d, C, cam, L, W);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_gcrv_means(const float* frames, int64_t F, int d, const int64_t* off, int C, float* inv, float* W,
+                              cudaStream_t st) {
+  frame_inv_norm_kernel<<<(unsigned)((F + 7) / 8), 256, 0, st>>>(frames, F, d, inv);
+  means_kernel<<<C, 256, 0, st>>>(frames, d, off, inv, nullptr, W);
   return cudaGetLastError();
 }
 

@@ -170,6 +170,9 @@ struct GcrvWs {
   double* rr;
 };
 int gcrv_iterations(float lambda);
+// Eq. 10 alone: W[c] = mean of tracklet c's L2-normalised frames (inv: F floats of scratch).
+cudaError_t launch_gcrv_means(const float* frames, int64_t F, int d, const int64_t* off, int C, float* inv, float* W,
+                              cudaStream_t st);
 cudaError_t launch_gcrv(const float* frames, int64_t F, int d, const int64_t* off, const int32_t* cam, int C,
                         int ncam, float lambda, float* W, const GcrvWs& w, cudaStream_t st);
 

@@ -244,3 +244,14 @@ def test_eval_validation_on_host(lib):
     assert lib.gcr_eval_retrieval(v, 10, 5, v, v, v, v, 20, 2, v, v, None) == 1
     assert lib.gcr_eval_retrieval(v, 10, 5, v, None, v, v, 20, 1, v, v, None) == 1
     assert lib.gcr_eval_retrieval(v, 10, 5, v, v, v, v, 20, 0, None, v, None) == 1
+
+
+def test_mean_profiles_validation_on_host(lib):
+    assert lib.gcrv_mean_profiles_workspace_size(1000, 128, 50) >= 4000
+    assert lib.gcrv_mean_profiles_workspace_size(1000, 130, 50) == 0
+    assert lib.gcrv_mean_profiles_workspace_size(0, 128, 50) == 0
+    p = ctypes.c_void_p(16)
+    assert lib.gcrv_mean_profiles(p, 1000, 130, p, 50, p, p, 1 << 30, None) == 5
+    assert lib.gcrv_mean_profiles(p, 1000, 128, p, 50, p, p, 100, None) == 2
+    assert lib.gcrv_mean_profiles(None, 1000, 128, p, 50, p, p, 1 << 30, None) == 1
+    assert lib.gcrv_mean_profiles(p, 1000, 128, p, 0, p, p, 1 << 30, None) == 1

@@ -54,6 +54,15 @@ def test_profiles_match_oracle(gcr, seed, d, lam):
     np.testing.assert_allclose(Wg[7], oracle.mean_profiles(oracle.l2_normalize(v.frames), v.trk_off)[7], atol=1e-6)
 
 
+@pytest.mark.parametrize("seed,d", [(3, 128), (4, 260)])
+def test_mean_profiles_match_oracle(gcr, seed, d):
+    # Eq. 10 on the normalised frames (the ablation baseline of the profile vectors)
+    v = _small(seed=seed, d=d)
+    W = gcr.gcrv_mean_profiles(_dev(v.frames), _dev(v.trk_off, torch.int64)).double().cpu().numpy()
+    Wo = oracle.mean_profiles(oracle.l2_normalize(v.frames), v.trk_off)
+    np.testing.assert_allclose(W, Wo, atol=1e-6, rtol=0)
+
+
 def test_gcrv_algorithm2_staged(gcr):
     """Algorithm 2: GPU profiles, then GPU GCR with both graphs; the oracle's GCR is run on the
     GPU's profiles (staged) and X_T must agree."""

@@ -183,12 +183,13 @@ def zipf(seed: int = 0, n_query: int = 1000, n_gallery: int = 200000, d: int = 5
 def video(seed: int = 0, n_query: int = 1980, n_gallery: int = 11310, d: int = 2048,
           n_ids: int = 1261, min_len: int = 2, max_len: int = 100, sigma_trk: float = 0.3,
           sigma_frame: float = 0.2, n_cams: int = 6, k: int = 20, T: int = 2,
-          lam: float = 10.0) -> VideoWorkload:
+          lam: float = 10.0, cam_bias: float = 0.0) -> VideoWorkload:
     """Video workload with the MARS shape: ragged tracklets of per-frame features.
 
     Tracklet centre = identity centroid + sigma_trk*eps; each frame = centre +
     sigma_frame*eps. Lengths are uniform in [min_len, max_len]; each tracklet has one
-    camera, uniform in [0, n_cams).
+    camera, uniform in [0, n_cams). With cam_bias > 0 every frame also gets its camera's
+    offset cam_bias*b_cam (drawn after everything else, so the other draws do not change).
     """
     rng = np.random.default_rng(seed)
     C = n_query + n_gallery
@@ -208,6 +209,12 @@ def video(seed: int = 0, n_query: int = 1980, n_gallery: int = 11310, d: int = 2
         owner = np.repeat(np.arange(c0, c1), lens[c0:c1])
         frames[f0:f1] = centre[owner]
         frames[f0:f1] += np.float32(sigma_frame) * rng.standard_normal((f1 - f0, d), dtype=np.float32)
+    if cam_bias > 0:
+        bias = rng.standard_normal((n_cams, d), dtype=np.float32)
+        for c0 in range(0, C, blk):
+            c1 = min(C, c0 + blk)
+            f0, f1 = int(off[c0]), int(off[c1])
+            frames[f0:f1] += np.float32(cam_bias) * bias[np.repeat(cam[c0:c1], lens[c0:c1])]
     return VideoWorkload("video", frames, off, cam, ident, n_query, k=k, T=T, lam=lam)
 
 
