@@ -198,11 +198,21 @@ rank_rows_radix_kernel(const float* __restrict__ D, int ng, int K, int32_t* __re
     const int shift = pass * W;
     for (int v = t; v < NW * kHistStride; v += NT) hist[v] = 0;
     __syncthreads();
-    // per-warp stable ranking, slot by slot (slot order = key order inside the warp)
+    // per-warp stable ranking, slot by slot (slot order = key order inside the warp). The lanes
+    // holding the same digit come from one ballot per digit bit (W = 8 or 9 ballots on the ALU
+    // pipe): __match_any_sync gives the same mask but its pipe bounded the whole sort
 #pragma unroll
     for (int i = 0; i < IPT; ++i) {
       const uint32_t dg = (key[i] >> shift) & mask;
-      const unsigned peers = __match_any_sync(GCR_FULL, dg);
+      unsigned peers = GCR_FULL;
+#pragma unroll
+      for (int b = 0; b < 9; ++b) {
+        if (b < W) {  // block-uniform
+          const bool bit = (dg >> b) & 1u;
+          const unsigned m = __ballot_sync(GCR_FULL, bit);
+          peers &= bit ? m : ~m;
+        }
+      }
       const uint32_t base = hw[dg];
       __syncwarp();
       if ((peers & lt) == 0) hw[dg] = base + (uint32_t)__popc(peers);  // the lowest peer updates
