@@ -155,9 +155,9 @@ def oracle_sample_step(w, rows_knn=96, rows_q=96, rows_prop=2000, seed=0):
     return est, dict(t_knn=t_knn, t_prop=t_prop, t_rerank=t_rr)
 
 
-# sample of the CPU baseline printed beside our arm (about 10 s of oracle work on 16 cores),
+# sample of the CPU baseline printed beside our arm (about 10-12 s of oracle work on 16 cores),
 # and the smaller per-step sample of the reference arm (a 20-step run stays within a minute)
-CPU_SAMPLE = dict(rows_knn=3072, rows_q=1536, rows_prop=4000)
+CPU_SAMPLE = dict(rows_knn=6144, rows_q=3072, rows_prop=6000)
 REF_SAMPLE = dict(rows_knn=384, rows_q=192, rows_prop=2000)
 
 

@@ -112,6 +112,22 @@ __device__ __forceinline__ void warp_merge32_desc(float& v, int& vi, int lane) {
   }
 }
 
+// The lanes of the warp whose dg equals this lane's (dg < 2^bits, bits <= 9, warp-uniform):
+// one ballot per bit, ANDed. The same mask as __match_any_sync(GCR_FULL, dg), but on the ALU
+// pipe (the pipe of __match_any_sync bounded the radix sorts that rank keys this way).
+__device__ __forceinline__ unsigned warp_peers(uint32_t dg, int bits) {
+  unsigned peers = GCR_FULL;
+#pragma unroll
+  for (int b = 0; b < 9; ++b) {
+    if (b < bits) {
+      const bool bit = (dg >> b) & 1u;
+      const unsigned m = __ballot_sync(GCR_FULL, bit);
+      peers &= bit ? m : ~m;
+    }
+  }
+  return peers;
+}
+
 // float -> uint32 whose unsigned order equals the float order (ascending).
 __device__ __forceinline__ uint32_t float_to_ordered(float f) {
   uint32_t u = __float_as_uint(f);

@@ -191,8 +191,8 @@ __global__ void long_list_kernel(int n, const int* __restrict__ tptr, int* __res
 // sort of the segment by source row (8-bit digits, nbits = bits of the largest row index),
 // chunk by chunk through global memory in segment order, so the work is linear in the
 // segment's length (an in-degree hub can hold tens of thousands of entries). Within a chunk
-// each warp ranks its keys slot by slot with __match_any_sync; a running per-digit offset
-// carries the order from chunk to chunk. The weights follow their keys. Then D_c(j) = 1 + sum
+// each warp ranks its keys slot by slot (lanes with equal digits found by ballots); a running
+// per-digit offset carries the order from chunk to chunk. The weights follow their keys. Then D_c(j) = 1 + sum
 // of the weights, reduced in a fixed order.
 template <int IPT>
 __global__ void __launch_bounds__(256) tsort_long_kernel(const int* __restrict__ tptr, int* src_tmp, float* w_tmp,
@@ -242,7 +242,7 @@ __global__ void __launch_bounds__(256) tsort_long_kernel(const int* __restrict__
           const int e = c0 + w * 32 * IPT + i * 32 + lane;
           key[i] = e < L ? (uint32_t)ka[e] : 0u;
           dg[i] = e < L ? ((key[i] >> shift) & 255u) : 256u;
-          const unsigned peers = __match_any_sync(GCR_FULL, dg[i]);
+          const unsigned peers = warp_peers(dg[i], 9);  // digits 0..256 (256: past the end)
           const uint32_t base = wcnt[w][dg[i]];
           __syncwarp();
           if ((peers & lt) == 0) wcnt[w][dg[i]] = base + (uint32_t)__popc(peers);  // the lowest peer updates

@@ -9,7 +9,7 @@
 //    usual case for one query's distances). Keys start in gallery-index order and every pass is
 //    stable, so equal distances stay in index order. Each thread keeps 16 keys in registers in
 //    a warp-striped layout (key e = (warp*16 + slot)*32 + lane); per pass a warp ranks its keys
-//    slot by slot with __match_any_sync (peers with the same digit, ranked by lane), per-warp
+//    slot by slot (peers with the same digit found by ballots, ranked by lane), per-warp
 //    digit counts go to shared memory, one block-wide scan in (digit, warp) order gives every
 //    key its destination, and keys and gallery indices are scattered to shared memory (the
 //    indices stay there, double-buffered; the keys are reloaded into registers).
@@ -198,21 +198,12 @@ rank_rows_radix_kernel(const float* __restrict__ D, int ng, int K, int32_t* __re
     const int shift = pass * W;
     for (int v = t; v < NW * kHistStride; v += NT) hist[v] = 0;
     __syncthreads();
-    // per-warp stable ranking, slot by slot (slot order = key order inside the warp). The lanes
-    // holding the same digit come from one ballot per digit bit (W = 8 or 9 ballots on the ALU
-    // pipe): __match_any_sync gives the same mask but its pipe bounded the whole sort
+    // per-warp stable ranking, slot by slot (slot order = key order inside the warp); the lanes
+    // holding the same digit from one ballot per digit bit
 #pragma unroll
     for (int i = 0; i < IPT; ++i) {
       const uint32_t dg = (key[i] >> shift) & mask;
-      unsigned peers = GCR_FULL;
-#pragma unroll
-      for (int b = 0; b < 9; ++b) {
-        if (b < W) {  // block-uniform
-          const bool bit = (dg >> b) & 1u;
-          const unsigned m = __ballot_sync(GCR_FULL, bit);
-          peers &= bit ? m : ~m;
-        }
-      }
+      const unsigned peers = warp_peers(dg, W);
       const uint32_t base = hw[dg];
       __syncwarp();
       if ((peers & lt) == 0) hw[dg] = base + (uint32_t)__popc(peers);  // the lowest peer updates
