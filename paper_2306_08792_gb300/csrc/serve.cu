@@ -17,52 +17,73 @@
 namespace gcr {
 namespace {
 
+// Merges the sorted list held by a warp (b, bi: KP entries, entry p*32 + lane) with the sorted
+// KP-entry list at (lv, li) (shared or global memory), keeping the KP best. Chunks of a sorted
+// list are sorted, so the merge stops at the first chunk whose best cannot enter.
+template <int KP>
+__device__ __forceinline__ void merge_list(float (&b)[KP / 32], int (&bi)[KP / 32], const float* lv, const int* li,
+                                           int lane) {
+  constexpr int P = KP / 32;
+#pragma unroll
+  for (int c = 0; c < P; ++c) {
+    float a = lv[c * 32 + lane];
+    int ai = li[c * 32 + lane];
+    const float worst = __shfl_sync(GCR_FULL, b[P - 1], 31);
+    const int worst_i = __shfl_sync(GCR_FULL, bi[P - 1], 31);
+    const float best = __shfl_sync(GCR_FULL, a, 0);
+    const int best_i = __shfl_sync(GCR_FULL, ai, 0);
+    if (!better(best, best_i, worst, worst_i)) break;
+    const float ar = __shfl_sync(GCR_FULL, a, 31 - lane);
+    const int ari = __shfl_sync(GCR_FULL, ai, 31 - lane);
+    if (better(ar, ari, b[P - 1], bi[P - 1])) { b[P - 1] = ar; bi[P - 1] = ari; }
+#pragma unroll
+    for (int stride = KP / 2; stride >= 32; stride >>= 1) {
+#pragma unroll
+      for (int p = 0; p < P; ++p) {
+        const int q2 = p ^ (stride >> 5);
+        if (q2 > p && better(b[q2], bi[q2], b[p], bi[p])) {
+          float tv = b[p]; b[p] = b[q2]; b[q2] = tv;
+          int ti = bi[p]; bi[p] = bi[q2]; bi[q2] = ti;
+        }
+      }
+    }
+#pragma unroll
+    for (int p = 0; p < P; ++p) warp_merge32_desc(b[p], bi[p], lane);
+  }
+}
+
 // Merge S sorted pools per (kind, row) into one: pools [S][kinds][na][KP] -> [kinds][na][KP].
+// One block of 8 warps per (kind, row): warp w merges splits w, w + 8, ..., then warp 0 merges
+// the 8 partial lists (the strict order makes the result independent of the merge order).
 template <int KP>
 __global__ void __launch_bounds__(256) merge_splits_kernel(const float* __restrict__ pv, const int* __restrict__ pi,
                                                            int S, int kinds, int na, float* __restrict__ ov,
                                                            int* __restrict__ oi) {
   constexpr int P = KP / 32;
-  const int lane = threadIdx.x & 31;
-  const long w = (long)blockIdx.x * 8 + (threadIdx.x >> 5);
-  if (w >= (long)kinds * na) return;
+  __shared__ float sv[8][KP];
+  __shared__ int si[8][KP];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const long w = blockIdx.x;  // (kind, row)
   float b[P];
   int bi[P];
 #pragma unroll
   for (int p = 0; p < P; ++p) {
-    b[p] = pv[w * KP + p * 32 + lane];
-    bi[p] = pi[w * KP + p * 32 + lane];
+    const bool has = warp < S;
+    b[p] = has ? pv[((size_t)warp * kinds * na + w) * KP + p * 32 + lane] : -CUDART_INF_F;
+    bi[p] = has ? pi[((size_t)warp * kinds * na + w) * KP + p * 32 + lane] : -1;
   }
-  for (int s = 1; s < S; ++s) {
+  for (int s = warp + 8; s < S; s += 8) {
     const size_t base = ((size_t)s * kinds * na + w) * KP;
-#pragma unroll
-    for (int c = 0; c < P; ++c) {
-      float a = pv[base + c * 32 + lane];
-      int ai = pi[base + c * 32 + lane];
-      // chunks of a sorted list are sorted; stop once its best cannot enter
-      const float worst = __shfl_sync(GCR_FULL, b[P - 1], 31);
-      const int worst_i = __shfl_sync(GCR_FULL, bi[P - 1], 31);
-      const float best = __shfl_sync(GCR_FULL, a, 0);
-      const int best_i = __shfl_sync(GCR_FULL, ai, 0);
-      if (!better(best, best_i, worst, worst_i)) break;
-      const float ar = __shfl_sync(GCR_FULL, a, 31 - lane);
-      const int ari = __shfl_sync(GCR_FULL, ai, 31 - lane);
-      if (better(ar, ari, b[P - 1], bi[P - 1])) { b[P - 1] = ar; bi[P - 1] = ari; }
-#pragma unroll
-      for (int stride = KP / 2; stride >= 32; stride >>= 1) {
-#pragma unroll
-        for (int p = 0; p < P; ++p) {
-          const int q2 = p ^ (stride >> 5);
-          if (q2 > p && better(b[q2], bi[q2], b[p], bi[p])) {
-            float tv = b[p]; b[p] = b[q2]; b[q2] = tv;
-            int ti = bi[p]; bi[p] = bi[q2]; bi[q2] = ti;
-          }
-        }
-      }
-#pragma unroll
-      for (int p = 0; p < P; ++p) warp_merge32_desc(b[p], bi[p], lane);
-    }
+    merge_list<KP>(b, bi, pv + base, pi + base, lane);
   }
+#pragma unroll
+  for (int p = 0; p < P; ++p) {
+    sv[warp][p * 32 + lane] = b[p];
+    si[warp][p * 32 + lane] = bi[p];
+  }
+  __syncthreads();
+  if (warp != 0) return;
+  for (int v = 1; v < 8 && v < S; ++v) merge_list<KP>(b, bi, sv[v], si[v], lane);
 #pragma unroll
   for (int p = 0; p < P; ++p) {
     ov[w * KP + p * 32 + lane] = b[p];
@@ -139,8 +160,7 @@ __global__ void layer_degree_kernel(const float* __restrict__ dr, const float* _
 
 cudaError_t launch_merge_splits(const float* pv, const int* pi, int S, int kinds, int na, int kp, float* ov, int* oi,
                                 cudaStream_t st) {
-  const long warps = (long)kinds * na;
-  dim3 grid((unsigned)((warps + 7) / 8));
+  dim3 grid((unsigned)((long)kinds * na));  // one block per (kind, row)
   if (kp == 32) merge_splits_kernel<32><<<grid, 256, 0, st>>>(pv, pi, S, kinds, na, ov, oi);
   else if (kp == 64) merge_splits_kernel<64><<<grid, 256, 0, st>>>(pv, pi, S, kinds, na, ov, oi);
   else if (kp == 128) merge_splits_kernel<128><<<grid, 256, 0, st>>>(pv, pi, S, kinds, na, ov, oi);
