@@ -272,7 +272,8 @@ int gcrv_mean_profiles(const float* frames, int64_t F, int32_t d, const int64_t*
  * computed and stored in advance the cost per query falls to O(N log N); this is that form:
  *  - gcr_gallery_build runs offline GCR (Eq. 3) on the gallery alone and stores, in the
  *    caller's state buffer (gcr_gallery_bytes), the layers G_0..G_T, the degrees of each
- *    layer's graph (D = (D_r + D_c)/2 of Eq. 7, or D_c of Eq. 6) and per-row statistics.
+ *    layer's graph (D = (D_r + D_c)/2 of Eq. 7, or D_c of Eq. 6), per-row statistics and the
+ *    kNN lists of the last layer's graph.
  *  - gcr_serve takes a batch of b raw queries (device float32 [b][d]) and, for t = 1..T,
  *    finds each query's certified k nearest rows of G_{t-1}, forms the query's row of the
  *    operator with the gallery frozen and no query-query edges
@@ -281,6 +282,12 @@ int gcrv_mean_profiles(const float* frames, int64_t F, int32_t d, const int64_t*
  *    (w_qj of Eq. 4) and normalises it; then it returns the certified top K = topk_out
  *    (1..127) of the gallery on G_T: idx_out int32 [b][K] by ascending squared distance
  *    (ties to the smaller index) and dist_out float [b][K] (FP32 re-scored distances).
+ * In the tensor-core modes every search after the first gives its column-split pools an
+ * admission floor, from the FP32 scores of the previous search's candidates (and, for the
+ * final search, of their gallery neighbours): provably below the approximate scores of at
+ * least k of the query's gallery rows, so the splits skip most of the pool merging and the
+ * certification (which takes the floor as the bound on every score it left out) is unchanged;
+ * the results are the same certified neighbours as without floors.
  * Every step is per query, so a query's result does not depend on its batch-mates. The
  * state is read-only during gcr_serve: concurrent calls with distinct workspaces may share
  * it. No host synchronisation: a call can be captured in a CUDA graph.

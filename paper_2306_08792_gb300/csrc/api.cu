@@ -464,6 +464,8 @@ struct GalleryView {
   float* enrm;     // (T+1) x ng
   float* anrm;     // (T+1) x ng
   RowScalars* sc;  // T+1
+  int32_t* nbr;    // ng x k: the kNN lists of the last layer's graph (T >= 1, k >= 1); candidates
+                   // for the seeds of the final search's split pools
 };
 
 int check_serve_params(const gcr_params* p, int64_t ng, int32_t d, Resolved* r) {
@@ -488,6 +490,7 @@ size_t carve_gallery(Carve& c, int64_t ng, int32_t d, const gcr_params* p, Galle
   t.enrm = bf ? c.take<float>(L * n) : nullptr;
   t.anrm = bf ? c.take<float>(L * n) : nullptr;
   t.sc = c.take<RowScalars>(L);
+  t.nbr = c.take<int32_t>(n * std::max(p->k, 1));
   if (v) *v = t;
   return c.off;
 }
@@ -543,6 +546,7 @@ struct ServeWs {
   int32_t* nbr;
   float* d2;
   unsigned long long* stats;
+  float* seed;         // per query: the admission floor of this search's split pools
 };
 
 constexpr int kServeMaxSplits = 152;
@@ -589,6 +593,7 @@ size_t carve_serve(Carve& c, int64_t b, int32_t d, const gcr_params* p, const Re
   t.nbr = c.take<int32_t>(nb * std::max(p->k, 1));
   t.d2 = c.take<float>(nb * std::max(p->k, 1));
   t.stats = c.take<unsigned long long>(GCR_STATS_LEN);
+  t.seed = c.take<float>(nb);
   if (w) *w = t;
   return c.off;
 }
@@ -607,9 +612,20 @@ GallerySide gallery_layer(const GalleryView& g, int layer, int ng, int d, size_t
                      g.n64 + (size_t)layer * ng, g.sc + layer};
 }
 
+// Where the seeds of a search's split pools come from: the previous search's merged pool
+// (prev_kp per query, still in the workspace) and optionally the gallery lists hop (hop_k per row).
+// Both searches run on the same query rows (at different layers).
+struct SeedSource {
+  int prev_kp = 0;          // 0: no seed
+  const int32_t* hop = nullptr;
+  int hop_k = 0;
+  int sample = 0;           // evenly spaced gallery rows added to the candidates
+};
+
 // Certified k nearest gallery rows for the b query rows xq: pool, merge, refine, band.
 int serve_knn(const float* xq, int b, int d, const gcr_params* p, int k, int kp, const GallerySide& gs, int ng,
-              const ServeWs& w, unsigned long long* stats, int32_t* nbr, float* d2, cudaStream_t st) {
+              const ServeWs& w, unsigned long long* stats, int32_t* nbr, float* d2, cudaStream_t st,
+              const SeedSource& seed_src = SeedSource()) {
   const bool bf = tensor_mode(p);
   const Elt elt = elt_of(p);
   const float* G = gs.G;
@@ -622,13 +638,26 @@ int serve_knn(const float* xq, int b, int d, const gcr_params* p, int k, int kp,
   GCR_CUDA_TRY(cudaMemsetAsync(w.unc_count, 0, sizeof(int) * 4, st));
   GCR_CUDA_TRY(cudaMemsetAsync(w.band_cnt, 0, sizeof(int) * b, st));
   int used_splits;
+  // the split pools' admission floors (tensor-core modes), from the previous search's merged
+  // pool and, when given, its rows' gallery lists
+  const bool seeded = bf && seed_src.prev_kp > 0 &&
+                      (long)seed_src.prev_kp * (1 + seed_src.hop_k) + seed_src.sample <= kSeedCandidates;
+  if (seeded) {
+    SeedArgs sa;
+    sa.xq = xq; sa.G = G; sa.b = b; sa.ng = ng; sa.d = d; sa.precision = p->precision;
+    sa.n64q = w.n64; sa.enrm = w.enrm; sa.anrm = w.anrm; sa.gsc = gs.sc;
+    sa.pool_i = w.pool_i; sa.prev_kp = seed_src.prev_kp; sa.hop = seed_src.hop; sa.hop_k = seed_src.hop ? seed_src.hop_k : 0;
+    sa.sample = seed_src.sample; sa.k = k; sa.kp = kp; sa.seed = w.seed;
+    StageScope sc_(GCR_STAGE_PREP, st);
+    GCR_CUDA_TRY(launch_serve_seed(sa, st));
+  }
   {
     StageScope sc_(GCR_STAGE_SIM_GEMM, st, 2);
     if (bf) {
       const int ntiles = (ng + 255) / 256;
       used_splits = split_count(splits, ntiles);
       GCR_CUDA_TRY(launch_umma_pool(w.qr, b, gs.Gr, ng, d, elt, nullptr, false, 0, kp, used_splits, w.part_v,
-                                    w.part_i, st));
+                                    w.part_i, st, seeded ? w.seed : nullptr));
     } else {
       const int ntiles = (ng + 127) / 128;
       used_splits = split_count(splits, ntiles);
@@ -647,6 +676,7 @@ int serve_knn(const float* xq, int b, int d, const gcr_params* p, int k, int kp,
   ra.unc_count = w.unc_count; ra.unc_row = w.unc_row; ra.unc_kind = w.unc_kind; ra.unc_thr = w.unc_thr;
   ra.stats = stats;
   ra.band_cnt = w.band_cnt; ra.band_v = w.band_v; ra.band_i = w.band_i; ra.bcap = kBandCap; ra.band_rows = b;
+  ra.floor = seeded ? w.seed : nullptr;
   {
     StageScope sc_(GCR_STAGE_REFINE, st);
     GCR_CUDA_TRY(launch_refine_pool(ra, st));
@@ -1037,6 +1067,8 @@ int gcr_gallery_build(const float* Xg, int64_t ng, int32_t d, const gcr_params* 
     GCR_CUDA_TRY(launch_propagate(w.g.op_rowptr, w.g.op_len, w.g.op_col, w.g.op_val, cur, nxt, n, d,
                                   p->k > 0 ? w.g.row_order : nullptr, st));
   }
+  if (p->T >= 1 && p->k > 0)
+    GCR_CUDA_TRY(cudaMemcpyAsync(g.nbr, w.g.nbr, sizeof(int32_t) * (size_t)n * p->k, cudaMemcpyDeviceToDevice, st));
   for (int t = 0; t <= p->T; ++t) {
     GCR_CUDA_TRY(launch_row_stats(g.layers + (size_t)t * n * d, n, d, g.n64 + (size_t)t * n, g.n32 + (size_t)t * n,
                                   bf ? g.xr + (size_t)t * n * d * es : nullptr, elt_of(p),
@@ -1077,7 +1109,10 @@ int gcr_serve(const void* state, size_t state_bytes, int64_t ng, const float* Xq
   int cur = 0;
   for (int t = 0; t < p->T; ++t) {
     if (p->k > 0) {
-      s = serve_knn(w.xq[cur], nq, d, p, p->k, r.kp, gallery_layer(g, t, n, d, elt_size(p)), n, w, stp, w.nbr, w.d2, st);
+      SeedSource src;  // every search after the first starts from the previous one's pool
+      if (t > 0) src.prev_kp = r.kp;
+      s = serve_knn(w.xq[cur], nq, d, p, p->k, r.kp, gallery_layer(g, t, n, d, elt_size(p)), n, w, stp, w.nbr, w.d2,
+                    st, src);
       if (s != GCR_OK) return s;
     }
     StageScope sc_(GCR_STAGE_PROPAGATE, st);
@@ -1085,8 +1120,21 @@ int gcr_serve(const void* state, size_t state_bytes, int64_t ng, const float* Xq
                                    w.d2, p->k, p->gamma, p->symmetric, w.xq[cur ^ 1], st));
     cur ^= 1;
   }
+  // the final search starts from the last layer search's pool, those rows' gallery lists and,
+  // when it must certify more rows than that pool holds, a sample of the gallery (the lists
+  // mostly lead back into the pool's own clusters)
+  SeedSource src;
+  if (p->T >= 1 && p->k > 0) {
+    src.prev_kp = r.kp;
+    if (r.kp * (1 + p->k) <= kSeedCandidates) {
+      src.hop = g.nbr;
+      src.hop_k = p->k;
+    }
+    if (p->topk_out > r.kp)
+      src.sample = (int)std::min<int64_t>(ng, kSeedCandidates - (int64_t)r.kp * (1 + src.hop_k));
+  }
   return serve_knn(w.xq[cur], nq, d, p, p->topk_out, serve_kp_final(p), gallery_layer(g, p->T, n, d, elt_size(p)), n, w, stp,
-                   idx_out, dist_out, st);
+                   idx_out, dist_out, st, src);
 }
 
 size_t gcr_pipeline_workspace_size(int64_t n, int64_t nq, int32_t d, const gcr_params* p) {

@@ -43,9 +43,12 @@ cudaError_t launch_sgemm_dist(const float* Xq, int nq, const float* Xg, int ng, 
 
 // ---- umma.cu (tcgen05 path; operands BF16 or TF32)
 // Pools of S = A . B^T rows: [split][kind][na][kp], kp = 32, 64 or 128.
+// seed (may be NULL): per row of A an admission floor; every split keeps only scores above it,
+// so a merged pool may hold fewer than kp entries, and every score left out of it is <= the
+// floor or <= its last entry.
 cudaError_t launch_umma_pool(const void* Ab, int na, const void* Bb, int nb, int d, Elt elt,
                              const int* cam, bool cross, int self_excl, int kp, int splits, float* pool_v,
-                             int* pool_i, cudaStream_t st);
+                             int* pool_i, cudaStream_t st, const float* seed = nullptr);
 // Threshold rescan: gathered rows Ab (cap rows, *count valid) against the n rows of Xb.
 cudaError_t launch_umma_band(const void* Xb, int n, int d, Elt elt, const int* cam, int self_excl,
                              const void* Ab, const int* count, int cap, const int* band_row,
@@ -95,8 +98,35 @@ struct RefineArgs {
   int bcap;
   int band_rows;            // capacity of the band buffers (rows beyond it are not rescanned)
   const int* order;         // processing order of the rows (NULL: 0..n-1); results do not depend on it
+  const float* floor;       // per row (kinds == 1), or NULL: the admission floor the pools were
+                            // searched with (a bound on every score left out of a short pool)
 };
 cudaError_t launch_refine_pool(const RefineArgs& a, cudaStream_t st);
+// Split-pool seeds of the serving search (see refine.cu): for each of the b query rows of xq,
+// an admission floor for its search against the gallery G, from the FP32 scores of the distinct
+// rows of the row's previous pool (prev_kp entries of pool_i), of their hop lists (hop_k per
+// gallery row, when hop != NULL) and of the sample rows floor(i * ng / sample), i < sample:
+// below the approximate score of every candidate among the best min(valid, kp), so that the
+// search keeps at least that many. -inf when fewer than k distinct candidates.
+constexpr int kSeedCandidates = 4096;  // prev_kp * (1 + hop_k) + sample must not exceed this
+struct SeedArgs {
+  const float* xq;          // b x d query rows of this search (FP32)
+  const float* G;           // ng x d gallery rows of this search (FP32)
+  int b, ng, d, precision;
+  const double* n64q;       // ||x_q||^2
+  const float* enrm;        // rounding statistics of the query rows (tensor-core modes)
+  const float* anrm;
+  const RowScalars* gsc;    // maxima over the gallery rows
+  const int* pool_i;        // b x prev_kp
+  int prev_kp;
+  const int32_t* hop;       // ng x hop_k, or NULL
+  int hop_k;
+  int sample;               // evenly spaced gallery rows added to the candidates (0..ng)
+  int k;                    // neighbours this search must certify
+  int kp;                   // pool size of this search
+  float* seed;              // b
+};
+cudaError_t launch_serve_seed(const SeedArgs& a, cudaStream_t st);
 cudaError_t launch_refine_band(const RefineArgs& a, cudaStream_t st);
 // Cluster-local row order from the pools (first k candidates): order[0..n) is a permutation.
 cudaError_t launch_row_order(const int* pool_i, int n, int kp, int k, int* key, int* cnt, int* off, int* fill,

@@ -21,15 +21,19 @@ namespace gcr {
 // reads during a merge are both conflict-free.
 struct PoolOwner {
   float tau;
+  float floor;  // admission floor (or -inf): scores at or below it are dropped, so tau never
+                // drops below it; the caller bounds what was dropped by it
   int qcnt;
   int len;
 };
 
-__device__ __forceinline__ void pool_init(PoolOwner& o, bool valid) {
-  o.tau = valid ? -CUDART_INF_F : CUDART_INF_F;
+__device__ __forceinline__ void pool_init(PoolOwner& o, bool valid, float floor) {
+  o.floor = floor;
+  o.tau = valid ? floor : CUDART_INF_F;
   o.qcnt = 0;
   o.len = 0;
 }
+__device__ __forceinline__ void pool_init(PoolOwner& o, bool valid) { pool_init(o, valid, -CUDART_INF_F); }
 
 // Branch-free append: the candidate is always written into the next free slot and the count
 // only advances when it passes (ok and v > tau). The caller guarantees qcnt < kQCap before
@@ -108,7 +112,7 @@ __device__ __forceinline__ void pool_merge_apply(int owner, int lane, float* lv,
   if (lane == owner) {
     me.len = r.len;
     me.qcnt = 0;
-    me.tau = (r.len == KP) ? r.last : -CUDART_INF_F;
+    me.tau = (r.len == KP) ? fmaxf(r.last, me.floor) : me.floor;
   }
 }
 

@@ -369,7 +369,11 @@ __global__ void __launch_bounds__(256) refine_pool_kernel(RefineArgs a) {
     return r;
   };
   const float s_k = pool_at(kk - 1);
-  const float tau = pool_at(KP - 1);
+  // bound on every approximate score left out of the pool: its last entry when full, else the
+  // admission floor it was searched with (-inf: nothing was left out)
+  const float fl = a.floor ? a.floor[row] : -CUDART_INF_F;
+  const bool full = mvalid == KP;
+  const float tau = full ? pool_at(KP - 1) : fl;
   double delta, eps;
   RowScalars sc;
   bounds<P>(a, row, VPL, delta, eps, sc);
@@ -383,7 +387,7 @@ __global__ void __launch_bounds__(256) refine_pool_kernel(RefineArgs a) {
   if (lane == 0 && a.stats) atomicAdd(&a.stats[GCR_STAT_RESCORED], (unsigned long long)r);
   wl_sort<P>(L, lane);
   const double sig_k = wl_sig(L, kk - 1);
-  if (mvalid == KP) {
+  if (full || fl > -CUDART_INF_F) {
     const bool cert = (sig_k - eps) > ((double)tau + delta - 0.5 * sc.nmin);
     // Saturated pool: the density of the pool's lower half, extrapolated over the band's
     // window below tau (about 2*delta wide), predicts more than 512 band entries, so the
@@ -393,7 +397,7 @@ __global__ void __launch_bounds__(256) refine_pool_kernel(RefineArgs a) {
     const float mid = pool_at(KP / 2);
     const double dens = (KP / 2) / fmax((double)mid - (double)tau, 1e-30);
     const double below = fmax(0.0, 2.0 * delta + 0.5 * (sc.nmax - sc.nmin) - ((double)s_k - (double)tau));
-    const bool saturated = KP + dens * below > 512.0;
+    const bool saturated = full && KP + dens * below > 512.0;
     if (!cert && lane == 0) {
       if (a.stats) atomicAdd(&a.stats[GCR_STAT_UNCERTIFIED], 1ull);
       if (saturated) {
@@ -556,6 +560,145 @@ cudaError_t launch_pool_vpl(const RefineArgs& a, cudaStream_t st) {
 }
 
 }  // namespace
+
+// ---------------------------------------------------------------------------- split-pool seeds
+// Serving splits the gallery sweep of a query batch over many CTAs, and each split's pool starts
+// empty: most of the search's time goes to filling those pools. A seed s_q lets every split
+// admit only scores above it. It comes from distinct gallery rows j scored here in FP32 (the
+// rows of the query's previous pool, their gallery kNN lists and, where those cannot supply k
+// rows, an evenly spaced sample of the gallery, whose best scores bound the sweep's quantile at
+// about (k - graph candidates) / sample from below): with valid such rows, V =
+// min(valid, kp) and S the V-th best of their scores, each within eps of the exact dot product,
+// and delta the certified bound of the GEMM's approximate scores (the same delta the refinement
+// uses), V rows have an approximate score >= S - eps - delta, so the search keeps at least V
+// entries above s_q = (S - eps - delta - (spread of the gallery's squared norms) / 2, rounded
+// down, one ulp lower). A pool may then hold fewer than kp entries; the refinement takes s_q as
+// the bound on every score left out of it and certifies (or rescans) the row as for a full
+// pool. With fewer than k candidates the seed is -inf and the row is searched unseeded.
+constexpr int kSeedCap = kSeedCandidates;  // candidate slots per query
+
+// Ascending bitonic sort of n (a power of two, <= kSeedCap) values in shared memory; the block's
+// threads share the compare-exchanges. KEY_DESC sorts descending instead.
+template <typename T, bool DESC>
+__device__ void block_bitonic(T* v, int n) {
+  for (int size = 2; size <= n; size <<= 1) {
+    for (int stride = size >> 1; stride > 0; stride >>= 1) {
+      for (int e = threadIdx.x; e < (n >> 1); e += blockDim.x) {
+        const int lo = 2 * e - (e & (stride - 1));
+        const int hi = lo + stride;
+        const bool up = ((lo & size) == 0) != DESC;
+        const T a = v[lo], b = v[hi];
+        if ((a > b) == up) { v[lo] = b; v[hi] = a; }
+      }
+      __syncthreads();
+    }
+  }
+}
+
+__global__ void __launch_bounds__(1024) serve_seed_kernel(SeedArgs a) {
+  __shared__ int cand[kSeedCap];
+  __shared__ float score[kSeedCap];
+  __shared__ int s_valid;
+  const int q = blockIdx.x, t = threadIdx.x, lane = t & 31, warp = t >> 5;
+  const int per = 1 + (a.hop ? a.hop_k : 0);
+  const int total1 = a.prev_kp * per;
+  const int total = total1 + a.sample;
+  int N = 32;
+  while (N < total) N <<= 1;
+  // candidates: the previous pool's rows, each followed by its hop list, then the evenly spaced
+  // sample rows floor(i * ng / sample) (absent entries: INT_MAX)
+  for (int e = t; e < N; e += blockDim.x) {
+    int j = -1;
+    if (e < total1) {
+      const int p = e / per, h = e % per;
+      const int j0 = a.pool_i[(size_t)q * a.prev_kp + p];
+      j = h == 0 ? j0 : (j0 >= 0 && j0 < a.ng ? a.hop[(size_t)j0 * a.hop_k + h - 1] : -1);
+    } else if (e < total) {
+      j = (int)((long)(e - total1) * a.ng / a.sample);
+    }
+    cand[e] = (j >= 0 && j < a.ng) ? j : INT_MAX;
+  }
+  if (t == 0) s_valid = 0;
+  __syncthreads();
+  block_bitonic<int, false>(cand, N);
+  // FP32 score of each distinct candidate (duplicates and absent slots: -inf); each warp takes
+  // four candidates at a time (their row loads in flight together), each lane a sequential chain
+  // over its slice, then the butterfly
+  const int vpl = (a.d + 127) / 128;
+  const float* x = a.xq + (size_t)q * a.d;
+  int nv = 0;
+  for (int e0 = warp * 4; e0 < N; e0 += (blockDim.x >> 5) * 4) {
+    int j[4];
+    bool ok[4];
+    float acc[4];
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+      const int e = e0 + c;
+      j[c] = cand[e];
+      ok[c] = j[c] != INT_MAX && (e == 0 || cand[e - 1] != j[c]);
+      acc[c] = 0.f;
+    }
+    for (int v = 0; v < vpl; ++v) {
+      const int off = v * 128 + lane * 4;
+      if (off < a.d) {
+        const float4 xv = *reinterpret_cast<const float4*>(x + off);
+        float4 gv[4];
+#pragma unroll
+        for (int c = 0; c < 4; ++c)
+          gv[c] = ok[c] ? *reinterpret_cast<const float4*>(a.G + (size_t)j[c] * a.d + off) : make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+          acc[c] = fmaf(xv.x, gv[c].x, acc[c]);
+          acc[c] = fmaf(xv.y, gv[c].y, acc[c]);
+          acc[c] = fmaf(xv.z, gv[c].z, acc[c]);
+          acc[c] = fmaf(xv.w, gv[c].w, acc[c]);
+        }
+      }
+    }
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+      acc[c] = warp_sum(acc[c]);
+      nv += ok[c] ? 1 : 0;
+      if (lane == 0) score[e0 + c] = ok[c] ? acc[c] : -CUDART_INF_F;
+    }
+  }
+  if (lane == 0 && nv) atomicAdd(&s_valid, nv);
+  __syncthreads();
+  const int valid = s_valid;
+  block_bitonic<float, true>(score, N);
+  if (t != 0) return;
+  if (valid < a.k || a.k < 1) {
+    a.seed[q] = -CUDART_INF_F;
+    return;
+  }
+  RowScalars sc = *a.gsc;
+  const double bmax = sqrt(sc.nmax) * (1.0 + 1e-12);
+  const double b_i = sqrt(a.n64q[q]);
+  double delta;
+  if (a.precision == GCR_PREC_FP32) {
+    delta = gamma_n((double)a.d, kU32) * b_i * bmax;
+  } else {
+    const double ai = a.anrm[q], ei = a.enrm[q];
+    delta = ai * sc.emax + ei * bmax + gamma_n((double)a.d + 32.0, kU32rz) * ai * sc.amax;
+  }
+  delta *= 1.0 + 1e-6;
+  const double eps = gamma_n((double)(4 * vpl + 6), kU32) * b_i * bmax * (1.0 + 1e-6);
+  // below the approximate score of each of the best V candidates (their exact scores are within
+  // eps of these, their approximate ones within delta of the exact), with the spread of the
+  // gallery's squared norms as slack for ranking by distance rather than by score
+  const int V = valid < a.kp ? valid : a.kp;
+  const double th = (double)score[V - 1] - eps - delta - 0.5 * (sc.nmax - sc.nmin);
+  a.seed[q] = nextafterf(__double2float_rd(th), -CUDART_INF_F);
+}
+
+cudaError_t launch_serve_seed(const SeedArgs& a, cudaStream_t st) {
+  const long total = (long)a.prev_kp * (1 + (a.hop ? a.hop_k : 0)) + a.sample;
+  if (total > kSeedCap || a.prev_kp < 1 || a.kp < 1 || a.k < 1 || a.k > a.kp || a.b < 1 || a.sample < 0 ||
+      a.sample > a.ng)
+    return cudaErrorInvalidValue;
+  serve_seed_kernel<<<a.b, 1024, 0, st>>>(a);
+  return cudaGetLastError();
+}
 
 cudaError_t launch_refine_pool(const RefineArgs& a, cudaStream_t st) {
   if (a.kp == 32) return launch_pool_vpl<1>(a, st);

@@ -173,6 +173,7 @@ struct UmmaArgs {
   // POOL
   float* pool_v;
   int* pool_i;
+  const float* seed;  // per row of A, or NULL: admission floor of the row's split pools
   // BAND
   const int* count;
   int cap;
@@ -385,7 +386,7 @@ umma_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
     if (MODE == POOL) {
       my_row = blockIdx.x * BM + r;
       const bool valid = my_row < a.a_rows;
-      pool_init(me, valid);
+      pool_init(me, valid, (valid && a.seed) ? a.seed[my_row] : -CUDART_INF_F);
       if (CROSS && valid) my_cam = a.cam[my_row];
     }
     for (int t = 0; t < tl.count; ++t) {
@@ -591,7 +592,7 @@ int umma_read_and_clear_timeouts() {
 
 cudaError_t launch_umma_pool(const void* Ab, int na, const void* Bb, int nb, int d, Elt elt,
                              const int* cam, bool cross, int self_excl, int kp, int splits, float* pool_v,
-                             int* pool_i, cudaStream_t st) {
+                             int* pool_i, cudaStream_t st, const float* seed) {
   CUtensorMap ta, tb;
   cudaError_t e = make_map(&ta, Ab, elt, na, d, BM);
   if (e != cudaSuccess) return e;
@@ -613,6 +614,7 @@ cudaError_t launch_umma_pool(const void* Ab, int na, const void* Bb, int nb, int
   a.cam = cam;
   a.pool_v = pool_v;
   a.pool_i = pool_i;
+  a.seed = seed;
   dim3 grid((na + BM - 1) / BM, splits);
   if (kp == 32) return cross ? launch<POOL, 32, true>(ta, tb, a, grid, st) : launch<POOL, 32, false>(ta, tb, a, grid, st);
   if (kp == 64) return cross ? launch<POOL, 64, true>(ta, tb, a, grid, st) : launch<POOL, 64, false>(ta, tb, a, grid, st);

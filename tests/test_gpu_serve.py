@@ -76,6 +76,36 @@ def test_serve_matches_oracle(gcr, precision):
     assert _check_topk(layers[2], xq, idx, dist, 50) == 0
 
 
+@pytest.mark.parametrize("precision", ["bf16", "tf32"])
+def test_serve_seeded_splits_match_oracle(gcr, precision):
+    """A gallery wide enough for every split of the sweep to see many column tiles: the searches
+    after the first run with admission floors (short split pools), the final one from the last
+    pool's rows and their gallery lists. The certified top-K must still be the oracle's, with no
+    row clamped below k."""
+    from paper_2306_08792_gb300.serving import Gallery
+    ng, d, K = 60000, 256, 100
+    w = workloads.serving(seed=3, n_gallery=ng, d=d, n_clusters=3000, n_requests=6)
+    p = gcr.default_params(k=20, T=2, topk_out=K, precision=precision)
+    G = Gallery(torch.from_numpy(w.gallery).cuda(), p)
+    layers, degs = _gallery_host(G, p, ng, d)
+    Q = np.concatenate([w.queries(r) for r in range(6)])[:24]
+    Xq = torch.from_numpy(Q).cuda()
+    import ctypes
+    from paper_2306_08792_gb300 import _lib
+    need = _lib.load().gcr_serve_workspace_size(Q.shape[0], ng, d, ctypes.byref(p))
+    ws = torch.empty(need, dtype=torch.uint8, device="cuda")
+    idx = torch.empty(Q.shape[0], K, dtype=torch.int32, device="cuda")
+    dist = torch.empty(Q.shape[0], K, dtype=torch.float32, device="cuda")
+    stats = torch.zeros(8, dtype=torch.int64, device="cuda")
+    G.serve(Xq, idx, dist, ws, stats)
+    torch.cuda.synchronize()
+    assert int(stats[5]) == 0  # GCR_STAT_CLAMPED
+    xq = oracle.l2_normalize(Q)
+    for t in range(2):
+        xq = oracle.serve_oracle._query_step(xq, layers[t], degs[t], 20, p.gamma, True)
+    assert _check_topk(layers[2], xq, idx.cpu().numpy(), dist.cpu().numpy(), K) == 0
+
+
 @pytest.mark.parametrize("precision", PRECISIONS)
 def test_serve_result_is_the_same_alone_and_in_the_mix(gcr, precision):
     from paper_2306_08792_gb300.serving import Gallery
