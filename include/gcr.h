@@ -282,12 +282,14 @@ int gcrv_mean_profiles(const float* frames, int64_t F, int32_t d, const int64_t*
  *    (w_qj of Eq. 4) and normalises it; then it returns the certified top K = topk_out
  *    (1..127) of the gallery on G_T: idx_out int32 [b][K] by ascending squared distance
  *    (ties to the smaller index) and dist_out float [b][K] (FP32 re-scored distances).
- * In the tensor-core modes every search after the first gives its column-split pools an
- * admission floor, from the FP32 scores of the previous search's candidates (and, for the
- * final search, of their gallery neighbours): provably below the approximate scores of at
- * least k of the query's gallery rows, so the splits skip most of the pool merging and the
- * certification (which takes the floor as the bound on every score it left out) is unchanged;
- * the results are the same certified neighbours as without floors.
+ * In the tensor-core modes the searches give their column-split pools admission floors,
+ * from the FP32 scores of the previous search's candidates (for the final search also of
+ * their gallery neighbours) and, where those cannot supply enough rows, of an evenly spaced
+ * sample of the gallery (the first search, for b >= 32, has only the sample; for b < 32 it
+ * runs without a floor): provably below the approximate scores of at least k of the query's
+ * gallery rows, so the splits skip most of the pool merging; the certification takes the
+ * floor as the bound on every score it left out, and the results are the same certified
+ * neighbours as without floors.
  * Every step is per query, so a query's result does not depend on its batch-mates. The
  * state is read-only during gcr_serve: concurrent calls with distinct workspaces may share
  * it. No host synchronisation: a call can be captured in a CUDA graph.

@@ -639,14 +639,14 @@ int serve_knn(const float* xq, int b, int d, const gcr_params* p, int k, int kp,
   GCR_CUDA_TRY(cudaMemsetAsync(w.band_cnt, 0, sizeof(int) * b, st));
   int used_splits;
   // the split pools' admission floors (tensor-core modes), from the previous search's merged
-  // pool and, when given, its rows' gallery lists
-  const bool seeded = bf && seed_src.prev_kp > 0 &&
+  // pool, when given its rows' gallery lists, and a sample of the gallery
+  const bool seeded = bf && (seed_src.prev_kp > 0 || seed_src.sample > 0) &&
                       (long)seed_src.prev_kp * (1 + seed_src.hop_k) + seed_src.sample <= kSeedCandidates;
   if (seeded) {
     SeedArgs sa;
     sa.xq = xq; sa.G = G; sa.b = b; sa.ng = ng; sa.d = d; sa.precision = p->precision;
     sa.n64q = w.n64; sa.enrm = w.enrm; sa.anrm = w.anrm; sa.gsc = gs.sc;
-    sa.pool_i = w.pool_i; sa.prev_kp = seed_src.prev_kp; sa.hop = seed_src.hop; sa.hop_k = seed_src.hop ? seed_src.hop_k : 0;
+    sa.pool_i = seed_src.prev_kp > 0 ? w.pool_i : nullptr; sa.prev_kp = seed_src.prev_kp; sa.hop = seed_src.hop; sa.hop_k = seed_src.hop ? seed_src.hop_k : 0;
     sa.sample = seed_src.sample; sa.k = k; sa.kp = kp; sa.seed = w.seed;
     StageScope sc_(GCR_STAGE_PREP, st);
     GCR_CUDA_TRY(launch_serve_seed(sa, st));
@@ -1109,8 +1109,15 @@ int gcr_serve(const void* state, size_t state_bytes, int64_t ng, const float* Xq
   int cur = 0;
   for (int t = 0; t < p->T; ++t) {
     if (p->k > 0) {
-      SeedSource src;  // every search after the first starts from the previous one's pool
-      if (t > 0) src.prev_kp = r.kp;
+      // every search after the first starts from the previous search's pool; the first one, for
+      // 32 queries or more, from a sample of the gallery (the seed kernel, one latency-bound CTA
+      // per query, costs more than it saves for fewer: measured 1.63 -> 1.76 ms per call at b = 1,
+      // 2.75 -> 2.37 ms at b = 64 on a 500,000 x 256 gallery)
+      SeedSource src;
+      if (t > 0)
+        src.prev_kp = r.kp;
+      else if (nq >= 32)
+        src.sample = (int)std::min<int64_t>(ng, kSeedCandidates);
       s = serve_knn(w.xq[cur], nq, d, p, p->k, r.kp, gallery_layer(g, t, n, d, elt_size(p)), n, w, stp, w.nbr, w.d2,
                     st, src);
       if (s != GCR_OK) return s;

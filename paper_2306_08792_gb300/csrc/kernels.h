@@ -117,7 +117,7 @@ struct SeedArgs {
   const float* enrm;        // rounding statistics of the query rows (tensor-core modes)
   const float* anrm;
   const RowScalars* gsc;    // maxima over the gallery rows
-  const int* pool_i;        // b x prev_kp
+  const int* pool_i;        // b x prev_kp (NULL when prev_kp == 0)
   int prev_kp;
   const int32_t* hop;       // ng x hop_k, or NULL
   int hop_k;

@@ -565,9 +565,10 @@ cudaError_t launch_pool_vpl(const RefineArgs& a, cudaStream_t st) {
 // Serving splits the gallery sweep of a query batch over many CTAs, and each split's pool starts
 // empty: most of the search's time goes to filling those pools. A seed s_q lets every split
 // admit only scores above it. It comes from distinct gallery rows j scored here in FP32 (the
-// rows of the query's previous pool, their gallery kNN lists and, where those cannot supply k
-// rows, an evenly spaced sample of the gallery, whose best scores bound the sweep's quantile at
-// about (k - graph candidates) / sample from below): with valid such rows, V =
+// rows of the query's previous pool, their gallery kNN lists and, where there is no previous
+// pool or it cannot supply k rows, an evenly spaced sample of the gallery, whose best scores
+// bound the sweep's quantile at about (k - graph candidates) / sample from below): with valid
+// such rows, V =
 // min(valid, kp) and S the V-th best of their scores, each within eps of the exact dot product,
 // and delta the certified bound of the GEMM's approximate scores (the same delta the refinement
 // uses), V rows have an approximate score >= S - eps - delta, so the search keeps at least V
@@ -693,8 +694,8 @@ __global__ void __launch_bounds__(1024) serve_seed_kernel(SeedArgs a) {
 
 cudaError_t launch_serve_seed(const SeedArgs& a, cudaStream_t st) {
   const long total = (long)a.prev_kp * (1 + (a.hop ? a.hop_k : 0)) + a.sample;
-  if (total > kSeedCap || a.prev_kp < 1 || a.kp < 1 || a.k < 1 || a.k > a.kp || a.b < 1 || a.sample < 0 ||
-      a.sample > a.ng)
+  if (total > kSeedCap || total < 1 || a.prev_kp < 0 || (a.prev_kp > 0 && !a.pool_i) || a.kp < 1 || a.k < 1 ||
+      a.k > a.kp || a.b < 1 || a.sample < 0 || a.sample > a.ng)
     return cudaErrorInvalidValue;
   serve_seed_kernel<<<a.b, 1024, 0, st>>>(a);
   return cudaGetLastError();

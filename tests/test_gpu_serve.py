@@ -78,17 +78,17 @@ def test_serve_matches_oracle(gcr, precision):
 
 @pytest.mark.parametrize("precision", ["bf16", "tf32"])
 def test_serve_seeded_splits_match_oracle(gcr, precision):
-    """A gallery wide enough for every split of the sweep to see many column tiles: the searches
-    after the first run with admission floors (short split pools), the final one from the last
-    pool's rows and their gallery lists. The certified top-K must still be the oracle's, with no
-    row clamped below k."""
+    """A gallery wide enough for every split of the sweep to see many column tiles: every
+    search runs with admission floors (short split pools), the first from a sample of the
+    gallery, the final one from the last pool's rows, their gallery lists and the sample. The
+    certified top-K must still be the oracle's, with no row clamped below k."""
     from paper_2306_08792_gb300.serving import Gallery
     ng, d, K = 60000, 256, 100
     w = workloads.serving(seed=3, n_gallery=ng, d=d, n_clusters=3000, n_requests=6)
     p = gcr.default_params(k=20, T=2, topk_out=K, precision=precision)
     G = Gallery(torch.from_numpy(w.gallery).cuda(), p)
     layers, degs = _gallery_host(G, p, ng, d)
-    Q = np.concatenate([w.queries(r) for r in range(6)])[:24]
+    Q = w.queries_of(40)  # 32 or more: the first search is seeded from the gallery sample too
     Xq = torch.from_numpy(Q).cuda()
     import ctypes
     from paper_2306_08792_gb300 import _lib
