@@ -186,6 +186,11 @@ def test_serving_validation_on_host(lib):
         kw.update(bad)
         q = _params(lib, **kw)
         assert lib.gcr_gallery_bytes(500000, 256, ctypes.byref(q)) == 0, bad
+    # the state keeps the last gallery graph's kNN lists (the final search's seed candidates):
+    # ng * k int32, the only region that grows with k
+    p30 = _params(lib, k=30, T=2, topk_out=100)
+    grow = lib.gcr_gallery_bytes(500000, 256, ctypes.byref(p30)) - lib.gcr_gallery_bytes(500000, 256, ctypes.byref(p))
+    assert 500000 * 10 * 4 <= grow < 500000 * 10 * 4 + 512
     v = ctypes.c_void_p(16)
     assert lib.gcr_serve(v, 1 << 40, 500000, v, 8, 256, ctypes.byref(p), v, v, None, None, 0, None) == 2
     assert lib.gcr_serve(None, 1 << 40, 500000, v, 8, 256, ctypes.byref(p), v, v, None, v, 1 << 40, None) == 1
