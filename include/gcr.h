@@ -201,13 +201,19 @@ int gcr_rerank(const float* Xq, int64_t nq, const float* Xg, int64_t ng, int32_t
  * once memory is fragmented), or an application that embeds this library without giving
  * it an allocator. The paper has no counterpart; this is an interface convenience.
  * Same arguments, results and errors as gcr_rerank, except that the scratch lives in a
- * fixed device array of GCR_RERANK_NOALLOC_SCRATCH_BYTES compiled into the library: it is
- * present on every GPU that loads the library until the process exits, and the call
- * returns GCR_E_WORKSPACE, launching nothing, when gcr_rerank_workspace_size() of the
- * problem exceeds it (for FP32, roughly nq * ng <= 4 million). The array's device address
- * is looked up on the first call made with a given device current, so make that first call
- * before any stream capture. Every call shares the one array: calls whose work overlaps on
- * the GPU race and must be serialised by the caller. Allocates no memory. */
+ * fixed device array of GCR_RERANK_NOALLOC_SCRATCH_BYTES compiled into the library. The
+ * driver reserves that array on a device when it loads the library's device code there; with
+ * CUDA's lazy module loading (the default) that happens during the first call of this entry
+ * point with the device current, and it then stays reserved until the process exits. That
+ * first call also looks up and caches the array's device address. So make the first call on
+ * each device during start-up, before the process fixes its memory budget (a first call with
+ * the device already full fails with GCR_E_CUDA) and before any stream capture. The cached
+ * address holds until the device is reset (cudaDeviceReset or a new primary context); do not
+ * call this entry point on a device after resetting it. The call returns GCR_E_WORKSPACE,
+ * launching nothing, when gcr_rerank_workspace_size() of the problem exceeds the array (for
+ * FP32 full rankings, roughly nq * ng <= 4 million). Every call shares the one array: calls
+ * whose work overlaps on the GPU race and must be serialised by the caller. No call
+ * allocates device memory itself. */
 #define GCR_RERANK_NOALLOC_SCRATCH_BYTES ((size_t)16 << 20)
 int gcr_rerank_noalloc(const float* Xq, int64_t nq, const float* Xg, int64_t ng, int32_t d,
                        const gcr_params* p, int32_t* idx_out, float* dist_out, gcr_stream_t stream);

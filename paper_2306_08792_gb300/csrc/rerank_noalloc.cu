@@ -9,10 +9,14 @@
 // fixed array that is part of the library's device image, so the call itself allocates
 // nothing.
 //
-// The array (GCR_RERANK_NOALLOC_SCRATCH_BYTES) exists on every GPU that loads the library
-// and stays resident until the process exits. Its device address is looked up once per
-// device, on the first call made with that device current; that first call should therefore
-// come before any stream capture. All calls share the one array: calls whose work overlaps
+// The array (GCR_RERANK_NOALLOC_SCRATCH_BYTES) is reserved on a device when the driver loads
+// this library's device code there. Under CUDA's lazy module loading (the default) that is the
+// cudaGetSymbolAddress call below, made during the first call of the entry point with the
+// device current; from then on it stays reserved until the process exits. A process that fixes
+// its memory budget at start-up should therefore make one call per device before doing so (with
+// the device already full, the first call fails with GCR_E_CUDA), and before any stream capture.
+// The address is cached per device; it stays valid until the device is reset (cudaDeviceReset,
+// or a new primary context), after which the entry point must not be called on that device. All calls share the one array: calls whose work overlaps
 // on the GPU (different streams, or different host threads without ordering) race on it and
 // must be serialised by the caller. Nothing in it needs to start at zero: every byte the
 // re-ranking reads is written earlier in the same call.

@@ -134,6 +134,8 @@ class Server:
                 dist_host=torch.zeros(max_batch, K, dtype=torch.float32).pin_memory(),
                 ws=torch.empty(full, dtype=torch.uint8, device=dev)))
         self.in_flight_bytes = 0
+        self.max_in_flight_bytes = 0   # peak of the admitted workspace footprint
+        self.memory_waited = set()     # requests whose admission waited because the footprint would exceed the budget
         self.launches = 0
 
     # -------------------------------------------------------------------------- one batch
@@ -176,6 +178,7 @@ class Server:
         slot.batch, slot.rows = batch, rows
         slot.footprint = self.ws_of(B)
         self.in_flight_bytes += slot.footprint
+        self.max_in_flight_bytes = max(self.max_in_flight_bytes, self.in_flight_bytes)
         self.launches += 1
 
     def _finish(self, slot: _Slot, now: float):
@@ -201,6 +204,10 @@ class Server:
     def run(self, requests: List[Request], realtime: bool = True) -> dict:
         """Serve `requests` (sorted by arrival, seconds from start). With realtime=False every
         request is available at once (closed-loop saturation)."""
+        too_big = [r.rid for r in requests if r.queries.shape[0] > self.max_batch]
+        if too_big:
+            # such a request could never be admitted and the loop would wait for it forever
+            raise ValueError(f"requests {too_big[:8]} have more query rows than max_batch={self.max_batch}")
         pending = list(requests)
         pending.reverse()
         queue: List[Request] = []
@@ -221,6 +228,8 @@ class Server:
                     if rows + b > self.max_batch:
                         break
                     if self.in_flight_bytes + self.ws_of(_bucket(rows + b)) > self.budget:
+                        if not batch:
+                            self.memory_waited.add(queue[0].rid)
                         break
                     batch.append(queue.pop(0))
                     rows += b
@@ -235,7 +244,9 @@ class Server:
         span = max(r.done for r in requests) - (requests[0].arrival if realtime else 0.0)
         return {"requests": len(requests), "queries": nq, "seconds": span, "queries_per_s": nq / span,
                 "p50_ms": float(np.percentile(lat, 50) * 1e3), "p99_ms": float(np.percentile(lat, 99) * 1e3),
-                "mean_ms": float(lat.mean() * 1e3), "launches": self.launches}
+                "mean_ms": float(lat.mean() * 1e3), "launches": self.launches,
+                "budget_bytes": self.budget, "max_in_flight_bytes": self.max_in_flight_bytes,
+                "memory_waits": len(self.memory_waited)}
 
 
 def make_requests(workload, n: int, realtime: bool = True) -> List[Request]:

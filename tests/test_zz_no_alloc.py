@@ -75,6 +75,28 @@ def test_noalloc_matches_workspace_rerank_twice(lib):
         assert np.all(np.diff(dist.cpu().numpy(), axis=1) >= 0)
 
 
+def test_noalloc_topk_matches_workspace_rerank_twice(lib):
+    """Top-K re-ranking (1 <= topk_out <= 127) goes through the certified pool search, whose
+    scratch layout differs from the full ranking's; it too must match gcr_rerank."""
+    stream = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    p = _params(lib, topk_out=20)
+    for seed, (nq, ng, d) in ((2, (300, 1500, 128)), (3, (257, 1100, 64))):
+        w = workloads.plain(seed=seed, n_query=nq, n_gallery=ng, d=d)
+        X = torch.from_numpy(w.X).cuda()
+        X = X / X.norm(dim=1, keepdim=True)
+        Xq, Xg = X[:nq].contiguous(), X[nq:].contiguous()
+        assert lib.gcr_rerank_workspace_size(nq, ng, d, ctypes.byref(p)) <= (16 << 20)
+        idx = torch.full((nq, 20), -7, dtype=torch.int32, device="cuda")
+        dist = torch.full((nq, 20), float("nan"), dtype=torch.float32, device="cuda")
+        st = lib.gcr_rerank_noalloc(_p(Xq), nq, _p(Xg), ng, d, ctypes.byref(p), _p(idx), _p(dist), stream)
+        assert st == 0, lib.gcr_status_string(st)
+        ridx, rdist = _reference(lib, Xq, Xg, p, stream)
+        torch.cuda.synchronize()
+        assert torch.equal(idx, ridx)
+        assert float((dist - rdist).abs().max()) <= TOL
+        assert np.all(np.diff(dist.cpu().numpy(), axis=1) >= 0)
+
+
 def test_noalloc_refuses_problems_beyond_its_scratch(lib):
     stream = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
     p = _params(lib)
