@@ -84,21 +84,28 @@ typedef struct {
 enum {
   GCR_STAT_ROWS = 0,          /* (row, graph) pairs searched                               */
   GCR_STAT_UNCERTIFIED = 1,   /* pairs whose candidate pool could not certify the k-th
-                                 neighbour and went through the threshold (band) rescan  */
+                                 neighbour: they go through the ball search (tensor-core
+                                 modes of gcr_build_graph) and, where that does not
+                                 certify them, the threshold (band) rescan               */
   GCR_STAT_BAND_FAILED = 2,   /* pairs whose band rescan found more than 512 columns
                                  within the certified margin of the k-th (a dense
-                                 boundary): they keep the pool's exact top k, whose
-                                 exact scores are within 2*delta of the exact k-th score
-                                 (delta = the certified bound of the GEMM)               */
+                                 boundary the ball search did not take): they keep the
+                                 pool's exact top k, whose exact scores are within
+                                 2*delta of the exact k-th score (delta = the certified
+                                 bound of the GEMM)                                       */
   GCR_STAT_FP64_ROWS = 3,     /* pairs whose k-th / (k+1)-th boundary needed FP64          */
   GCR_STAT_FP64_DOTS = 4,     /* FP64 dot products computed for those boundaries           */
   GCR_STAT_CLAMPED = 5,       /* pairs with fewer than k eligible samples                  */
   GCR_STAT_RESCORED = 6,      /* FP32 re-scored candidates                                 */
-  GCR_STAT_SATURATED = 7,     /* uncertified pairs whose pool is saturated with near-ties:
-                                 the density of its lower half predicts more than 512
-                                 band entries, so the rescan is skipped; the same 2*delta
+  GCR_STAT_SATURATED = 7,     /* searches against a gallery (gcr_rerank top-K, gcr_serve):
+                                 uncertified pairs whose pool is saturated with near-ties
+                                 (its lower half's density predicts more than 512 band
+                                 entries), so the rescan is skipped; the same 2*delta
                                  guarantee as GCR_STAT_BAND_FAILED                        */
-  GCR_STATS_LEN = 8
+  GCR_STAT_BALL = 8,          /* uncertified pairs certified by the ball search: the exact
+                                 search, in coordinates centred on a shared ball, of every
+                                 sample that can be among their k nearest                 */
+  GCR_STATS_LEN = 9
 };
 
 /* The graph produced by gcr_build_graph and consumed by gcr_propagate. All arrays are
@@ -377,6 +384,7 @@ enum {
   GCR_STAGE_DIST_GEMM = 7, /* S7 re-ranked distance GEMM                    */
   GCR_STAGE_SORT = 8,      /* S7 segmented sort                             */
   GCR_STAGE_GCRV = 9,      /* S8 GCRV profile vectors                       */
+  GCR_STAGE_BALL = 10,     /* S3 ball search of the uncertified pairs       */
   GCR_STAGES = 12
 };
 int gcr_profile_enable(int on);

@@ -12,10 +12,11 @@ LIB_PATH = os.path.join(PKG, "libgcr.so")
 GCR_OK, GCR_E_INVALID, GCR_E_WORKSPACE, GCR_E_CUDA, GCR_E_TIMEOUT, GCR_E_UNSUPPORTED = range(6)
 GCR_PREC_FP32, GCR_PREC_BF16, GCR_PREC_TF32 = 0, 1, 2
 STAGE_NAMES = ["normalize", "prep", "sim_gemm", "refine", "band", "graph", "propagate", "dist_gemm", "sort",
-               "gcrv"]
+               "gcrv", "ball"]
 GCR_STAGES = 12
-STAT_NAMES = ["rows", "uncertified", "band_failed", "fp64_rows", "fp64_dots", "clamped", "rescored", "saturated"]
-GCR_STATS_LEN = 8
+STAT_NAMES = ["rows", "uncertified", "band_failed", "fp64_rows", "fp64_dots", "clamped", "rescored", "saturated",
+              "ball"]
+GCR_STATS_LEN = 9
 
 
 class Params(ctypes.Structure):

@@ -113,10 +113,17 @@ struct BuildWs {
   int* unc_row;
   int* unc_kind;
   float* unc_thr;
+  float* unc_dk;
+  float* dk_all;       // k-th distance bound of every (row, graph)
+  int* bq_count;       // pairs the ball search hands on to the band rescan
+  int* bq_row;
+  int* bq_kind;
+  float* bq_thr;
   int* band_cnt;
   float* band_v;
   int* band_i;
-  void* band_a;        // gathered rounded rows of the band rescan
+  void* band_a;        // gathered rounded rows of the band rescan (also the ball centres)
+  BallArgs ball;       // workspace of the ball search (tensor-core modes)
   float* w;
   int* cnt;
   int* fill;
@@ -160,10 +167,20 @@ size_t carve_build(Carve& c, int64_t n, int32_t d, const gcr_params* p, const Re
   t.unc_row = c.take<int>((size_t)kinds * nn);
   t.unc_kind = c.take<int>((size_t)kinds * nn);
   t.unc_thr = c.take<float>((size_t)kinds * nn);
+  t.unc_dk = c.take<float>((size_t)kinds * nn);
+  t.dk_all = c.take<float>((size_t)kinds * nn);
+  t.bq_count = c.take<int>(4);
+  t.bq_row = c.take<int>((size_t)kinds * nn);
+  t.bq_kind = c.take<int>((size_t)kinds * nn);
+  t.bq_thr = c.take<float>((size_t)kinds * nn);
   t.band_cnt = c.take<int>(band_rows);
   t.band_v = c.take<float>((size_t)band_rows * kBandCap);
   t.band_i = c.take<int>((size_t)band_rows * kBandCap);
   t.band_a = bf ? c.take<char>((size_t)band_rows * d * es) : nullptr;
+  std::memset(&t.ball, 0, sizeof(t.ball));
+  // ball search: up to 2n gathered members (centred rows and their operand copies); balls of
+  // one contracted cluster overlap, so their total can exceed n
+  if (bf && p->k > 0) carve_ball(c, (int)n, d, kinds, r.kp, elt_of(p), (int)std::min<int64_t>(2 * n, INT32_MAX / 2), &t.ball);
   t.w = c.take<float>((size_t)kinds * nn * p->k);
   t.cnt = c.take<int>((size_t)kinds * (nn + 1));
   t.fill = c.take<int>((size_t)kinds * nn);
@@ -236,24 +253,46 @@ int knn_impl(const float* X, int64_t n64_, int32_t d, const int32_t* cam, const 
   if (p->k == 0 && g->row_order)
     GCR_CUDA_TRY(launch_row_order(w.pool_i, n, r.kp, 0, w.okey, w.ocnt, w.ooff, w.ofill, order, st));
   if (p->k > 0) {
+    ra.unc_dk = w.unc_dk;
+    ra.dk_all = bf ? w.dk_all : nullptr;
+    // the tensor-core modes queue every uncertified pair for the ball search; FP32 keeps the
+    // prediction of saturated pools (no ball search on the CUDA-core path)
+    ra.skip_saturated = bf ? 0 : 1;
     {
       StageScope sc_(GCR_STAGE_REFINE, st, 5);
       GCR_CUDA_TRY(launch_row_order(w.pool_i, n, r.kp, p->k, w.okey, w.ocnt, w.ooff, w.ofill, order, st));
       ra.order = order;
       GCR_CUDA_TRY(launch_refine_pool(ra, st));
     }
-    // threshold rescan of the rows whose pool could not certify the k-th neighbour
+    // the queue the band rescan takes: the ball search's leftovers, or the refinement's queue
+    RefineArgs rb = ra;
+    if (bf) {
+      StageScope sc_(GCR_STAGE_BALL, st, 20);
+      BallArgs b = w.ball;
+      b.X = X; b.xr = w.xr; b.elt = elt; b.n = n; b.d = d; b.k = p->k; b.kp = r.kp; b.kinds = kinds;
+      b.precision = p->precision; b.n64 = w.n64; b.enrm = w.enrm; b.anrm = w.anrm; b.sc = w.sc; b.cam = camp;
+      b.pool_i = w.pool_i; b.unc_count = w.unc_count; b.unc_row = w.unc_row; b.unc_kind = w.unc_kind;
+      b.unc_dk = w.unc_dk; b.dk_all = w.dk_all; b.unc_cap = kinds * n; b.cent = w.band_a; b.err = w.err;
+      GCR_CUDA_TRY(launch_ball_prepare(b, st));
+      GCR_CUDA_TRY(launch_umma_gpool(b.Yr, b.cap_rows, d, elt, b.gcam, kinds == 2, 1, r.kp, b.items, b.ioff + n,
+                                     b.max_items, b.hy, b.gpool_v, b.gpool_i, st));
+      GCR_CUDA_TRY(cudaMemsetAsync(w.bq_count, 0, sizeof(int) * 4, st));
+      ra.bq_count = w.bq_count; ra.bq_row = w.bq_row; ra.bq_kind = w.bq_kind; ra.bq_thr = w.bq_thr;
+      GCR_CUDA_TRY(launch_refine_ball(ra, b, st));
+      rb.unc_count = w.bq_count; rb.unc_row = w.bq_row; rb.unc_kind = w.bq_kind; rb.unc_thr = w.bq_thr;
+    }
+    // threshold rescan of the pairs still uncertified
     StageScope sc_(GCR_STAGE_BAND, st, bf ? 3 : 2);
     if (bf) {
-      GCR_CUDA_TRY(launch_gather_rows(w.xr, (size_t)d * elt_bytes(elt), w.unc_count, w.unc_row, w.band_rows,
+      GCR_CUDA_TRY(launch_gather_rows(w.xr, (size_t)d * elt_bytes(elt), rb.unc_count, rb.unc_row, w.band_rows,
                                       w.band_a, st));
-      GCR_CUDA_TRY(launch_umma_band(w.xr, n, d, elt, camp, 1, w.band_a, w.unc_count, w.band_rows, w.unc_row,
-                                    w.unc_kind, w.unc_thr, kBandCap, w.band_cnt, w.band_v, w.band_i, st));
+      GCR_CUDA_TRY(launch_umma_band(w.xr, n, d, elt, camp, 1, w.band_a, rb.unc_count, w.band_rows, rb.unc_row,
+                                    rb.unc_kind, rb.unc_thr, kBandCap, w.band_cnt, w.band_v, w.band_i, st));
     } else {
-      GCR_CUDA_TRY(launch_sgemm_band(X, X, n, d, camp, 1, w.unc_count, w.band_rows, w.unc_row, w.unc_kind,
-                                     w.unc_thr, kBandCap, w.band_cnt, w.band_v, w.band_i, st));
+      GCR_CUDA_TRY(launch_sgemm_band(X, X, n, d, camp, 1, rb.unc_count, w.band_rows, rb.unc_row, rb.unc_kind,
+                                     rb.unc_thr, kBandCap, w.band_cnt, w.band_v, w.band_i, st));
     }
-    GCR_CUDA_TRY(launch_refine_band(ra, st));
+    GCR_CUDA_TRY(launch_refine_band(rb, st));
   }
   return GCR_OK;
 }
@@ -677,6 +716,7 @@ int serve_knn(const float* xq, int b, int d, const gcr_params* p, int k, int kp,
   ra.stats = stats;
   ra.band_cnt = w.band_cnt; ra.band_v = w.band_v; ra.band_i = w.band_i; ra.bcap = kBandCap; ra.band_rows = b;
   ra.floor = seeded ? w.seed : nullptr;
+  ra.skip_saturated = 1;  // no ball search against a gallery: saturated pools keep the 2 delta bound
   {
     StageScope sc_(GCR_STAGE_REFINE, st);
     GCR_CUDA_TRY(launch_refine_pool(ra, st));

@@ -6,6 +6,9 @@
 
 namespace gcr {
 
+struct Carve;     // bump allocator over a caller's workspace (common.cuh)
+struct BallArgs;  // ball search of the pairs a pool could not certify (below)
+
 // Element type of the tensor-core GEMM operands: BF16 copies of the rows, or FP32 rows
 // rounded to TF32 (10 explicit mantissa bits, low 13 bits zero).
 enum class Elt : int { BF16 = 0, TF32 = 1 };
@@ -49,11 +52,21 @@ cudaError_t launch_sgemm_dist(const float* Xq, int nq, const float* Xg, int ng, 
 cudaError_t launch_umma_pool(const void* Ab, int na, const void* Bb, int nb, int d, Elt elt,
                              const int* cam, bool cross, int self_excl, int kp, int splits, float* pool_v,
                              int* pool_i, cudaStream_t st, const float* seed = nullptr);
-// Threshold rescan: gathered rows Ab (cap rows, *count valid) against the n rows of Xb.
+// Pools of row blocks of the gathered matrix Y (rows x d, rounded operand) against column ranges
+// of Y: work item w = {first row, rows <= 128, first column, columns} of *n_items (<= max_items);
+// pool entry (s - col_bias[j], j), j a position in Y; column j == row skipped when self_excl;
+// gcam: camera per position (cross-camera pools). Pools [kind][rows][kp].
+cudaError_t launch_umma_gpool(const void* Y, int rows, int d, Elt elt, const int* gcam, bool cross, int self_excl,
+                              int kp, const int4* items, const int* n_items, int max_items, const float* col_bias,
+                              float* pool_v, int* pool_i, cudaStream_t st);
+// Threshold rescan: gathered rows Ab (cap rows, *count valid) against the n rows of Xb. Row u
+// counts every column whose score reaches band_thr[u] in band_cnt[u] and writes the first
+// band_lim[u] (NULL: bcap) of them at band_off[u] (NULL: u * bcap); band_v may be NULL.
 cudaError_t launch_umma_band(const void* Xb, int n, int d, Elt elt, const int* cam, int self_excl,
                              const void* Ab, const int* count, int cap, const int* band_row,
                              const int* band_kind, const float* band_thr, int bcap, int* band_cnt, float* band_v,
-                             int* band_i, cudaStream_t st);
+                             int* band_i, cudaStream_t st, const int* band_off = nullptr,
+                             const int* band_lim = nullptr);
 cudaError_t launch_umma_dist(const __nv_bfloat16* Qb, int nq, const __nv_bfloat16* Gb, int ng, int d,
                              const float* nrm_q, const float* nrm_g, float* D, cudaStream_t st);
 // G_s = Z_s Z_s^T + lambda n_s I for every camera s (d x d, FP32, [ncam][d][d]), Z the
@@ -90,6 +103,14 @@ struct RefineArgs {
   int* unc_row;
   int* unc_kind;
   float* unc_thr;
+  float* unc_dk;            // per queued pair (may be NULL): an upper bound on its exact k-th
+                            // squared distance
+  float* dk_all;            // [kinds][n] (may be NULL): the same bound for every (row, graph)
+  int skip_saturated;       // 1: pairs whose pool is saturated with near-ties are not queued
+  int* bq_count;            // ball refinement: pairs handed on to the band rescan
+  int* bq_row;
+  int* bq_kind;
+  float* bq_thr;
   unsigned long long* stats;
   // band rescan results
   const int* band_cnt;
@@ -102,6 +123,10 @@ struct RefineArgs {
                             // searched with (a bound on every score left out of a short pool)
 };
 cudaError_t launch_refine_pool(const RefineArgs& a, cudaStream_t st);
+// Refinement of the grouped pools of the ball search (ball.cu): each queued pair of a searched
+// group is certified in the centred coordinates of its ball (result written, counted in
+// GCR_STAT_BALL) or handed on to the band queue bq_* with its original threshold.
+cudaError_t launch_refine_ball(const RefineArgs& a, const BallArgs& b, cudaStream_t st);
 // Split-pool seeds of the serving search (see refine.cu): for each of the b query rows of xq,
 // an admission floor for its search against the gallery G, from the FP32 scores of the distinct
 // rows of the row's previous pool (prev_kp entries of pool_i), of their hop lists (hop_k per
@@ -134,6 +159,53 @@ cudaError_t launch_row_order(const int* pool_i, int n, int kp, int k, int* key, 
 // Copies rows[u] of src (row_bytes each, a multiple of 16) to row u of out, u < min(*count, max_rows).
 cudaError_t launch_gather_rows(const void* src, size_t row_bytes, const int* count, const int* rows,
                                int max_rows, void* out, cudaStream_t st);
+
+// ---- ball.cu: certified search of the pending (row, graph) pairs inside balls shared by
+// groups of them, in coordinates centred on each ball (see ball.cu)
+struct BallArgs {
+  // inputs
+  const float* X;           // n x d FP32 rows (the search's features)
+  const void* xr;           // their rounded operand copy (BF16, or TF32 held as FP32)
+  Elt elt;
+  int n, d, k, kp, kinds, precision;
+  const double* n64;        // ||x||^2 per row
+  const float* enrm;        // rounding statistics per row
+  const float* anrm;
+  const RowScalars* sc;     // maxima over the rows
+  const int* cam;           // camera per row (cross-camera graph), or NULL
+  const int* pool_i;        // [kinds][n][kp] pools of the first search
+  const int* unc_count;     // pending pairs (device count), capacity unc_cap
+  const int* unc_row;
+  const int* unc_kind;
+  const float* unc_dk;      // per pair: an upper bound on its exact k-th squared distance
+  const float* dk_all;      // [kinds][n]: that bound for every (row, graph) of the first search
+  int unc_cap;
+  void* cent;               // scratch: n rounded rows (the centres' operand copies)
+  int* err;                 // set when a union-find link gives up
+  // workspace (carve_ball)
+  int *parent, *pend, *acnt, *active, *gid, *pos_of_row, *root_of_row;
+  float* rad;
+  int *groot, *ga, *gkind, *gsize, *rsize, *goff, *gfill, *afill, *bfill, *gfail, *icnt, *ioff;
+  float *gthr, *gthr_fill;
+  RowScalars* gsc;          // per group: maxima over its positions
+  int4* items;
+  int max_items;
+  int* ball_j;              // listed members, cap_rows
+  int* gmap;                // position -> row
+  int* ggrp;                // position -> group (-1: unused)
+  double* n64y;             // per position: ||y||^2
+  float* hy;                //               ||y||^2 / 2 (the pool scores' bias)
+  float* enrm_y;
+  float* anrm_y;
+  int* gcam;                // camera per position (cross-camera graph)
+  float* Y;                 // centred rows, cap_rows x d
+  void* Yr;                 // their rounded operand copy
+  float* gpool_v;           // [kinds][cap_rows][kp] pools of the grouped search
+  int* gpool_i;
+  int cap_rows;
+};
+size_t carve_ball(Carve& c, int n, int d, int kinds, int kp, Elt elt, int cap_rows, BallArgs* out);
+cudaError_t launch_ball_prepare(const BallArgs& a, cudaStream_t st);
 
 // ---- graph.cu
 struct GraphArgs {

@@ -231,12 +231,15 @@ __device__ __forceinline__ void rescore(const RefineArgs& a, const float4 (&xi)[
 
 // Settles the k-th boundary of the FP32-ranked list L (sorted, r >= kk finite entries) and
 // writes the kk neighbours of (row, kind) with their squared distances; pads to k.
+// frow: the row's index in X (its norm n64[frow]); orow: the output row; idmap (may be NULL):
+// the output index of a candidate (the ball search lists gathered positions), also the key of
+// exact FP64 ties.
 template <int VPL, int P>
 __device__ void finalize(const RefineArgs& a, const float4 (&xi)[VPL], WList<P>& L, int r, int kk,
-                         double eps, int row, int kind, int lane) {
-  int32_t* onbr = a.nbr[kind] + (size_t)row * a.k;
-  float* od2 = a.d2[kind] + (size_t)row * a.k;
-  const double n_i = a.n64[row];
+                         double eps, int frow, int orow, int kind, int lane, const int* idmap = nullptr) {
+  int32_t* onbr = a.nbr[kind] + (size_t)orow * a.k;
+  float* od2 = a.d2[kind] + (size_t)orow * a.k;
+  const double n_i = a.n64[frow];
   int acnt = kk, zcnt = kk;
   int rank[P];
 #pragma unroll
@@ -268,20 +271,27 @@ __device__ void finalize(const RefineArgs& a, const float4 (&xi)[VPL], WList<P>&
           }
         }
       }
-      // rank of each ambiguous entry among the ambiguous ones (larger sig64 first, then index)
+      // rank of each ambiguous entry among the ambiguous ones (larger sig64 first, then the
+      // smaller output index)
+      int key[P];
+#pragma unroll
+      for (int p = 0; p < P; ++p) {
+        const int me = p * 32 + lane;
+        key[p] = (idmap && me >= acnt && me < zcnt) ? idmap[L.id[p]] : L.id[p];
+      }
       for (int e = acnt; e < zcnt; ++e) {
         double os = -CUDART_INF;
         int oi = 0;
 #pragma unroll
         for (int p = 0; p < P; ++p) {
           const double t = __shfl_sync(GCR_FULL, sig64[p], e & 31);
-          const int ti = __shfl_sync(GCR_FULL, L.id[p], e & 31);
+          const int ti = __shfl_sync(GCR_FULL, key[p], e & 31);
           if ((e >> 5) == p) { os = t; oi = ti; }
         }
 #pragma unroll
         for (int p = 0; p < P; ++p) {
           const int me = p * 32 + lane;
-          if (me >= acnt && me < zcnt && me != e && better_d(os, oi, sig64[p], L.id[p])) ++rank[p];
+          if (me >= acnt && me < zcnt && me != e && better_d(os, oi, sig64[p], key[p])) ++rank[p];
         }
       }
       if (lane == 0 && a.stats) {
@@ -299,7 +309,7 @@ __device__ void finalize(const RefineArgs& a, const float4 (&xi)[VPL], WList<P>&
     if (slot >= 0) {
       const int j = L.id[p];
       double dd = n_i + a.n64B[j] - 2.0 * L.val[p];
-      onbr[slot] = j;
+      onbr[slot] = idmap ? idmap[j] : j;
       od2[slot] = (float)(dd > 0.0 ? dd : 0.0);
     }
   }
@@ -387,6 +397,10 @@ __global__ void __launch_bounds__(256) refine_pool_kernel(RefineArgs a) {
   if (lane == 0 && a.stats) atomicAdd(&a.stats[GCR_STAT_RESCORED], (unsigned long long)r);
   wl_sort<P>(L, lane);
   const double sig_k = wl_sig(L, kk - 1);
+  // at least kk candidates have exact sigma >= sig_k - eps: the exact k-th squared distance is at
+  // most n_i - 2 (sig_k - eps) (the local scale the ball search groups rows by)
+  const float dk = __double2float_ru(fmax(0.0, a.n64[row] - 2.0 * (sig_k - eps)) * (1.0 + 1e-9));
+  if (a.dk_all && lane == 0) a.dk_all[(size_t)kind * a.n + row] = dk;
   if (full || fl > -CUDART_INF_F) {
     const bool cert = (sig_k - eps) > ((double)tau + delta - 0.5 * sc.nmin);
     // Saturated pool: the density of the pool's lower half, extrapolated over the band's
@@ -397,7 +411,7 @@ __global__ void __launch_bounds__(256) refine_pool_kernel(RefineArgs a) {
     const float mid = pool_at(KP / 2);
     const double dens = (KP / 2) / fmax((double)mid - (double)tau, 1e-30);
     const double below = fmax(0.0, 2.0 * delta + 0.5 * (sc.nmax - sc.nmin) - ((double)s_k - (double)tau));
-    const bool saturated = full && KP + dens * below > 512.0;
+    const bool saturated = a.skip_saturated && full && KP + dens * below > 512.0;
     if (!cert && lane == 0) {
       if (a.stats) atomicAdd(&a.stats[GCR_STAT_UNCERTIFIED], 1ull);
       if (saturated) {
@@ -407,10 +421,11 @@ __global__ void __launch_bounds__(256) refine_pool_kernel(RefineArgs a) {
         a.unc_row[u] = row;
         a.unc_kind[u] = kind;
         a.unc_thr[u] = __double2float_rd(sig_k - eps + 0.5 * sc.nmin - delta);
+        if (a.unc_dk) a.unc_dk[u] = dk;
       }
     }
   }
-  finalize<VPL, P>(a, xi, L, r, kk, eps, row, kind, lane);
+  finalize<VPL, P>(a, xi, L, r, kk, eps, row, row, kind, lane);
 }
 
 // The kk-th largest of the cnt (<= 512) band scores bv[0..cnt): an MSB-first radix select on
@@ -506,8 +521,97 @@ __global__ void __launch_bounds__(256, 3) refine_band_kernel(RefineArgs a) {
     if (lane == 0 && a.stats) atomicAdd(&a.stats[GCR_STAT_RESCORED], (unsigned long long)total);
     const int r = min(total, 32 * P);
     const int kk = min(a.k, r);
-    finalize<VPL, P>(a, xi, L, r, kk, eps, row, kind, lane);
+    finalize<VPL, P>(a, xi, L, r, kk, eps, row, row, kind, lane);
   }
+}
+
+// One warp per queued pair (i, graph) of the ball search. The pool of the pair's position p in
+// its ball holds the best approximate sigma^ = y_p . y_j - ||y_j||^2 / 2 (y centred on the
+// ball), so it ranks by distance and needs no norm-spread slack. With delta the GEMM bound over
+// the ball plus the rounding of the bias and of the subtraction, the pair is certified when the
+// pool holds every eligible member (not full) or sigma_(k) - eps > tau + delta; every exact
+// neighbour lies in the ball, so the pool's refined top k is then N_i. Otherwise, and for pairs
+// outside the searched groups, the pair goes on to the band queue with its original threshold.
+template <int VPL, int P>
+__global__ void __launch_bounds__(256) refine_ball_kernel(RefineArgs a, BallArgs b) {
+  constexpr int KP = 32 * P;
+  const int lane = threadIdx.x & 31;
+  const int u = blockIdx.x * 8 + (threadIdx.x >> 5);
+  if (u >= min(*a.unc_count, b.unc_cap)) return;
+  const int i = a.unc_row[u], kind = a.unc_kind[u];
+  const int p = b.pos_of_row[i];
+  const int g = p >= 0 ? b.ggrp[p] : -1;
+  auto hand_on = [&]() {
+    if (lane == 0) {
+      const int v = atomicAdd(a.bq_count, 1);
+      a.bq_row[v] = i;
+      a.bq_kind[v] = kind;
+      a.bq_thr[v] = a.unc_thr[u];
+    }
+  };
+  if (g < 0 || b.gfail[g]) { hand_on(); return; }
+  const float* pv = b.gpool_v + ((size_t)kind * b.cap_rows + p) * KP;
+  const int* pi = b.gpool_i + ((size_t)kind * b.cap_rows + p) * KP;
+  WList<P> L;
+  float pval[P];
+  int mvalid = 0;
+#pragma unroll
+  for (int q = 0; q < P; ++q) {
+    pval[q] = pv[q * 32 + lane];
+    L.id[q] = pi[q * 32 + lane];
+    L.sig[q] = -CUDART_INF;
+    L.val[q] = 0.0;
+    mvalid += __popc(__ballot_sync(GCR_FULL, L.id[q] >= 0));
+  }
+  const int kk = min(a.k, mvalid);
+  if (kk < a.k || kk == 0) { hand_on(); return; }  // the ball lacks k eligible members
+  auto pool_at = [&](int e) {
+    float r = 0.f;
+#pragma unroll
+    for (int q = 0; q < P; ++q) {
+      float t = __shfl_sync(GCR_FULL, pval[q], e & 31);
+      if ((e >> 5) == q) r = t;
+    }
+    return r;
+  };
+  const float s_k = pool_at(kk - 1);
+  const bool full = mvalid == KP;
+  const double tau = full ? (double)pool_at(KP - 1) : -CUDART_INF;
+  const RowScalars sc = b.gsc[g];
+  const double bmax = sqrt(sc.nmax) * (1.0 + 1e-12);
+  const double b_i = sqrt(b.n64y[p]);
+  double delta;
+  if (a.precision == GCR_PREC_FP32) {
+    delta = gamma_n((double)a.d, kU32) * b_i * bmax;
+  } else {
+    const double ai = b.anrm_y[p], ei = b.enrm_y[p];
+    delta = ai * sc.emax + ei * bmax + gamma_n((double)a.d + 32.0, kU32rz) * ai * sc.amax;
+  }
+  // the bias ||y_j||^2 / 2 is rounded to FP32, and so is the difference stored in the pool
+  const double amax = a.precision == GCR_PREC_FP32 ? bmax : sc.amax;
+  const double ai_ = a.precision == GCR_PREC_FP32 ? b_i : (double)b.anrm_y[p];
+  delta += 2.0 * kU32 * (ai_ * amax * 1.01 + sc.nmax);
+  delta *= 1.0 + 1e-6;
+  const int vpl = VPL;
+  const double eps = gamma_n((double)(4 * vpl + 6), kU32) * b_i * bmax * (1.0 + 1e-6);
+  const double thr = (double)s_k - 2.0 * delta;
+  int r = 0;
+#pragma unroll
+  for (int q = 0; q < P; ++q) r += __popc(__ballot_sync(GCR_FULL, L.id[q] >= 0 && (double)pval[q] >= thr));
+  RefineArgs c = a;  // the ball's coordinates: centred rows and their norms, indexed by position
+  c.X = b.Y;
+  c.XB = b.Y;
+  c.n64 = b.n64y;
+  c.n64B = b.n64y;
+  float4 xi[VPL];
+  load_row<VPL>(b.Y, a.d, p, lane, xi);
+  rescore<VPL, P>(c, xi, L, r, lane);
+  if (lane == 0 && a.stats) atomicAdd(&a.stats[GCR_STAT_RESCORED], (unsigned long long)r);
+  wl_sort<P>(L, lane);
+  const double sig_k = wl_sig(L, kk - 1);
+  if (full && !(sig_k - eps > tau + delta)) { hand_on(); return; }
+  if (lane == 0 && a.stats) atomicAdd(&a.stats[GCR_STAT_BALL], 1ull);
+  finalize<VPL, P>(c, xi, L, r, kk, eps, p, i, kind, lane, b.gmap);
 }
 
 // Cluster-local processing order. key(i) = the smallest index among i and its first k pool
@@ -720,6 +824,27 @@ cudaError_t launch_band_p(const RefineArgs& a, cudaStream_t st) {
   else if (vpl <= 32) refine_band_kernel<32, P><<<grid, 256, 0, st>>>(a);
   else return cudaErrorInvalidValue;
   return cudaGetLastError();
+}
+
+template <int P>
+cudaError_t launch_ball_vpl(const RefineArgs& a, const BallArgs& b, cudaStream_t st) {
+  dim3 grid((unsigned)((b.unc_cap + 7) / 8));
+  const int vpl = (a.d + 127) / 128;
+  if (vpl <= 1) refine_ball_kernel<1, P><<<grid, 256, 0, st>>>(a, b);
+  else if (vpl <= 2) refine_ball_kernel<2, P><<<grid, 256, 0, st>>>(a, b);
+  else if (vpl <= 4) refine_ball_kernel<4, P><<<grid, 256, 0, st>>>(a, b);
+  else if (vpl <= 8) refine_ball_kernel<8, P><<<grid, 256, 0, st>>>(a, b);
+  else if (vpl <= 16) refine_ball_kernel<16, P><<<grid, 256, 0, st>>>(a, b);
+  else if (vpl <= 32) refine_ball_kernel<32, P><<<grid, 256, 0, st>>>(a, b);
+  else return cudaErrorInvalidValue;
+  return cudaGetLastError();
+}
+
+cudaError_t launch_refine_ball(const RefineArgs& a, const BallArgs& b, cudaStream_t st) {
+  if (a.kp == 32) return launch_ball_vpl<1>(a, b, st);
+  if (a.kp == 64) return launch_ball_vpl<2>(a, b, st);
+  if (a.kp == 128) return launch_ball_vpl<4>(a, b, st);
+  return cudaErrorInvalidValue;
 }
 
 cudaError_t launch_refine_band(const RefineArgs& a, cudaStream_t st) {

@@ -41,7 +41,7 @@ constexpr int STAGE_BYTES = A_BYTES + B_BYTES;
 constexpr uint32_t TMEM_COLS = 512;
 constexpr unsigned long long kTimeoutNs = 2000000000ull;
 
-enum Mode { POOL = 0, BAND = 1, DIST = 2, GRAM = 3, MUL = 4 };
+enum Mode { POOL = 0, BAND = 1, DIST = 2, GRAM = 3, MUL = 4, GPOOL = 5 };
 
 // ------------------------------------------------------------------------ PTX wrappers
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
@@ -182,8 +182,10 @@ struct UmmaArgs {
   const float* band_thr;
   int bcap;
   int* band_cnt;
-  float* band_v;
+  float* band_v;       // may be NULL (indices only)
   int* band_i;
+  const int* band_off; // NULL: row u writes at u * bcap; else at band_off[u]
+  const int* band_lim; // NULL: bcap entries per row; else band_lim[u]
   // DIST
   const float* nrm_q;
   const float* nrm_g;
@@ -203,6 +205,13 @@ struct UmmaArgs {
   int dist_tiles;  // all tiles; CTA b takes tiles b, b + grid, ... in column-major tile order,
                    // so the CTAs at work share the (small) query blocks and stream each gallery
                    // column tile once
+  // GPOOL: pools of the rows of a gathered matrix against column ranges of the same matrix.
+  // Work item w = {first row, rows (<= BM), first column, columns}; CTA b takes the items
+  // b, b + grid, ... of the *n_items; a pool entry holds s - col_bias[j]; column j == row is
+  // skipped when self_excl; cam (may be NULL) is indexed by gathered position.
+  const int4* items;
+  const int* n_items;
+  const float* col_bias;
 };
 
 struct __align__(8) Bars {
@@ -213,6 +222,29 @@ struct __align__(8) Bars {
   uint64_t drain;
   uint32_t tmem_base;
   int abort_flag;
+};
+
+// GPOOL walk over a CTA's work items and their column tiles: every role keeps its own cursor
+// and advances it once per tile, so all roles see the same sequence.
+struct ItemCursor {
+  int item, ct, nt;
+  int4 w;
+  __device__ void load(const UmmaArgs& a, int nitems) {
+    w = item < nitems ? a.items[item] : make_int4(0, 0, 0, 0);
+    nt = (w.w + BN - 1) / BN;
+  }
+  __device__ void start(const UmmaArgs& a, int nitems) {
+    item = blockIdx.x;
+    ct = 0;
+    load(a, nitems);
+  }
+  __device__ void advance(const UmmaArgs& a, int nitems) {
+    if (++ct >= nt) {
+      item += gridDim.x;
+      ct = 0;
+      load(a, nitems);
+    }
+  }
 };
 
 // Work list of a CTA: tiles (row block of A, column tile of B) in order.
@@ -255,7 +287,13 @@ umma_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
   const int mul_b0 = MODE == MUL ? max(0, a.mul_rowcam[blockIdx.y]) * a.n : 0;
 
   Tiles<MODE> tl;
-  if (MODE == POOL) tl.count = max(0, min(a.tps, (a.n + BN - 1) / BN - (int)blockIdx.y * a.tps));
+  int nitems = 0;
+  if (MODE == GPOOL) {
+    nitems = *a.n_items;
+    if ((int)blockIdx.x >= nitems) return;  // nothing to do: leave before any barrier or TMEM use
+    tl.count = 0;
+    for (int it = blockIdx.x; it < nitems; it += gridDim.x) tl.count += (a.items[it].w + BN - 1) / BN;
+  } else if (MODE == POOL) tl.count = max(0, min(a.tps, (a.n + BN - 1) / BN - (int)blockIdx.y * a.tps));
   else if (MODE == BAND) {
     const int U = min(*a.count, a.cap);
     const int tiles = (U + BM - 1) / BM;
@@ -298,8 +336,12 @@ umma_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
     // ------------------------------------------------------------ TMA producer
     if (lane == 0) {
       int it = 0;
+      ItemCursor cur;
+      if (MODE == GPOOL) cur.start(a, nitems);
       for (int t = 0; t < tl.count && !*abort_flag; ++t) {
-        const int r0 = tl.row0(a, t), c0 = tl.col0(a, t);
+        const int r0 = MODE == GPOOL ? cur.w.x : tl.row0(a, t);
+        const int c0 = MODE == GPOOL ? cur.w.z + cur.ct * BN : tl.col0(a, t);
+        if (MODE == GPOOL) cur.advance(a, nitems);
         for (int kb = 0; kb < kb_count; ++kb, ++it) {
           const int s = it % NST;
           const uint32_t round = it / NST;
@@ -389,12 +431,28 @@ umma_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
       pool_init(me, valid, (valid && a.seed) ? a.seed[my_row] : -CUDART_INF_F);
       if (CROSS && valid) my_cam = a.cam[my_row];
     }
+    ItemCursor cur;
+    if (MODE == GPOOL) cur.start(a, nitems);
+    bool g_valid = false;        // GPOOL: this thread's row belongs to the current item
+    int g_row0 = 0, g_cend = 0;  // GPOOL: first row of the item, end of its columns
     for (int t = 0; t < tl.count; ++t) {
       const int buf = t & 1;
       const uint32_t use = t >> 1;
       if (!mbar_wait(&bars.tfull[buf], use & 1, abort_flag)) break;
       tc_fence_after();
-      const int r0 = tl.row0(a, t), c0 = tl.col0(a, t);
+      const int r0 = MODE == GPOOL ? cur.w.x : tl.row0(a, t);
+      const int c0 = MODE == GPOOL ? cur.w.z + cur.ct * BN : tl.col0(a, t);
+      const bool g_first = MODE == GPOOL && cur.ct == 0;
+      const bool g_last = MODE == GPOOL && cur.ct == cur.nt - 1;
+      if (g_first) {
+        g_row0 = cur.w.x;
+        g_cend = cur.w.z + cur.w.w;
+        g_valid = r < cur.w.y;
+        my_row = g_row0 + r;
+        pool_init(me, g_valid);
+        if (CROSS && g_valid) my_cam = a.cam[my_row];
+      }
+      if (MODE == GPOOL) cur.advance(a, nitems);
       int u = -1;
       if (MODE == BAND) {
         u = r0 + r;
@@ -416,13 +474,35 @@ umma_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
         my_row = r0 + r;
         my_nq = a.gram_lambda * (float)a.gram_nf[blockIdx.z];  // lambda n_s, added on the diagonal
       }
-      const int ncol = min(BN, a.n - c0);
+      const int cend = MODE == GPOOL ? g_cend : a.n;  // end of this tile's valid columns
+      const int ncol = min(BN, cend - c0);
       for (int ch = 0; ch < BN / 32; ++ch) {
         if (ch * 32 >= ncol) break;
         float v[32];
         tmem_ld32(tmem + lane_addr + buf * BN + ch * 32, v);
         const int cb = c0 + ch * 32;
-        if (MODE == POOL) {
+        if (MODE == GPOOL) {
+          if (kind == 0 || CROSS) {
+            int ccam = 0;
+            if (CROSS && kind == 1) ccam = (cb + lane < cend) ? a.cam[cb + lane] : -1;
+            const float hb = (cb + lane < cend) ? a.col_bias[cb + lane] : 0.f;
+            float2* myq = qs + qrow * kQCap;
+#pragma unroll
+            for (int g = 0; g < 8; ++g) {
+              pool_make_room<KP>(4, lane, me, g_row0 + quad * 32, kind * BM + quad * 32, qs, pv, pi);
+#pragma unroll
+              for (int c = 0; c < 4; ++c) {
+                const int cc = g * 4 + c;
+                const int j = cb + cc;
+                const int cj = __shfl_sync(GCR_FULL, ccam, cc);
+                const float hj = __shfl_sync(GCR_FULL, hb, cc);
+                bool ok = j < cend && !(a.self_excl && j == my_row);
+                if (CROSS && kind == 1) ok = ok && cj != my_cam;
+                pool_push(me, v[cc] - hj, j, ok, myq, sw);
+              }
+            }
+          }
+        } else if (MODE == POOL) {
           if (kind == 0 || CROSS) {
             int ccam = 0;
             if (CROSS && kind == 1) ccam = (cb + lane < a.n) ? a.cam[cb + lane] : -1;
@@ -456,9 +536,10 @@ umma_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
               if (u < 0 || j >= a.n || (a.self_excl && j == my_row) || v[cc] < my_thr) continue;
               if (my_kind == 1 && cj == my_cam) continue;
               const int pos = atomicAdd(&a.band_cnt[u], 1);
-              if (pos < a.bcap) {
-                a.band_v[(size_t)u * a.bcap + pos] = v[cc];
-                a.band_i[(size_t)u * a.bcap + pos] = j;
+              if (pos < (a.band_lim ? a.band_lim[u] : a.bcap)) {
+                const size_t at = (a.band_off ? (size_t)a.band_off[u] : (size_t)u * a.bcap) + pos;
+                if (a.band_v) a.band_v[at] = v[cc];
+                a.band_i[at] = j;
               }
             }
           }
@@ -493,6 +574,8 @@ umma_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
       tc_fence_before();
       __syncwarp();
       if (lane == 0) mbar_arrive(&bars.tempty[buf]);
+      if (g_last && (kind == 0 || CROSS))
+        pool_flush<KP>(lane, g_valid, me, g_row0 + quad * 32, kind * BM + quad * 32, qs, pv, pi);
     }
     if (MODE == POOL && (kind == 0 || CROSS) && !*abort_flag)
       pool_flush<KP>(lane, my_row < a.a_rows, me, blockIdx.x * BM + quad * 32, kind * BM + quad * 32, qs, pv, pi);
@@ -561,7 +644,7 @@ cudaError_t make_map(CUtensorMap* m, const void* base, Elt elt, int rows, int d,
 
 size_t smem_bytes(int mode) {
   size_t s = 1024 + (size_t)NST * STAGE_BYTES;
-  if (mode == POOL) s += 2 * BM * kQCap * (sizeof(float) + sizeof(int));
+  if (mode == POOL || mode == GPOOL) s += 2 * BM * kQCap * (sizeof(float) + sizeof(int));
   return s;
 }
 
@@ -622,10 +705,40 @@ cudaError_t launch_umma_pool(const void* Ab, int na, const void* Bb, int nb, int
   return cudaErrorInvalidValue;
 }
 
+cudaError_t launch_umma_gpool(const void* Y, int rows, int d, Elt elt, const int* gcam, bool cross, int self_excl,
+                              int kp, const int4* items, const int* n_items, int max_items, const float* col_bias,
+                              float* pool_v, int* pool_i, cudaStream_t st) {
+  if (rows < 1 || max_items < 1) return cudaSuccess;
+  CUtensorMap ta, tb;
+  cudaError_t e = make_map(&ta, Y, elt, rows, d, BM);
+  if (e != cudaSuccess) return e;
+  e = make_map(&tb, Y, elt, rows, d, BN);
+  if (e != cudaSuccess) return e;
+  UmmaArgs a{};
+  a.mode = GPOOL;
+  a.tf32 = elt == Elt::TF32;
+  a.n = rows;
+  a.d = d;
+  a.a_rows = rows;
+  a.self_excl = self_excl;
+  a.cam = gcam;
+  a.pool_v = pool_v;
+  a.pool_i = pool_i;
+  a.items = items;
+  a.n_items = n_items;
+  a.col_bias = col_bias;
+  // persistent: one CTA per SM (the POOL shared memory allows one), items strided over the grid
+  dim3 grid((unsigned)std::max(1, std::min(max_items, 152)));
+  if (kp == 32) return cross ? launch<GPOOL, 32, true>(ta, tb, a, grid, st) : launch<GPOOL, 32, false>(ta, tb, a, grid, st);
+  if (kp == 64) return cross ? launch<GPOOL, 64, true>(ta, tb, a, grid, st) : launch<GPOOL, 64, false>(ta, tb, a, grid, st);
+  if (kp == 128) return cross ? launch<GPOOL, 128, true>(ta, tb, a, grid, st) : launch<GPOOL, 128, false>(ta, tb, a, grid, st);
+  return cudaErrorInvalidValue;
+}
+
 cudaError_t launch_umma_band(const void* Xb, int n, int d, Elt elt, const int* cam, int self_excl,
                              const void* Ab, const int* count, int cap, const int* band_row,
                              const int* band_kind, const float* band_thr, int bcap, int* band_cnt, float* band_v,
-                             int* band_i, cudaStream_t st) {
+                             int* band_i, cudaStream_t st, const int* band_off, const int* band_lim) {
   CUtensorMap ta, tb;
   cudaError_t e = make_map(&ta, Ab, elt, cap, d, BM);
   if (e != cudaSuccess) return e;
@@ -648,6 +761,8 @@ cudaError_t launch_umma_band(const void* Xb, int n, int d, Elt elt, const int* c
   a.band_cnt = band_cnt;
   a.band_v = band_v;
   a.band_i = band_i;
+  a.band_off = band_off;
+  a.band_lim = band_lim;
   // the row tiles (known only on the device) are strided over grid.y so that the grid covers
   // the GPU about twice even when the columns give few tiles
   const int gx = (n + BN - 1) / BN;

@@ -260,3 +260,18 @@ def test_mean_profiles_validation_on_host(lib):
     assert lib.gcrv_mean_profiles(p, 1000, 128, p, 50, p, p, 100, None) == 2
     assert lib.gcrv_mean_profiles(None, 1000, 128, p, 50, p, p, 1 << 30, None) == 1
     assert lib.gcrv_mean_profiles(p, 1000, 128, p, 0, p, p, 1 << 30, None) == 1
+
+
+def test_python_constants_match_the_header():
+    """The binding's counter and stage tables follow the enums of include/gcr.h."""
+    import re
+    from paper_2306_08792_gb300 import _lib
+    with open(os.path.join(ROOT, "include", "gcr.h")) as f:
+        h = f.read()
+    val = {m.group(1): int(m.group(2)) for m in re.finditer(r"\b(GCR_[A-Z0-9_]+)\s*=\s*(\d+)", h)}
+    assert val["GCR_STATS_LEN"] == _lib.GCR_STATS_LEN == len(_lib.STAT_NAMES)
+    for i, name in enumerate(_lib.STAT_NAMES):
+        assert val["GCR_STAT_" + name.upper()] == i
+    assert val["GCR_STAGES"] == _lib.GCR_STAGES
+    for i, name in enumerate(_lib.STAGE_NAMES):
+        assert val["GCR_STAGE_" + name.upper()] == i

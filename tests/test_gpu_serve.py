@@ -96,7 +96,7 @@ def test_serve_seeded_splits_match_oracle(gcr, precision):
     ws = torch.empty(need, dtype=torch.uint8, device="cuda")
     idx = torch.empty(Q.shape[0], K, dtype=torch.int32, device="cuda")
     dist = torch.empty(Q.shape[0], K, dtype=torch.float32, device="cuda")
-    stats = torch.zeros(8, dtype=torch.int64, device="cuda")
+    stats = torch.zeros(_lib.GCR_STATS_LEN, dtype=torch.int64, device="cuda")
     G.serve(Xq, idx, dist, ws, stats)
     torch.cuda.synchronize()
     assert int(stats[5]) == 0  # GCR_STAT_CLAMPED
