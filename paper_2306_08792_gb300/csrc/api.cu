@@ -269,10 +269,12 @@ int knn_impl(const float* X, int64_t n64_, int32_t d, const int32_t* cam, const 
     if (bf) {
       StageScope sc_(GCR_STAGE_BALL, st, 20);
       BallArgs b = w.ball;
-      b.X = X; b.xr = w.xr; b.elt = elt; b.n = n; b.d = d; b.k = p->k; b.kp = r.kp; b.kinds = kinds;
-      b.precision = p->precision; b.n64 = w.n64; b.enrm = w.enrm; b.anrm = w.anrm; b.sc = w.sc; b.cam = camp;
-      b.pool_i = w.pool_i; b.unc_count = w.unc_count; b.unc_row = w.unc_row; b.unc_kind = w.unc_kind;
-      b.unc_dk = w.unc_dk; b.dk_all = w.dk_all; b.unc_cap = kinds * n; b.cent = w.band_a; b.err = w.err;
+      b.two = 0; b.XA = b.XB = X; b.xrA = b.xrB = w.xr; b.elt = elt; b.na = n; b.nb = n; b.d = d; b.k = p->k;
+      b.kp = r.kp; b.kinds = kinds; b.precision = p->precision; b.n64A = b.n64B = w.n64;
+      b.enrmA = b.enrmB = w.enrm; b.anrmA = b.anrmB = w.anrm; b.scB = w.sc; b.cam = camp;
+      b.pool_i = w.pool_i; b.pool_v = w.pool_v; b.unc_count = w.unc_count; b.unc_row = w.unc_row;
+      b.unc_kind = w.unc_kind; b.unc_dk = w.unc_dk; b.dk_all = w.dk_all; b.unc_cap = kinds * n;
+      b.cent = w.band_a; b.cent_rows = w.band_rows; b.err = w.err;
       GCR_CUDA_TRY(launch_ball_prepare(b, st));
       GCR_CUDA_TRY(launch_umma_gpool(b.Yr, b.cap_rows, d, elt, b.gcam, kinds == 2, 1, r.kp, b.items, b.ioff + n,
                                      b.max_items, b.hy, b.gpool_v, b.gpool_i, st));
@@ -578,6 +580,12 @@ struct ServeWs {
   int* unc_row;
   int* unc_kind;
   float* unc_thr;
+  float* unc_dk;
+  int* bq_count;       // pairs the ball search hands on to the band rescan
+  int* bq_row;
+  int* bq_kind;
+  float* bq_thr;
+  int* err;
   int* band_cnt;
   float* band_v;
   int* band_i;
@@ -625,6 +633,12 @@ size_t carve_serve(Carve& c, int64_t b, int32_t d, const gcr_params* p, const Re
   t.unc_row = c.take<int>(nb);
   t.unc_kind = c.take<int>(nb);
   t.unc_thr = c.take<float>(nb);
+  t.unc_dk = c.take<float>(nb);
+  t.bq_count = c.take<int>(4);
+  t.bq_row = c.take<int>(nb);
+  t.bq_kind = c.take<int>(nb);
+  t.bq_thr = c.take<float>(nb);
+  t.err = c.take<int>(4);
   t.band_cnt = c.take<int>(nb);
   t.band_v = c.take<float>(nb * kBandCap);
   t.band_i = c.take<int>(nb * kBandCap);
@@ -644,11 +658,14 @@ struct GallerySide {
   const void* Gr;
   const double* n64;
   const RowScalars* sc;
+  const float* enrm;  // rounding statistics of the rows (tensor-core modes)
+  const float* anrm;
 };
 
 GallerySide gallery_layer(const GalleryView& g, int layer, int ng, int d, size_t es) {
   return GallerySide{g.layers + (size_t)layer * ng * d, g.xr ? g.xr + (size_t)layer * ng * d * es : nullptr,
-                     g.n64 + (size_t)layer * ng, g.sc + layer};
+                     g.n64 + (size_t)layer * ng, g.sc + layer,
+                     g.enrm ? g.enrm + (size_t)layer * ng : nullptr, g.anrm ? g.anrm + (size_t)layer * ng : nullptr};
 }
 
 // Where the seeds of a search's split pools come from: the previous search's merged pool
@@ -662,9 +679,11 @@ struct SeedSource {
 };
 
 // Certified k nearest gallery rows for the b query rows xq: pool, merge, refine, band.
+// ball (may be NULL; tensor-core modes): workspace of the ball search of the rows the pools
+// cannot certify (without it, pools saturated with near-ties keep the 2 delta bound).
 int serve_knn(const float* xq, int b, int d, const gcr_params* p, int k, int kp, const GallerySide& gs, int ng,
               const ServeWs& w, unsigned long long* stats, int32_t* nbr, float* d2, cudaStream_t st,
-              const SeedSource& seed_src = SeedSource()) {
+              const SeedSource& seed_src = SeedSource(), const BallArgs* ball = nullptr) {
   const bool bf = tensor_mode(p);
   const Elt elt = elt_of(p);
   const float* G = gs.G;
@@ -716,22 +735,43 @@ int serve_knn(const float* xq, int b, int d, const gcr_params* p, int k, int kp,
   ra.stats = stats;
   ra.band_cnt = w.band_cnt; ra.band_v = w.band_v; ra.band_i = w.band_i; ra.bcap = kBandCap; ra.band_rows = b;
   ra.floor = seeded ? w.seed : nullptr;
-  ra.skip_saturated = 1;  // no ball search against a gallery: saturated pools keep the 2 delta bound
+  const bool use_ball = bf && ball != nullptr && !seeded;
+  ra.skip_saturated = use_ball ? 0 : 1;
+  ra.unc_dk = w.unc_dk;
   {
     StageScope sc_(GCR_STAGE_REFINE, st);
     GCR_CUDA_TRY(launch_refine_pool(ra, st));
   }
+  RefineArgs rb = ra;
+  if (use_ball) {
+    StageScope sc_(GCR_STAGE_BALL, st, 20);
+    BallArgs bl = *ball;
+    bl.two = 1; bl.XA = xq; bl.XB = G; bl.xrA = w.qr; bl.xrB = gs.Gr; bl.elt = elt; bl.na = b; bl.nb = ng;
+    bl.d = d; bl.k = k; bl.kp = kp; bl.kinds = 1; bl.precision = p->precision; bl.n64A = w.n64; bl.n64B = gs.n64;
+    bl.enrmA = w.enrm; bl.anrmA = w.anrm; bl.enrmB = gs.enrm; bl.anrmB = gs.anrm; bl.scB = gs.sc; bl.cam = nullptr;
+    bl.pool_i = w.pool_i; bl.pool_v = w.pool_v; bl.unc_count = w.unc_count; bl.unc_row = w.unc_row;
+    bl.unc_kind = w.unc_kind; bl.unc_dk = w.unc_dk; bl.dk_all = nullptr; bl.unc_cap = b; bl.cent = w.band_a;
+    bl.cent_rows = b; bl.err = w.err;
+    GCR_CUDA_TRY(cudaMemsetAsync(w.err, 0, sizeof(int) * 4, st));
+    GCR_CUDA_TRY(launch_ball_prepare(bl, st));
+    GCR_CUDA_TRY(launch_umma_gpool(bl.Yr, bl.cap_rows, d, elt, nullptr, false, 0, kp, bl.items, bl.ioff + b + ng,
+                                   bl.max_items, bl.hy, bl.gpool_v, bl.gpool_i, st));
+    GCR_CUDA_TRY(cudaMemsetAsync(w.bq_count, 0, sizeof(int) * 4, st));
+    ra.bq_count = w.bq_count; ra.bq_row = w.bq_row; ra.bq_kind = w.bq_kind; ra.bq_thr = w.bq_thr;
+    GCR_CUDA_TRY(launch_refine_ball(ra, bl, st));
+    rb.unc_count = w.bq_count; rb.unc_row = w.bq_row; rb.unc_kind = w.bq_kind; rb.unc_thr = w.bq_thr;
+  }
   {
     StageScope sc_(GCR_STAGE_BAND, st, bf ? 3 : 2);
     if (bf) {
-      GCR_CUDA_TRY(launch_gather_rows(w.qr, (size_t)d * elt_bytes(elt), w.unc_count, w.unc_row, b, w.band_a, st));
-      GCR_CUDA_TRY(launch_umma_band(gs.Gr, ng, d, elt, nullptr, 0, w.band_a, w.unc_count, b, w.unc_row, w.unc_kind,
-                                    w.unc_thr, kBandCap, w.band_cnt, w.band_v, w.band_i, st));
+      GCR_CUDA_TRY(launch_gather_rows(w.qr, (size_t)d * elt_bytes(elt), rb.unc_count, rb.unc_row, b, w.band_a, st));
+      GCR_CUDA_TRY(launch_umma_band(gs.Gr, ng, d, elt, nullptr, 0, w.band_a, rb.unc_count, b, rb.unc_row,
+                                    rb.unc_kind, rb.unc_thr, kBandCap, w.band_cnt, w.band_v, w.band_i, st));
     } else {
-      GCR_CUDA_TRY(launch_sgemm_band(xq, G, ng, d, nullptr, 0, w.unc_count, b, w.unc_row, w.unc_kind, w.unc_thr,
+      GCR_CUDA_TRY(launch_sgemm_band(xq, G, ng, d, nullptr, 0, rb.unc_count, b, rb.unc_row, rb.unc_kind, rb.unc_thr,
                                      kBandCap, w.band_cnt, w.band_v, w.band_i, st));
     }
-    GCR_CUDA_TRY(launch_refine_band(ra, st));
+    GCR_CUDA_TRY(launch_refine_band(rb, st));
   }
   return GCR_OK;
 }
@@ -744,6 +784,7 @@ struct TopkRerankWs {
   float* genrm;
   float* ganrm;
   RowScalars* scg;
+  BallArgs ball;       // ball search of the queries the pools cannot certify (tensor-core modes)
 };
 
 size_t carve_topk_rerank(Carve& c, int64_t nq, int64_t ng, int32_t d, const gcr_params* p, TopkRerankWs* w) {
@@ -759,6 +800,10 @@ size_t carve_topk_rerank(Carve& c, int64_t nq, int64_t ng, int32_t d, const gcr_
   t.genrm = c.take<float>(ng);
   t.ganrm = c.take<float>(ng);
   t.scg = c.take<RowScalars>(1);
+  std::memset(&t.ball, 0, sizeof(t.ball));
+  // gathered positions: each group's queries and its ball of gallery rows (balls may overlap)
+  if (bf) carve_ball(c, (int)(nq + ng), d, 1, r.kp, elt_of(p), (int)std::min<int64_t>(nq + 2 * ng, INT32_MAX / 2),
+                     &t.ball, (int)ng);
   if (w) *w = t;
   return c.off;
 }
@@ -772,9 +817,9 @@ int topk_rerank_impl(const float* Xq, int64_t nq, const float* Xg, int64_t ng, i
                                   w.scg, st));
   }
   GCR_CUDA_TRY(cudaMemsetAsync(w.sw.stats, 0, sizeof(unsigned long long) * GCR_STATS_LEN, st));
-  const GallerySide gs{Xg, w.gr, w.n64g, w.scg};
+  const GallerySide gs{Xg, w.gr, w.n64g, w.scg, w.genrm, w.ganrm};
   return serve_knn(Xq, (int)nq, d, p, p->topk_out, serve_kp_final(p), gs, (int)ng, w.sw, w.sw.stats, idx_out,
-                   dist_out, st);
+                   dist_out, st, SeedSource(), bf ? &w.ball : nullptr);
 }
 
 // The whole re-ranking on device buffers (gcr_pipeline); hd (may be NULL) delivers the

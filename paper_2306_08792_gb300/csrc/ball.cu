@@ -65,16 +65,27 @@ __device__ __forceinline__ bool uf_unite(int* parent, int a, int b) {
   return false;
 }
 
+// Node ids: the A rows (the rows searched) are nodes 0 .. na-1; in a search against a gallery
+// (two = 1) the B rows (the gallery) are nodes na .. na+nb-1, otherwise B is A.
+__device__ __forceinline__ int node_count(const BallArgs& a) { return a.two ? a.na + a.nb : a.na; }
+__device__ __forceinline__ const float* node_row(const BallArgs& a, int v) {
+  return (a.two && v >= a.na) ? a.XB + (size_t)(v - a.na) * a.d : a.XA + (size_t)v * a.d;
+}
+
 __global__ void ball_init_kernel(BallArgs a) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= a.n) return;
-  a.parent[i] = i;
-  a.pend[i] = 0;
-  a.acnt[i] = 0;
-  a.rad[i] = 0.f;
-  a.active[i] = 0;
-  a.pos_of_row[i] = -1;
-  a.root_of_row[i] = -1;
+  const int v = blockIdx.x * blockDim.x + threadIdx.x;
+  if (v < node_count(a)) {
+    a.parent[v] = v;
+    a.acnt[v] = 0;
+    a.rad[v] = 0.f;
+    a.active[v] = 0;
+  }
+  if (v < a.na) {
+    a.pend[v] = 0;
+    a.pos_of_row[v] = -1;
+    a.root_of_row[v] = -1;
+  }
+  if (a.two && v < a.nb) a.gscale[v] = CUDART_INF_F;
 }
 
 __global__ void ball_mark_kernel(BallArgs a) {
@@ -83,20 +94,48 @@ __global__ void ball_mark_kernel(BallArgs a) {
   atomicOr(a.pend + a.unc_row[u], 1 << a.unc_kind[u]);
 }
 
-// One warp per pending pair: link i with each j of its first k pool entries whose k-th distance
-// bound is within kScaleRatio of i's (same graph).
+// Approximate squared distance of pending row i to its pool entry s (against a gallery).
+__device__ __forceinline__ float pool_d2(const BallArgs& a, int i, int kind, int s, int j) {
+  const float v = a.pool_v[((size_t)kind * a.na + i) * a.kp + s];
+  return fmaxf(0.f, (float)(a.n64A[i] + a.n64B[j]) - 2.f * v);
+}
+
+// Against a gallery, a gallery row has no kNN list of its own: its local scale is the smallest
+// approximate squared distance at which a pending row lists it among its first k candidates.
+__global__ void ball_scale_kernel(BallArgs a) {
+  const int lane = threadIdx.x & 31;
+  const int u = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  if (u >= min(*a.unc_count, a.unc_cap)) return;
+  const int i = a.unc_row[u], kind = a.unc_kind[u];
+  const int* pi = a.pool_i + ((size_t)kind * a.na + i) * a.kp;
+  for (int s = lane; s < a.k; s += 32) {
+    const int j = pi[s];
+    if (j < 0) continue;
+    atomicMin(reinterpret_cast<int*>(a.gscale) + j, __float_as_int(pool_d2(a, i, kind, s, j)));
+  }
+}
+
+// One warp per pending pair: link i with each j of its first k pool entries of a similar local
+// scale (within kScaleRatio): among the A rows, the two k-th distance bounds; against a gallery,
+// i's distance to j and j's scale.
 __global__ void ball_link_kernel(BallArgs a) {
   const int lane = threadIdx.x & 31;
   const int u = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
   if (u >= min(*a.unc_count, a.unc_cap)) return;
   const int i = a.unc_row[u], kind = a.unc_kind[u];
-  const int* pi = a.pool_i + ((size_t)kind * a.n + i) * a.kp;
-  const float di = a.dk_all[(size_t)kind * a.n + i];
+  const int* pi = a.pool_i + ((size_t)kind * a.na + i) * a.kp;
+  const float di = a.two ? 0.f : a.dk_all[(size_t)kind * a.na + i];
   for (int s = lane; s < a.k; s += 32) {
     const int j = pi[s];
-    if (j < 0 || j == i) continue;
-    const float dj = a.dk_all[(size_t)kind * a.n + j];
-    if (di <= kScaleRatio * dj && dj <= kScaleRatio * di && !uf_unite(a.parent, i, j)) atomicOr(a.err, 1);
+    if (j < 0 || (!a.two && j == i)) continue;
+    bool link;
+    if (a.two) {
+      link = pool_d2(a, i, kind, s, j) <= kScaleRatio * a.gscale[j];
+    } else {
+      const float dj = a.dk_all[(size_t)kind * a.na + j];
+      link = di <= kScaleRatio * dj && dj <= kScaleRatio * di;
+    }
+    if (link && !uf_unite(a.parent, i, a.two ? a.na + j : j)) atomicOr(a.err, 1);
   }
 }
 
@@ -110,8 +149,8 @@ __global__ void ball_root_kernel(BallArgs a) {
   int root = 0;
   if (lane == 0) root = uf_find(a.parent, i);
   root = __shfl_sync(GCR_FULL, root, 0);
-  const float4* xi = reinterpret_cast<const float4*>(a.X + (size_t)i * a.d);
-  const float4* xc = reinterpret_cast<const float4*>(a.X + (size_t)root * a.d);
+  const float4* xi = reinterpret_cast<const float4*>(a.XA + (size_t)i * a.d);
+  const float4* xc = reinterpret_cast<const float4*>(node_row(a, root));
   float ss = 0.f;
   for (int v = lane; v < (a.d >> 2); v += 32) {
     const float4 p = xi[v], q = xc[v];
@@ -132,39 +171,61 @@ __global__ void ball_root_kernel(BallArgs a) {
 
 // Group table from the scanned active flags; the sweep threshold of each centre:
 // ||x_j - c||^2 <= R^2 implies s_cj >= (||x_j||^2 + ||c||^2 - R^2) / 2 >= (nmin + ||c||^2 - R^2) / 2,
-// and the approximate score is within delta_c (the GEMM bound of row c) of s_cj.
+// and the approximate score is within delta_c (the GEMM bound of row c against the B rows) of s_cj.
 __global__ void ball_group_kernel(BallArgs a) {
   const int r = blockIdx.x * blockDim.x + threadIdx.x;
-  if (r >= a.n || !a.active[r]) return;
+  if (r >= node_count(a) || !a.active[r]) return;
   const int g = a.gid[r];
   a.groot[g] = r;
   a.ga[g] = a.acnt[r];
   a.gkind[g] = 0;
-  const RowScalars sc = *a.sc;
+  const bool on_b = a.two && r >= a.na;
+  const int rr = on_b ? r - a.na : r;
+  const double n_c = on_b ? a.n64B[rr] : a.n64A[rr];
+  const double an = on_b ? a.anrmB[rr] : a.anrmA[rr];
+  const double en = on_b ? a.enrmB[rr] : a.enrmA[rr];
+  const RowScalars sc = *a.scB;
   const double bmax = sqrt(sc.nmax) * (1.0 + 1e-12);
   const double R = (double)a.rad[r];
   double delta;
   if (a.precision == GCR_PREC_FP32) {
-    delta = (a.d * kU32b / (1.0 - a.d * kU32b)) * sqrt(a.n64[r]) * bmax;
+    delta = (a.d * kU32b / (1.0 - a.d * kU32b)) * sqrt(n_c) * bmax;
   } else {
     const double gacc = (a.d + 32.0) * 2.0 * kU32b / (1.0 - (a.d + 32.0) * 2.0 * kU32b);
-    delta = (double)a.anrm[r] * sc.emax + (double)a.enrm[r] * bmax + gacc * (double)a.anrm[r] * sc.amax;
+    delta = an * sc.emax + en * bmax + gacc * an * sc.amax;
   }
   delta *= 1.0 + 1e-6;
-  const double thr = 0.5 * (sc.nmin + a.n64[r] - R * R) - delta;
+  const double thr = 0.5 * (sc.nmin + n_c - R * R) - delta;
   a.gthr[g] = nextafterf(__double2float_rd(thr), -CUDART_INF_F);
 }
 
-// Groups searched: ball no larger than half of the rows and holding at least the group's
-// pending rows (the rest is a numerical impossibility, handled as a failure).
+// The centres' rounded operand rows (from the A or the B copy), 16 bytes per thread.
+__global__ void ball_centres_kernel(BallArgs a) {
+  const int G = a.gid[node_count(a)];
+  const size_t w16 = (size_t)a.d * (a.elt == Elt::TF32 ? 4 : 2) / 16;
+  for (size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x; t < (size_t)G * w16;
+       t += (size_t)gridDim.x * blockDim.x) {
+    const size_t g = t / w16, c = t % w16;
+    const int r = a.groot[g];
+    const bool on_b = a.two && r >= a.na;
+    const uint4* src = static_cast<const uint4*>(on_b ? a.xrB : a.xrA) + (size_t)(on_b ? r - a.na : r) * w16;
+    static_cast<uint4*>(a.cent)[g * w16 + c] = src[c];
+  }
+}
+
+// Groups searched: a ball no larger than half of the B rows (among the A rows it must also hold
+// the group's pending rows; anything else is a numerical impossibility, handled as a failure).
+// Segment size: the pending rows plus the ball against a gallery, the ball alone otherwise.
 __global__ void ball_route_kernel(BallArgs a) {
   const int g = blockIdx.x * blockDim.x + threadIdx.x;
-  if (g >= a.n) return;
-  const int G = a.gid[a.n];
+  const int nn = node_count(a);
+  if (g >= nn) return;
+  const int G = a.gid[nn];
   int sz = 0;
   if (g < G) {
     const int c = a.gsize[g];
-    sz = (c <= a.n / 2 && c >= a.ga[g]) ? c : 0;
+    if (a.two) sz = c <= a.nb / 2 ? a.ga[g] + c : 0;
+    else sz = (c <= a.na / 2 && c >= a.ga[g]) ? c : 0;
   }
   a.rsize[g] = sz;
   a.gfill[g] = 0;
@@ -173,15 +234,18 @@ __global__ void ball_route_kernel(BallArgs a) {
   a.gfail[g] = 0;
 }
 
-// Capacity cut (segments in scan order) and the fill-pass thresholds (+inf: not searched).
+// Capacity cut (segments in scan order), fill-pass thresholds (+inf: not searched), and where
+// the fill pass lists each ball: after the pending rows against a gallery, else the segment.
 __global__ void ball_cut_kernel(BallArgs a) {
   const int g = blockIdx.x * blockDim.x + threadIdx.x;
-  const int G = a.gid[a.n];
+  const int G = a.gid[node_count(a)];
   if (g >= G) return;
   const bool fits = a.rsize[g] > 0 && a.goff[g] + a.rsize[g] <= a.cap_rows;
   if (!fits) a.rsize[g] = 0;
   a.gthr_fill[g] = fits ? a.gthr[g] : CUDART_INF_F;
   if (!fits) a.gfail[g] = 1;
+  a.boff[g] = a.goff[g] + (a.two ? a.ga[g] : 0);
+  a.blim[g] = fits ? (a.two ? a.rsize[g] - a.ga[g] : a.rsize[g]) : 0;
 }
 
 __device__ __forceinline__ int group_of(const int* goff, int G, int e) {
@@ -194,18 +258,24 @@ __device__ __forceinline__ int group_of(const int* goff, int G, int e) {
   return lo;
 }
 
-// Places each listed member in its group's segment: the group's pending rows first.
+// Places each listed member in its group's segment. Among the A rows the list holds the
+// group's pending rows too, which go first; against a gallery the list already sits after them.
 __global__ void ball_place_kernel(BallArgs a) {
   const int e = blockIdx.x * blockDim.x + threadIdx.x;
-  const int G = a.gid[a.n];
+  const int G = a.gid[node_count(a)];
   if (G == 0 || e >= min(a.goff[G], a.cap_rows)) return;
   const int g = group_of(a.goff, G, e);
-  if (a.rsize[g] == 0 || e >= a.goff[g] + a.rsize[g]) return;
-  if (a.gfill[g] != a.rsize[g]) {  // the fill pass listed a different count than the count pass
+  if (a.rsize[g] == 0 || e < a.boff[g] || e >= a.boff[g] + a.blim[g]) return;
+  if (a.gfill[g] != a.blim[g]) {  // the fill pass listed a different count than the count pass
     a.gfail[g] = 1;
     return;
   }
   const int j = a.ball_j[e];
+  if (a.two) {
+    a.gmap[e] = j;
+    a.ggrp[e] = g;
+    return;
+  }
   const int root = a.groot[g];
   const bool is_a = a.pend[j] != 0 && a.root_of_row[j] == root;
   int p;
@@ -223,11 +293,28 @@ __global__ void ball_place_kernel(BallArgs a) {
   a.ggrp[p] = g;
 }
 
+// Against a gallery: the pending rows of each searched group at the head of its segment.
+__global__ void ball_place_rows_kernel(BallArgs a) {
+  const int u = blockIdx.x * blockDim.x + threadIdx.x;
+  if (u >= min(*a.unc_count, a.unc_cap)) return;
+  const int i = a.unc_row[u], kind = a.unc_kind[u];
+  if ((a.pend[i] & ((1 << kind) - 1)) != 0) return;  // once per row
+  const int g = a.gid[a.root_of_row[i]];
+  if (a.rsize[g] == 0) return;
+  const int s = atomicAdd(a.afill + g, 1);
+  if (s >= a.ga[g]) { a.gfail[g] = 1; return; }
+  const int p = a.goff[g] + s;
+  a.pos_of_row[i] = p;
+  a.gmap[p] = i;
+  a.ggrp[p] = g;
+}
+
 // Every pending row of a group must have been placed; work items of the searched groups.
 __global__ void ball_items_count_kernel(BallArgs a) {
   const int g = blockIdx.x * blockDim.x + threadIdx.x;
-  if (g >= a.n) return;
-  const int G = a.gid[a.n];
+  const int nn = node_count(a);
+  if (g >= nn) return;
+  const int G = a.gid[nn];
   int c = 0;
   if (g < G && a.rsize[g] > 0) {
     if (a.afill[g] != a.ga[g]) a.gfail[g] = 1;
@@ -244,29 +331,30 @@ __global__ void ball_items_count_kernel(BallArgs a) {
 
 __global__ void ball_items_kernel(BallArgs a) {
   const int g = blockIdx.x * blockDim.x + threadIdx.x;
-  const int G = a.gid[a.n];
+  const int G = a.gid[node_count(a)];
   if (g >= G || a.icnt[g] == 0) return;
   const int o = a.ioff[g];
   for (int b = 0; b < a.icnt[g]; ++b)
-    a.items[o + b] = make_int4(a.goff[g] + 128 * b, min(128, a.ga[g] - 128 * b), a.goff[g], a.rsize[g]);
+    a.items[o + b] = make_int4(a.goff[g] + 128 * b, min(128, a.ga[g] - 128 * b), a.boff[g], a.blim[g]);
 }
 
 __device__ __forceinline__ unsigned long long dbits_b(double v) { return (unsigned long long)__double_as_longlong(v); }
 
-// One warp per position of a searched group: y = fl(x_j - c_g), its rounded operand copy, the
+// One warp per position of a searched group: y = fl(x - c_g), its rounded operand copy, the
 // squared norm (float-float, combined in FP64), the bias ||y||^2 / 2 of the pool scores, the
 // rounding-error norms (rounded up as in the row statistics) and the group maxima.
 template <Elt E>
 __global__ void __launch_bounds__(256) ball_center_kernel(BallArgs a) {
   const int lane = threadIdx.x & 31;
   const int p = blockIdx.x * 8 + (threadIdx.x >> 5);
-  const int G = a.gid[a.n];
+  const int G = a.gid[node_count(a)];
   if (G == 0 || p >= min(a.goff[G], a.cap_rows)) return;
   const int g = a.ggrp[p];
   if (g < 0 || a.gfail[g] || a.rsize[g] == 0) return;
   const int j = a.gmap[p];
-  const float4* xj = reinterpret_cast<const float4*>(a.X + (size_t)j * a.d);
-  const float4* xc = reinterpret_cast<const float4*>(a.X + (size_t)a.groot[g] * a.d);
+  const bool on_b = a.two && p >= a.goff[g] + a.ga[g];
+  const float4* xj = reinterpret_cast<const float4*>(on_b ? a.XB + (size_t)j * a.d : a.XA + (size_t)j * a.d);
+  const float4* xc = reinterpret_cast<const float4*>(node_row(a, a.groot[g]));
   float4* y = reinterpret_cast<float4*>(a.Y + (size_t)p * a.d);
   FF acc;
   float ee = 0.f, aa = 0.f;
@@ -301,7 +389,7 @@ __global__ void __launch_bounds__(256) ball_center_kernel(BallArgs a) {
   a.hy[p] = (float)(0.5 * ss);
   a.enrm_y[p] = en;
   a.anrm_y[p] = an;
-  if (a.cam) a.gcam[p] = a.cam[j];
+  if (a.gcam) a.gcam[p] = a.cam[j];
   RowScalars* sc = a.gsc + g;
   atomicMin(reinterpret_cast<unsigned long long*>(&sc->nmin), dbits_b(ss));
   atomicMax(reinterpret_cast<unsigned long long*>(&sc->nmax), dbits_b(ss));
@@ -311,7 +399,8 @@ __global__ void __launch_bounds__(256) ball_center_kernel(BallArgs a) {
 
 }  // namespace
 
-size_t carve_ball(Carve& c, int n, int d, int kinds, int kp, Elt elt, int cap_rows, BallArgs* out) {
+size_t carve_ball(Carve& c, int n, int d, int kinds, int kp, Elt elt, int cap_rows, BallArgs* out, int nb) {
+  // n: nodes (the A rows, plus the nb gallery rows of a search against a gallery)
   BallArgs t{};
   t.parent = c.take<int>(n);
   t.pend = c.take<int>(n);
@@ -329,6 +418,9 @@ size_t carve_ball(Carve& c, int n, int d, int kinds, int kp, Elt elt, int cap_ro
   t.gsize = c.take<int>(n + 1);
   t.rsize = c.take<int>(n + 1);
   t.goff = c.take<int>(n + 1);
+  t.boff = c.take<int>(n);
+  t.blim = c.take<int>(n);
+  t.gscale = c.take<float>(nb > 0 ? nb : 1);
   t.gfill = c.take<int>(n);
   t.afill = c.take<int>(n);
   t.bfill = c.take<int>(n);
@@ -357,7 +449,7 @@ size_t carve_ball(Carve& c, int n, int d, int kinds, int kp, Elt elt, int cap_ro
     GCR_BALL_TAKE(parent); GCR_BALL_TAKE(pend); GCR_BALL_TAKE(acnt); GCR_BALL_TAKE(rad); GCR_BALL_TAKE(active);
     GCR_BALL_TAKE(gid); GCR_BALL_TAKE(pos_of_row); GCR_BALL_TAKE(root_of_row); GCR_BALL_TAKE(groot);
     GCR_BALL_TAKE(ga); GCR_BALL_TAKE(gkind); GCR_BALL_TAKE(gthr); GCR_BALL_TAKE(gthr_fill); GCR_BALL_TAKE(gsize);
-    GCR_BALL_TAKE(rsize); GCR_BALL_TAKE(goff); GCR_BALL_TAKE(gfill); GCR_BALL_TAKE(afill); GCR_BALL_TAKE(bfill);
+    GCR_BALL_TAKE(rsize); GCR_BALL_TAKE(goff); GCR_BALL_TAKE(boff); GCR_BALL_TAKE(blim); GCR_BALL_TAKE(gscale); GCR_BALL_TAKE(gfill); GCR_BALL_TAKE(afill); GCR_BALL_TAKE(bfill);
     GCR_BALL_TAKE(gfail); GCR_BALL_TAKE(icnt); GCR_BALL_TAKE(ioff); GCR_BALL_TAKE(gsc); GCR_BALL_TAKE(max_items);
     GCR_BALL_TAKE(items); GCR_BALL_TAKE(ball_j); GCR_BALL_TAKE(gmap); GCR_BALL_TAKE(ggrp); GCR_BALL_TAKE(n64y);
     GCR_BALL_TAKE(hy); GCR_BALL_TAKE(enrm_y); GCR_BALL_TAKE(anrm_y); GCR_BALL_TAKE(gcam); GCR_BALL_TAKE(Y);
@@ -370,40 +462,43 @@ size_t carve_ball(Carve& c, int n, int d, int kinds, int kp, Elt elt, int cap_ro
 // Steps 1-5 (see the top of this file). The caller then runs the grouped GEMM and the
 // refinement of its pools.
 cudaError_t launch_ball_prepare(const BallArgs& a, cudaStream_t st) {
-  const int n = a.n;
-  if (n < 1) return cudaSuccess;
-  const int nb = (n + 255) / 256;
+  const int nn = a.two ? a.na + a.nb : a.na;
+  if (a.na < 1 || a.unc_cap < 1) return cudaSuccess;
+  const int nb = (nn + 255) / 256;
   const int wb = (a.unc_cap + 7) / 8;
   ball_init_kernel<<<nb, 256, 0, st>>>(a);
   ball_mark_kernel<<<(a.unc_cap + 255) / 256, 256, 0, st>>>(a);
+  if (a.two) ball_scale_kernel<<<wb, 256, 0, st>>>(a);
   ball_link_kernel<<<wb, 256, 0, st>>>(a);
   ball_root_kernel<<<wb, 256, 0, st>>>(a);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  e = launch_scan(a.active, a.gid, n, st);  // group ids; gid[n] = number of groups
+  e = launch_scan(a.active, a.gid, nn, st);  // group ids; gid[nn] = number of groups
   if (e != cudaSuccess) return e;
   ball_group_kernel<<<nb, 256, 0, st>>>(a);
-  // sweep pass 1: ball sizes
-  e = launch_gather_rows(a.xr, (size_t)a.d * elt_bytes(a.elt), a.gid + n, a.groot, n, a.cent, st);
+  ball_centres_kernel<<<152 * 4, 256, 0, st>>>(a);
+  // sweep pass 1: ball sizes (the centre rows: at most cent_rows groups, one per pending row)
+  e = cudaMemsetAsync(a.gsize, 0, sizeof(int) * (nn + 1), st);
   if (e != cudaSuccess) return e;
-  e = cudaMemsetAsync(a.gsize, 0, sizeof(int) * (n + 1), st);
-  if (e != cudaSuccess) return e;
-  e = launch_umma_band(a.xr, n, a.d, a.elt, nullptr, 0, a.cent, a.gid + n, n, a.groot, a.gkind, a.gthr, 0, a.gsize,
-                       nullptr, a.ball_j, st);
+  const int B_rows = a.two ? a.nb : a.na;
+  const void* xrB = a.two ? a.xrB : a.xrA;
+  e = launch_umma_band(xrB, B_rows, a.d, a.elt, nullptr, 0, a.cent, a.gid + nn, a.cent_rows, a.groot, a.gkind,
+                       a.gthr, 0, a.gsize, nullptr, a.ball_j, st);
   if (e != cudaSuccess) return e;
   ball_route_kernel<<<nb, 256, 0, st>>>(a);
-  e = launch_scan(a.rsize, a.goff, n, st);
+  e = launch_scan(a.rsize, a.goff, nn, st);
   if (e != cudaSuccess) return e;
   ball_cut_kernel<<<nb, 256, 0, st>>>(a);
   // sweep pass 2: members of the searched balls at their offsets
-  e = launch_umma_band(a.xr, n, a.d, a.elt, nullptr, 0, a.cent, a.gid + n, n, a.groot, a.gkind, a.gthr_fill, 0,
-                       a.gfill, nullptr, a.ball_j, st, a.goff, a.rsize);
+  e = launch_umma_band(xrB, B_rows, a.d, a.elt, nullptr, 0, a.cent, a.gid + nn, a.cent_rows, a.groot, a.gkind,
+                       a.gthr_fill, 0, a.gfill, nullptr, a.ball_j, st, a.boff, a.blim);
   if (e != cudaSuccess) return e;
   e = cudaMemsetAsync(a.ggrp, 0xff, sizeof(int) * a.cap_rows, st);
   if (e != cudaSuccess) return e;
   ball_place_kernel<<<(a.cap_rows + 255) / 256, 256, 0, st>>>(a);
+  if (a.two) ball_place_rows_kernel<<<(a.unc_cap + 255) / 256, 256, 0, st>>>(a);
   ball_items_count_kernel<<<nb, 256, 0, st>>>(a);
-  e = launch_scan(a.icnt, a.ioff, n, st);
+  e = launch_scan(a.icnt, a.ioff, nn, st);
   if (e != cudaSuccess) return e;
   ball_items_kernel<<<nb, 256, 0, st>>>(a);
   const unsigned cb = (unsigned)((a.cap_rows + 7) / 8);

@@ -163,35 +163,45 @@ cudaError_t launch_gather_rows(const void* src, size_t row_bytes, const int* cou
 // ---- ball.cu: certified search of the pending (row, graph) pairs inside balls shared by
 // groups of them, in coordinates centred on each ball (see ball.cu)
 struct BallArgs {
-  // inputs
-  const float* X;           // n x d FP32 rows (the search's features)
-  const void* xr;           // their rounded operand copy (BF16, or TF32 held as FP32)
+  // inputs. The A rows are the rows searched; the B rows the candidates: the A rows themselves
+  // (two = 0, an offline graph) or a gallery (two = 1, a search against it)
+  int two;
+  const float* XA;          // na x d FP32 rows
+  const float* XB;          // nb x d (two = 1)
+  const void* xrA;          // rounded operand copies (BF16, or TF32 held as FP32)
+  const void* xrB;
   Elt elt;
-  int n, d, k, kp, kinds, precision;
-  const double* n64;        // ||x||^2 per row
-  const float* enrm;        // rounding statistics per row
-  const float* anrm;
-  const RowScalars* sc;     // maxima over the rows
-  const int* cam;           // camera per row (cross-camera graph), or NULL
-  const int* pool_i;        // [kinds][n][kp] pools of the first search
+  int na, nb, d, k, kp, kinds, precision;
+  const double* n64A;       // ||x||^2 per row
+  const double* n64B;
+  const float* enrmA;       // rounding statistics per row
+  const float* anrmA;
+  const float* enrmB;
+  const float* anrmB;
+  const RowScalars* scB;    // maxima over the B rows
+  const int* cam;           // camera per row (cross-camera graph, two = 0), or NULL
+  const int* pool_i;        // [kinds][na][kp] pools of the first search (indices of B rows)
+  const float* pool_v;      //                 and their approximate scores
   const int* unc_count;     // pending pairs (device count), capacity unc_cap
   const int* unc_row;
   const int* unc_kind;
   const float* unc_dk;      // per pair: an upper bound on its exact k-th squared distance
-  const float* dk_all;      // [kinds][n]: that bound for every (row, graph) of the first search
+  const float* dk_all;      // [kinds][na]: that bound for every (row, graph) (two = 0)
   int unc_cap;
-  void* cent;               // scratch: n rounded rows (the centres' operand copies)
+  void* cent;               // scratch: cent_rows rounded rows (the centres' operand copies)
+  int cent_rows;            // >= the number of groups (at most one per pending row)
   int* err;                 // set when a union-find link gives up
   // workspace (carve_ball)
   int *parent, *pend, *acnt, *active, *gid, *pos_of_row, *root_of_row;
   float* rad;
-  int *groot, *ga, *gkind, *gsize, *rsize, *goff, *gfill, *afill, *bfill, *gfail, *icnt, *ioff;
+  float* gscale;            // per B row (two = 1): its local scale
+  int *groot, *ga, *gkind, *gsize, *rsize, *goff, *boff, *blim, *gfill, *afill, *bfill, *gfail, *icnt, *ioff;
   float *gthr, *gthr_fill;
   RowScalars* gsc;          // per group: maxima over its positions
   int4* items;
   int max_items;
   int* ball_j;              // listed members, cap_rows
-  int* gmap;                // position -> row
+  int* gmap;                // position -> row (of A, or of B for the ball members when two = 1)
   int* ggrp;                // position -> group (-1: unused)
   double* n64y;             // per position: ||y||^2
   float* hy;                //               ||y||^2 / 2 (the pool scores' bias)
@@ -204,7 +214,8 @@ struct BallArgs {
   int* gpool_i;
   int cap_rows;
 };
-size_t carve_ball(Carve& c, int n, int d, int kinds, int kp, Elt elt, int cap_rows, BallArgs* out);
+// n: nodes (the A rows, plus the nb B rows when two = 1); cap_rows: gathered positions.
+size_t carve_ball(Carve& c, int n, int d, int kinds, int kp, Elt elt, int cap_rows, BallArgs* out, int nb = 0);
 cudaError_t launch_ball_prepare(const BallArgs& a, cudaStream_t st);
 
 // ---- graph.cu
