@@ -51,8 +51,13 @@ def _args():
     ap.add_argument("--no-video", action="store_true", help="skip the GCRV video workload")
     ap.add_argument("--no-local", action="store_true", help="skip the DSFP (Algorithm 1) comparison")
     ap.add_argument("--no-quality", action="store_true", help="skip the retrieval-quality measurements")
-    ap.add_argument("--serving-requests", type=int, default=800)
+    ap.add_argument("--serving-requests", type=int, default=10000,
+                    help="requests of the serving run of the headline precision (the others serve 1,000)")
     ap.add_argument("--pool", type=int, default=0, help="candidate pool per row (0: library default)")
+    ap.add_argument("--only", choices=["zipf"], default=None,
+                    help="run one workload alone and print its object (profiling runs)")
+    ap.add_argument("--zipf-gallery", type=int, default=200000,
+                    help="gallery rows of the zipf workload (a smaller case for --only zipf profiling runs)")
     return ap.parse_args()
 
 
@@ -299,10 +304,33 @@ def sampled_error(torch, pl, w, nsample=8):
     return err
 
 
+def capture_staged(gcr, torch, X, cam, p, nq, rows, queries):
+    """An untimed layer-by-layer run of the same path (gcr_build_graph, gcr_propagate,
+    gcr_rerank), keeping on the host what the oracle comparison of the CPU-baseline leg needs:
+    each layer's input features X_{t-1} and kNN lists, the propagated rows of the sample, X_T
+    and the ranking of the sampled queries. No oracle here."""
+    Xt = gcr.gcr_normalize(X)
+    layers = []
+    for t in range(p.T):
+        G = gcr.gcr_build_graph(Xt, p, cam)
+        Xn = gcr.gcr_propagate(G, Xt)
+        torch.cuda.synchronize()
+        layers.append({"X": Xt.cpu().numpy(), "nbr": G.nbr.cpu().numpy(),
+                       "nbr_cr": G.nbr_cr.cpu().numpy() if G.nbr_cr is not None else None,
+                       "X_next_rows": Xn.cpu().numpy()[rows], "stats": G.stats_dict()})
+        del G
+        Xt = Xn
+    idx, dist = gcr.gcr_rerank(Xt[:nq].contiguous(), Xt[nq:].contiguous(), p)
+    torch.cuda.synchronize()
+    return {"layers": layers, "XT": Xt.cpu().numpy(), "idx": idx.cpu().numpy()[queries],
+            "dist": dist.cpu().numpy()[queries], "rows": rows, "queries": queries, "p": p, "nq": nq}
+
+
 def serving_bench(gcr, torch, precision, n_requests):
     """Serving workload: 500,000 x 256 resident gallery (25,000 clusters), k = 20, T = 2, top-100;
     Poisson arrivals at 200 requests/s with log-uniform batch sizes in 1..512. Returns latency
     percentiles and throughput of the continuous-batching loop (real time, then saturation)."""
+    import numpy as np
     import workloads
     from paper_2306_08792_gb300.serving import Gallery, Server, make_requests
     w = workloads.serving(n_requests=n_requests)
@@ -328,11 +356,25 @@ def serving_bench(gcr, torch, precision, n_requests):
         per_batch[str(b)] = round(statistics.median(ts), 3)
     srv = Server(G, n_slots=4, max_batch=512)
     srv.warmup()
-    rt = srv.run(make_requests(w, n_requests))
+    reqs = make_requests(w, n_requests)
+    rt = srv.run(reqs)
     sat = srv.run(make_requests(w, n_requests, realtime=False), realtime=False)
+    # served rows kept for the oracle comparison of the CPU-baseline leg: 64 query rows drawn
+    # from the real-time run's requests, with the gallery's stored layers and degrees
+    rng = np.random.default_rng(11)
+    picks = [(int(r), int(rng.integers(reqs[r].queries.shape[0]))) for r in rng.choice(len(reqs), 64)]
+    T, ng, d = p.T, w.gallery.shape[0], w.gallery.shape[1]
+    L = (T + 1) * ng * d * 4
+    off = (L + 255) // 256 * 256
+    staged = {"Q": np.stack([reqs[r].queries[i] for r, i in picks]),
+              "idx": np.stack([reqs[r].idx[i] for r, i in picks]),
+              "dist": np.stack([reqs[r].dist[i] for r, i in picks]),
+              "layers": G.state[:L].view(torch.float32).reshape(T + 1, ng, d).cpu().numpy(),
+              "degs": G.state[off:off + T * ng * 4].view(torch.float32).reshape(T, ng).cpu().numpy(),
+              "k": w.k, "gamma": p.gamma, "T": T, "K": p.topk_out}
     del srv, G
     torch.cuda.empty_cache()
-    return {"precision": precision, "gallery_build_s": build_s,
+    return {"precision": precision, "gallery_build_s": build_s, "_staged": staged,
             "offered_requests_per_s": 200.0, "requests": n_requests,
             "p50_ms": rt["p50_ms"], "p99_ms": rt["p99_ms"], "queries_per_s": rt["queries_per_s"],
             "saturation_queries_per_s": sat["queries_per_s"], "saturation_p99_ms": sat["p99_ms"],
@@ -340,7 +382,7 @@ def serving_bench(gcr, torch, precision, n_requests):
             "launches": rt["launches"]}
 
 
-def zipf_bench(gcr, torch, precision, steps, warmup):
+def zipf_bench(gcr, torch, precision, steps, warmup, staged=True, n_gallery=200000):
     """Large-scale workload: 1,000 queries + 200,000 gallery, d = 512, 10,000 Zipf(1.1)-sized
     clusters, k = 30, T = 3, top-100 re-ranking (the certified top-K search; the full ranking of
     200,000 rows per query is outside the segmented sort). Step time, stage times and the HBM
@@ -348,7 +390,7 @@ def zipf_bench(gcr, torch, precision, steps, warmup):
     import workloads
     from paper_2306_08792_gb300 import _lib
     import ctypes
-    w = workloads.zipf()
+    w = workloads.zipf(n_gallery=n_gallery)
     p = gcr.default_params(k=w.k, T=w.T, precision=precision, topk_out=100)
     X = torch.from_numpy(w.X).cuda()
     pl = gcr.Pipeline(w.n, w.n_query, w.d, p)
@@ -382,10 +424,19 @@ def zipf_bench(gcr, torch, precision, steps, warmup):
     peaks, psrc = _peaks()
     gbs = bytes_layer / (prop_ms / 1e3) / 1e9
     ms = statistics.mean(per)
-    del pl, G, X0, X
+    del pl, G, X0
+    import numpy as np
+    rng = np.random.default_rng(3)
+    if staged:
+        staged = capture_staged(gcr, torch, X, None, p, w.n_query,
+                                np.sort(rng.choice(w.n, w.n // 20, replace=False)),
+                                np.sort(rng.choice(w.n_query, 64, replace=False)))
+    del X
     torch.cuda.empty_cache()
-    return {"workload": "zipf: 1,000 queries + 200,000 gallery, d=512, 10,000 Zipf(1.1) clusters, k=30, T=3, "
-                        "top-100 re-ranking",
+    return {"_staged": staged, "_cfg": dict(k=w.k, gamma=w.gamma, cam=None, cross=False, alpha=1.0, topk=100,
+                                            sample="5% of the rows (10,050) per layer, 64 queries"),
+            "workload": f"zipf: 1,000 queries + {w.n - w.n_query:,} gallery, d=512, 10,000 Zipf(1.1) clusters, k=30, "
+                        "T=3, top-100 re-ranking",
             "precision": precision, "steps": steps, "warmup": warmup, "ms_per_step": ms,
             "queries_per_s": w.n_query / (ms / 1e3), "stages_ms": stages,
             "propagate_roofline": {"bound": "hbm", "achieved": gbs, "peak": peaks["hbm_gbs"], "unit": "GB/s",
@@ -431,9 +482,18 @@ def video_bench(gcr, torch, precision, steps, warmup):
         rr.append(ev[1].elapsed_time(ev[2]))
     F, d = frames.shape
     ms = statistics.mean(prof) + statistics.mean(rr)
-    del pl, frames
+    import numpy as np
+    W = gcr.gcrv_profiles(frames, off, cam, ncam, w.lam)
+    rng = np.random.default_rng(4)
+    staged = capture_staged(gcr, torch, W, cam, p, w.n_query, np.sort(rng.choice(C, 2000, replace=False)),
+                            np.sort(rng.choice(w.n_query, 32, replace=False)))
+    staged["W"] = W.cpu().numpy()
+    del pl, frames, W
     torch.cuda.empty_cache()
-    return {"workload": f"video: {w.n_query:,} query + {C - w.n_query:,} gallery tracklets, {F:,} frames of "
+    return {"_staged": staged, "_cfg": dict(k=w.k, gamma=w.gamma, cam=w.trk_cam, cross=True, alpha=0.7, topk=0,
+                                            sample="2,000 of 13,290 tracklets per layer, 32 queries, "
+                                                   "Eq. 17 residual of 3 tracklets per camera", video=w),
+            "workload": f"video: {w.n_query:,} query + {C - w.n_query:,} gallery tracklets, {F:,} frames of "
                         f"d={d}, 6 cameras, lambda={w.lam}; GCR k={w.k}, T={w.T}, cross-camera, full ranking",
             "precision": precision, "steps": steps, "warmup": warmup, "ms_per_step": ms,
             "queries_per_s": w.n_query / (ms / 1e3), "profiles_ms": statistics.mean(prof),
@@ -593,6 +653,116 @@ def quality_bench(gcr, torch):
             "wall_s": time.perf_counter() - t0}
 
 
+# ------------------------------------------------------------------ error against the oracle
+# These run in the CPU-baseline leg (the FP64 oracle on the host cores), on the staged outputs
+# the GPU part kept: the oracle is fed the GPU's own previous-stage outputs.
+TIE = 1e-9   # a kNN mismatch is a certified tie when the FP64 gap to the k-th is below this
+
+
+def _knn_vs_oracle(oracle, np, X64, rows, gpu_nbr, k, cam=None, cross=False):
+    o_idx, o_d2 = oracle.knn_rows(X64, rows, k, cam, cross)
+    mism = ties = 0
+    worst = 0.0
+    for t, r in enumerate(rows):
+        g = set(int(j) for j in gpu_nbr[t] if j >= 0)
+        o = set(int(j) for j in o_idx[t] if j >= 0)
+        if g == o:
+            continue
+        valid = o_d2[t][np.isfinite(o_d2[t])]
+        if len(g) != len(o) or valid.size == 0:
+            mism += 1
+            continue
+        diff = np.array(sorted(g ^ o), dtype=np.int64)
+        dd = X64[diff] - X64[r][None, :]
+        gaps = np.abs(np.sum(dd * dd, axis=1) - valid[-1])
+        worst = max(worst, float(gaps.max()))
+        if np.all(gaps < TIE):
+            ties += 1
+        else:
+            mism += 1
+    return {"mismatched": mism, "certified_ties": ties, "worst_tie_gap": worst}
+
+
+def staged_vs_oracle(oracle, np, st, cfg):
+    """kNN sets and propagation of every layer on the sampled rows, and the final ranking of the
+    sampled queries, against the FP64 oracle run on the GPU's previous-stage outputs."""
+    rows, k = st["rows"], cfg["k"]
+    out = {"sample": cfg["sample"], "tie_gap": TIE, "layers": []}
+    for t, L in enumerate(st["layers"]):
+        X64 = L["X"].astype(np.float64)
+        rec = {"layer": t + 1, "search_stats": L["stats"],
+               "knn": _knn_vs_oracle(oracle, np, X64, rows, L["nbr"][rows], k)}
+        if cfg["cross"]:
+            rec["knn_cross_camera"] = _knn_vs_oracle(oracle, np, X64, rows, L["nbr_cr"][rows], k, cfg["cam"], True)
+        g_o = oracle.build_graph(X64, k, cfg["gamma"], cfg["cam"], cfg["cross"], True, cfg["alpha"],
+                                 nbr=L["nbr"], nbr_cr=L["nbr_cr"])
+        ref = oracle.propagate(X64, g_o["M"][rows])
+        rec["max_propagation_err"] = float(np.max(np.abs(L["X_next_rows"] - ref)))
+        out["layers"].append(rec)
+        del X64, g_o
+    XT = st["XT"].astype(np.float64)
+    nq, q = st["nq"], st["queries"]
+    D = oracle.sq_dist(XT[q], XT[nq:])
+    idx = st["idx"].astype(np.int64)
+    dq = np.take_along_axis(D, idx, axis=1)
+    out["queries"] = int(len(q))
+    out["max_dist_err"] = float(np.max(np.abs(dq - st["dist"])))
+    out["max_order_violation"] = float(np.max(np.maximum(0.0, dq[:, :-1] - dq[:, 1:]))) if dq.shape[1] > 1 else 0.0
+    if cfg["topk"]:
+        bad = 0
+        for t in range(len(q)):
+            o = np.argsort(D[t], kind="stable")[:cfg["topk"]]
+            diff = sorted(set(o) ^ set(idx[t]))
+            if diff and not np.all(np.abs(D[t, diff] - D[t, o[-1]]) < TIE):
+                bad += 1
+        out["topk_mismatched_queries"] = bad
+    return out
+
+
+def profiles_vs_oracle(oracle, np, W, v, per_cam=3):
+    """Eq. 17 profiles: the FP64 normal-equation residual ||(X_s^T X_s + lambda n_s I) w - (mu_c -
+    mu_s)|| / ||mu_c - mu_s|| of sampled tracklets of every camera (cond <= 1 + 1/lambda, so the
+    profile's relative error is at most that factor times the residual)."""
+    rng = np.random.default_rng(0)
+    off, worst = v.trk_off, 0.0
+    for s in np.unique(v.trk_cam):
+        members = np.nonzero(v.trk_cam == s)[0]
+        fr = np.concatenate([np.arange(off[c], off[c + 1]) for c in members])
+        Xs = oracle.l2_normalize(v.frames[fr])
+        mu_s = Xs.mean(axis=0)
+        for c in rng.choice(members, min(per_cam, members.size), replace=False):
+            rhs = oracle.l2_normalize(v.frames[off[c]:off[c + 1]]).mean(axis=0) - mu_s
+            w = W[c].astype(np.float64)
+            res = Xs.T @ (Xs @ w) + v.lam * Xs.shape[0] * w - rhs
+            worst = max(worst, float(np.linalg.norm(res) / np.linalg.norm(rhs)))
+        del Xs
+    return {"max_relative_residual": worst, "tracklets_per_camera": per_cam,
+            "max_relative_profile_err_bound": worst * (1.0 + 1.0 / v.lam)}
+
+
+def serving_vs_oracle(oracle, np, st):
+    """Staged oracle query steps (the serving form of Eq. 6/7 with the gallery frozen) on the
+    GPU's stored gallery layers and degrees, for the sampled served query rows."""
+    xq = oracle.l2_normalize(st["Q"])
+    layers = st["layers"]
+    for t in range(st["T"]):
+        xq = oracle.serve_oracle._query_step(xq, layers[t].astype(np.float64), st["degs"][t].astype(np.float64),
+                                             st["k"], st["gamma"], True)
+    GT = layers[st["T"]].astype(np.float64)
+    D = oracle.sq_dist(xq, GT)
+    idx = st["idx"].astype(np.int64)
+    dq = np.take_along_axis(D, idx, axis=1)
+    bad = 0
+    for t in range(idx.shape[0]):
+        o = np.argsort(D[t], kind="stable")[:st["K"]]
+        diff = sorted(set(o) ^ set(idx[t]))
+        if diff and not np.all(np.abs(D[t, diff] - D[t, o[-1]]) < TIE):
+            bad += 1
+    return {"sample": f"{idx.shape[0]} served query rows from the real-time run", "tie_gap": TIE,
+            "topk_mismatched_queries": bad, "max_dist_err": float(np.max(np.abs(dq - st["dist"]))),
+            "max_order_violation": float(np.max(np.maximum(0.0, dq[:, :-1] - dq[:, 1:])))}
+
+
 def max_over_ranks(value: float, dist, device=None) -> float:
     """Largest value over all ranks (the slowest replica sets the job's time)."""
     if dist is None:
@@ -630,6 +800,14 @@ def run_ours(a):
 
     if not gcr.device_supported(torch.cuda.current_device()):
         raise SystemExit("libgcr needs an sm_103 GPU")
+    if a.only == "zipf":
+        z = zipf_bench(gcr, torch, "tf32" if a.precision == "auto" else a.precision, a.steps, a.warmup, staged=False,
+                       n_gallery=a.zipf_gallery)
+        z.pop("_staged", None)
+        z.pop("_cfg", None)
+        z["max_device_bytes"] = torch.cuda.max_memory_allocated()
+        print(json.dumps(z), flush=True)
+        return
     w = workloads.crosscam()
     Xh = torch.from_numpy(w.X).pin_memory()
     camh = torch.from_numpy(w.cam).pin_memory()
@@ -663,6 +841,12 @@ def run_ours(a):
     R["pipeline"](X, cam, keep_features=True)
     torch.cuda.synchronize()
     err = sampled_error(torch, R["pipeline"], w)
+    rng = np.random.default_rng(2)
+    cross_staged = None
+    if rank == 0 and world == 1 and not a.no_cpu_baseline:
+        cross_staged = capture_staged(gcr, torch, X, cam, R["params"], w.n_query,
+                                      np.sort(rng.choice(w.n, 2000, replace=False)),
+                                      np.sort(rng.choice(w.n_query, 32, replace=False)))
 
     peaks, psrc = _peaks()
     n, d = w.n, w.d
@@ -741,18 +925,40 @@ def run_ours(a):
         serving = {}
         for prec in prec_order:
             try:
-                serving[prec] = serving_bench(gcr, torch, prec, a.serving_requests)
+                nreq = a.serving_requests if prec == primary else min(1000, a.serving_requests)
+                serving[prec] = serving_bench(gcr, torch, prec, nreq)
             except gcr.GcrError as e:
                 serving[prec] = {"error": str(e)}
         line["serving"] = {"workload": "500,000 x 256 resident gallery, 25,000 clusters, k=20, T=2, top-100; "
                                        "Poisson 200 req/s, batch log-uniform 1..512, 4 slots, CUDA graphs",
                            **serving}
     if rank == 0 and world == 1 and not a.no_cpu_baseline:
+        import oracle
         t0 = time.perf_counter()
         est, det = oracle_sample_step(w, **CPU_SAMPLE)
         line["cpu_baseline"] = {"value": w.n_query / est, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
                                 "sample": cpu_sample_description(**CPU_SAMPLE), "wall_s": time.perf_counter() - t0,
                                 "stage_s": det}
+        # error of every result against the oracle, fed the GPU's previous-stage outputs
+        t0 = time.perf_counter()
+        line["vs_oracle"] = staged_vs_oracle(oracle, np, cross_staged, dict(
+            k=w.k, gamma=w.gamma, cam=w.cam, cross=True, alpha=w.alpha, topk=0,
+            sample="2,000 of 19,281 rows per layer (both graphs), 32 queries (full ranking)"))
+        z = line.get("zipf", {})
+        if "_staged" in z:
+            z["vs_oracle"] = staged_vs_oracle(oracle, np, z["_staged"], z["_cfg"])
+        v = line.get("video", {})
+        if "_staged" in v:
+            v["vs_oracle"] = staged_vs_oracle(oracle, np, v["_staged"], v["_cfg"])
+            v["vs_oracle"]["profiles"] = profiles_vs_oracle(oracle, np, v["_staged"]["W"], v["_cfg"]["video"])
+        for prec, sv in line.get("serving", {}).items():
+            if isinstance(sv, dict) and "_staged" in sv:
+                sv["vs_oracle"] = serving_vs_oracle(oracle, np, sv["_staged"])
+        line["vs_oracle"]["wall_s_all_workloads"] = time.perf_counter() - t0
+    for obj in [line.get("zipf", {}), line.get("video", {})] + list(line.get("serving", {}).values()):
+        if isinstance(obj, dict):
+            obj.pop("_staged", None)
+            obj.pop("_cfg", None)
     if rank == 0:
         print(json.dumps(line), flush=True)
     if dist:

@@ -119,6 +119,8 @@ struct BuildWs {
   int* bq_row;
   int* bq_kind;
   float* bq_thr;
+  int* bq_flag;
+  int* bq_pos;
   int* band_cnt;
   float* band_v;
   int* band_i;
@@ -173,6 +175,8 @@ size_t carve_build(Carve& c, int64_t n, int32_t d, const gcr_params* p, const Re
   t.bq_row = c.take<int>((size_t)kinds * nn);
   t.bq_kind = c.take<int>((size_t)kinds * nn);
   t.bq_thr = c.take<float>((size_t)kinds * nn);
+  t.bq_flag = c.take<int>((size_t)kinds * nn);
+  t.bq_pos = c.take<int>((size_t)kinds * nn + 1);
   t.band_cnt = c.take<int>(band_rows);
   t.band_v = c.take<float>((size_t)band_rows * kBandCap);
   t.band_i = c.take<int>((size_t)band_rows * kBandCap);
@@ -278,8 +282,8 @@ int knn_impl(const float* X, int64_t n64_, int32_t d, const int32_t* cam, const 
       GCR_CUDA_TRY(launch_ball_prepare(b, st));
       GCR_CUDA_TRY(launch_umma_gpool(b.Yr, b.cap_rows, d, elt, b.gcam, kinds == 2, 1, r.kp, b.items, b.ioff + n,
                                      b.max_items, b.hy, b.gpool_v, b.gpool_i, st));
-      GCR_CUDA_TRY(cudaMemsetAsync(w.bq_count, 0, sizeof(int) * 4, st));
       ra.bq_count = w.bq_count; ra.bq_row = w.bq_row; ra.bq_kind = w.bq_kind; ra.bq_thr = w.bq_thr;
+      ra.bq_flag = w.bq_flag; ra.bq_pos = w.bq_pos;
       GCR_CUDA_TRY(launch_refine_ball(ra, b, st));
       rb.unc_count = w.bq_count; rb.unc_row = w.bq_row; rb.unc_kind = w.bq_kind; rb.unc_thr = w.bq_thr;
     }
@@ -295,6 +299,14 @@ int knn_impl(const float* X, int64_t n64_, int32_t d, const int32_t* cam, const 
                                      rb.unc_thr, kBandCap, w.band_cnt, w.band_v, w.band_i, st));
     }
     GCR_CUDA_TRY(launch_refine_band(rb, st));
+    // the propagation walks the rows cluster by cluster of the final lists (its gathers then hit
+    // in L2); the refinement above used the candidate pools' order
+    if (g->row_order) {
+      StageScope so_(GCR_STAGE_GRAPH, st, 5);
+      // scratch: the graph build's buffers (free until it runs); w.okey holds the pools' keys
+      GCR_CUDA_TRY(launch_cluster_order(g->nbr, g->nbr_d2, n, d, p->k, w.okey, w.fill, w.long_list, w.op_cnt,
+                                        w.ocnt, w.ooff, w.ofill, g->row_order, w.err, st));
+    }
   }
   return GCR_OK;
 }
@@ -585,6 +597,8 @@ struct ServeWs {
   int* bq_row;
   int* bq_kind;
   float* bq_thr;
+  int* bq_flag;
+  int* bq_pos;
   int* err;
   int* band_cnt;
   float* band_v;
@@ -638,6 +652,8 @@ size_t carve_serve(Carve& c, int64_t b, int32_t d, const gcr_params* p, const Re
   t.bq_row = c.take<int>(nb);
   t.bq_kind = c.take<int>(nb);
   t.bq_thr = c.take<float>(nb);
+  t.bq_flag = c.take<int>(nb);
+  t.bq_pos = c.take<int>(nb + 1);
   t.err = c.take<int>(4);
   t.band_cnt = c.take<int>(nb);
   t.band_v = c.take<float>(nb * kBandCap);
@@ -756,8 +772,8 @@ int serve_knn(const float* xq, int b, int d, const gcr_params* p, int k, int kp,
     GCR_CUDA_TRY(launch_ball_prepare(bl, st));
     GCR_CUDA_TRY(launch_umma_gpool(bl.Yr, bl.cap_rows, d, elt, nullptr, false, 0, kp, bl.items, bl.ioff + b + ng,
                                    bl.max_items, bl.hy, bl.gpool_v, bl.gpool_i, st));
-    GCR_CUDA_TRY(cudaMemsetAsync(w.bq_count, 0, sizeof(int) * 4, st));
     ra.bq_count = w.bq_count; ra.bq_row = w.bq_row; ra.bq_kind = w.bq_kind; ra.bq_thr = w.bq_thr;
+    ra.bq_flag = w.bq_flag; ra.bq_pos = w.bq_pos;
     GCR_CUDA_TRY(launch_refine_ball(ra, bl, st));
     rb.unc_count = w.bq_count; rb.unc_row = w.bq_row; rb.unc_kind = w.bq_kind; rb.unc_thr = w.bq_thr;
   }

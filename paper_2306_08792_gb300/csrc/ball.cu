@@ -21,12 +21,15 @@
 //  3. a threshold sweep of the centres against all rows (the tensor-core kernel's BAND mode,
 //     in two passes: count, then fill at scanned offsets) lists each ball's members, a superset
 //     that allows for the sweep's rounding bound; balls holding more than half of the rows, or
-//     beyond the gathered capacity, are not searched (their pairs go to the threshold rescan);
+//     beyond the gathered capacity, are not searched (their pairs go to the threshold rescan),
+//     nor, unless a pair's band is predicted to overflow, groups of fewer than kMinGroupRows
+//     pending rows or whose ball is not contracted (R^2 > ||c||^2 / 4): the rescan is cheaper;
 //  4. each ball's members are gathered, centred (y = fl(x - c_g)) and rounded to the GEMM's
 //     operand type, the group's pending rows first, with per-position norms and per-group
 //     maxima for the rounding bounds;
 //  5. work items for the grouped pool GEMM: 128 pending rows of a group against its members.
 // The grouped GEMM (umma.cu, GPOOL) and the refinement of its pools (refine.cu) follow.
+#include <algorithm>
 #include <climits>
 
 #include "common.cuh"
@@ -37,6 +40,9 @@ namespace {
 
 constexpr double kU32b = 5.9604644775390625e-08;  // 2^-24
 constexpr float kScaleRatio = 8.f;  // largest ratio of the k-th distance bounds of linked rows
+// A group of fewer pending rows than this, none of them predicted to overflow the band, is left
+// to the threshold rescan: its ball sweep and 128-row GEMM tiles cost more than their rows' sweeps.
+constexpr int kMinGroupRows = 8;
 
 // Union-find over row indices. Every parent pointer goes to a smaller or equal index, so a find
 // ends after at most x steps. Parents are read and written through L2 (ld/st.cg): the atomics
@@ -79,6 +85,8 @@ __global__ void ball_init_kernel(BallArgs a) {
     a.acnt[v] = 0;
     a.rad[v] = 0.f;
     a.active[v] = 0;
+    a.seen[v] = 0;
+    a.rdense[v] = 0;
   }
   if (v < a.na) {
     a.pend[v] = 0;
@@ -89,9 +97,9 @@ __global__ void ball_init_kernel(BallArgs a) {
 }
 
 __global__ void ball_mark_kernel(BallArgs a) {
-  const int u = blockIdx.x * blockDim.x + threadIdx.x;
-  if (u >= min(*a.unc_count, a.unc_cap)) return;
-  atomicOr(a.pend + a.unc_row[u], 1 << a.unc_kind[u]);
+  const int U = min(*a.unc_count, a.unc_cap);
+  for (int u = blockIdx.x * blockDim.x + threadIdx.x; u < U; u += gridDim.x * blockDim.x)
+    atomicOr(a.pend + a.unc_row[u], 1 << a.unc_kind[u]);
 }
 
 // Approximate squared distance of pending row i to its pool entry s (against a gallery).
@@ -104,14 +112,16 @@ __device__ __forceinline__ float pool_d2(const BallArgs& a, int i, int kind, int
 // approximate squared distance at which a pending row lists it among its first k candidates.
 __global__ void ball_scale_kernel(BallArgs a) {
   const int lane = threadIdx.x & 31;
-  const int u = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-  if (u >= min(*a.unc_count, a.unc_cap)) return;
-  const int i = a.unc_row[u], kind = a.unc_kind[u];
-  const int* pi = a.pool_i + ((size_t)kind * a.na + i) * a.kp;
-  for (int s = lane; s < a.k; s += 32) {
-    const int j = pi[s];
-    if (j < 0) continue;
-    atomicMin(reinterpret_cast<int*>(a.gscale) + j, __float_as_int(pool_d2(a, i, kind, s, j)));
+  const int U = min(*a.unc_count, a.unc_cap);
+  const int nw = gridDim.x * (blockDim.x >> 5);
+  for (int u = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); u < U; u += nw) {
+    const int i = a.unc_row[u], kind = a.unc_kind[u];
+    const int* pi = a.pool_i + ((size_t)kind * a.na + i) * a.kp;
+    for (int s = lane; s < a.k; s += 32) {
+      const int j = pi[s];
+      if (j < 0) continue;
+      atomicMin(reinterpret_cast<int*>(a.gscale) + j, __float_as_int(pool_d2(a, i, kind, s, j)));
+    }
   }
 }
 
@@ -120,22 +130,24 @@ __global__ void ball_scale_kernel(BallArgs a) {
 // i's distance to j and j's scale.
 __global__ void ball_link_kernel(BallArgs a) {
   const int lane = threadIdx.x & 31;
-  const int u = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-  if (u >= min(*a.unc_count, a.unc_cap)) return;
-  const int i = a.unc_row[u], kind = a.unc_kind[u];
-  const int* pi = a.pool_i + ((size_t)kind * a.na + i) * a.kp;
-  const float di = a.two ? 0.f : a.dk_all[(size_t)kind * a.na + i];
-  for (int s = lane; s < a.k; s += 32) {
-    const int j = pi[s];
-    if (j < 0 || (!a.two && j == i)) continue;
-    bool link;
-    if (a.two) {
-      link = pool_d2(a, i, kind, s, j) <= kScaleRatio * a.gscale[j];
-    } else {
-      const float dj = a.dk_all[(size_t)kind * a.na + j];
-      link = di <= kScaleRatio * dj && dj <= kScaleRatio * di;
+  const int U = min(*a.unc_count, a.unc_cap);
+  const int nw = gridDim.x * (blockDim.x >> 5);
+  for (int u = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); u < U; u += nw) {
+    const int i = a.unc_row[u], kind = a.unc_kind[u];
+    const int* pi = a.pool_i + ((size_t)kind * a.na + i) * a.kp;
+    const float di = a.two ? 0.f : a.dk_all[(size_t)kind * a.na + i];
+    for (int s = lane; s < a.k; s += 32) {
+      const int j = pi[s];
+      if (j < 0 || (!a.two && j == i)) continue;
+      bool link;
+      if (a.two) {
+        link = pool_d2(a, i, kind, s, j) <= kScaleRatio * a.gscale[j];
+      } else {
+        const float dj = a.dk_all[(size_t)kind * a.na + j];
+        link = di <= kScaleRatio * dj && dj <= kScaleRatio * di;
+      }
+      if (link && !uf_unite(a.parent, i, a.two ? a.na + j : j)) atomicOr(a.err, 1);
     }
-    if (link && !uf_unite(a.parent, i, a.two ? a.na + j : j)) atomicOr(a.err, 1);
   }
 }
 
@@ -143,30 +155,48 @@ __global__ void ball_link_kernel(BallArgs a) {
 // (||x_i - c|| + sqrt(Dbar), rounded up) and, once per row, the group's pending-row count.
 __global__ void ball_root_kernel(BallArgs a) {
   const int lane = threadIdx.x & 31;
-  const int u = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-  if (u >= min(*a.unc_count, a.unc_cap)) return;
-  const int i = a.unc_row[u], kind = a.unc_kind[u];
-  int root = 0;
-  if (lane == 0) root = uf_find(a.parent, i);
-  root = __shfl_sync(GCR_FULL, root, 0);
-  const float4* xi = reinterpret_cast<const float4*>(a.XA + (size_t)i * a.d);
-  const float4* xc = reinterpret_cast<const float4*>(node_row(a, root));
-  float ss = 0.f;
-  for (int v = lane; v < (a.d >> 2); v += 32) {
-    const float4 p = xi[v], q = xc[v];
-    const float e0 = p.x - q.x, e1 = p.y - q.y, e2 = p.z - q.z, e3 = p.w - q.w;
-    ss = fmaf(e0, e0, fmaf(e1, e1, fmaf(e2, e2, fmaf(e3, e3, ss))));
+  const int U = min(*a.unc_count, a.unc_cap);
+  const int nw = gridDim.x * (blockDim.x >> 5);
+  for (int u = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); u < U; u += nw) {
+    const int i = a.unc_row[u], kind = a.unc_kind[u];
+    int root = 0;
+    if (lane == 0) root = uf_find(a.parent, i);
+    root = __shfl_sync(GCR_FULL, root, 0);
+    const float4* xi = reinterpret_cast<const float4*>(a.XA + (size_t)i * a.d);
+    const float4* xc = reinterpret_cast<const float4*>(node_row(a, root));
+    float ss = 0.f;
+    for (int v = lane; v < (a.d >> 2); v += 32) {
+      const float4 p = xi[v], q = xc[v];
+      const float e0 = p.x - q.x, e1 = p.y - q.y, e2 = p.z - q.z, e3 = p.w - q.w;
+      ss = fmaf(e0, e0, fmaf(e1, e1, fmaf(e2, e2, fmaf(e3, e3, ss))));
+    }
+    ss = warp_sum(ss);
+    if (lane == 0) {
+      // FP32 differences and sums carry a relative error below (d + 2) * 2^-24 <= 2.5e-4 (d <= 4096)
+      const double dist = sqrt((double)ss * (1.0 + 1e-3));
+      const float dk = a.unc_dk[u];  // negative: the refinement predicted an overflowing band
+      const double R = (dist + sqrt((double)fabsf(dk))) * (1.0 + 1e-6) + 1e-12;
+      atomicMax(reinterpret_cast<int*>(a.rad) + root, __float_as_int(__double2float_ru(R)));
+      a.seen[root] = 1;
+      if (dk < 0.f) a.rdense[root] = 1;
+      a.root_of_row[i] = root;
+      const int pm = a.pend[i];
+      if ((pm & ((1 << kind) - 1)) == 0) atomicAdd(a.acnt + root, 1);  // lowest pending graph of the row
+    }
   }
-  ss = warp_sum(ss);
-  if (lane != 0) return;
-  // FP32 differences and sums carry a relative error below (d + 2) * 2^-24 <= 2.5e-4 (d <= 4096)
-  const double dist = sqrt((double)ss * (1.0 + 1e-3));
-  const double R = (dist + sqrt((double)a.unc_dk[u])) * (1.0 + 1e-6) + 1e-12;
-  atomicMax(reinterpret_cast<int*>(a.rad) + root, __float_as_int(__double2float_ru(R)));
-  a.active[root] = 1;
-  a.root_of_row[i] = root;
-  const int pm = a.pend[i];
-  if ((pm & ((1 << kind) - 1)) == 0) atomicAdd(a.acnt + root, 1);  // lowest pending graph of the row
+}
+
+// The groups searched: roots with a pair whose band the refinement predicted to overflow, or with
+// at least kMinGroupRows pending rows in a contracted ball (R^2 <= ||c||^2 / 4: centring shrinks
+// the rounding bound by (R / ||c||)^2, so a wider ball gains too little over the rescan); the
+// others' pairs go to the threshold rescan.
+__global__ void ball_elig_kernel(BallArgs a) {
+  for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < node_count(a); v += gridDim.x * blockDim.x) {
+    const double nc = (a.two && v >= a.na) ? a.n64B[v - a.na] : a.n64A[v];
+    const double R = (double)a.rad[v];
+    const bool contracted = R * R <= 0.25 * nc;
+    a.active[v] = (a.seen[v] && (a.rdense[v] || (a.acnt[v] >= kMinGroupRows && contracted))) ? 1 : 0;
+  }
 }
 
 // Group table from the scanned active flags; the sweep threshold of each centre:
@@ -260,10 +290,7 @@ __device__ __forceinline__ int group_of(const int* goff, int G, int e) {
 
 // Places each listed member in its group's segment. Among the A rows the list holds the
 // group's pending rows too, which go first; against a gallery the list already sits after them.
-__global__ void ball_place_kernel(BallArgs a) {
-  const int e = blockIdx.x * blockDim.x + threadIdx.x;
-  const int G = a.gid[node_count(a)];
-  if (G == 0 || e >= min(a.goff[G], a.cap_rows)) return;
+__device__ __forceinline__ void ball_place_one(const BallArgs& a, int G, int e) {
   const int g = group_of(a.goff, G, e);
   if (a.rsize[g] == 0 || e < a.boff[g] || e >= a.boff[g] + a.blim[g]) return;
   if (a.gfill[g] != a.blim[g]) {  // the fill pass listed a different count than the count pass
@@ -293,20 +320,30 @@ __global__ void ball_place_kernel(BallArgs a) {
   a.ggrp[p] = g;
 }
 
+__global__ void ball_place_kernel(BallArgs a) {
+  const int G = a.gid[node_count(a)];
+  if (G == 0) return;
+  const int E = min(a.goff[G], a.cap_rows);
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < E; e += gridDim.x * blockDim.x)
+    ball_place_one(a, G, e);
+}
 // Against a gallery: the pending rows of each searched group at the head of its segment.
 __global__ void ball_place_rows_kernel(BallArgs a) {
-  const int u = blockIdx.x * blockDim.x + threadIdx.x;
-  if (u >= min(*a.unc_count, a.unc_cap)) return;
-  const int i = a.unc_row[u], kind = a.unc_kind[u];
-  if ((a.pend[i] & ((1 << kind) - 1)) != 0) return;  // once per row
-  const int g = a.gid[a.root_of_row[i]];
-  if (a.rsize[g] == 0) return;
-  const int s = atomicAdd(a.afill + g, 1);
-  if (s >= a.ga[g]) { a.gfail[g] = 1; return; }
-  const int p = a.goff[g] + s;
-  a.pos_of_row[i] = p;
-  a.gmap[p] = i;
-  a.ggrp[p] = g;
+  const int U = min(*a.unc_count, a.unc_cap);
+  for (int u = blockIdx.x * blockDim.x + threadIdx.x; u < U; u += gridDim.x * blockDim.x) {
+    const int i = a.unc_row[u], kind = a.unc_kind[u];
+    if ((a.pend[i] & ((1 << kind) - 1)) != 0) continue;  // once per row
+    const int root = a.root_of_row[i];
+    if (!a.active[root]) continue;                        // a group left to the rescan
+    const int g = a.gid[root];
+    if (a.rsize[g] == 0) continue;
+    const int s = atomicAdd(a.afill + g, 1);
+    if (s >= a.ga[g]) { a.gfail[g] = 1; continue; }
+    const int p = a.goff[g] + s;
+    a.pos_of_row[i] = p;
+    a.gmap[p] = i;
+    a.ggrp[p] = g;
+  }
 }
 
 // Every pending row of a group must have been placed; work items of the searched groups.
@@ -344,11 +381,19 @@ __device__ __forceinline__ unsigned long long dbits_b(double v) { return (unsign
 // squared norm (float-float, combined in FP64), the bias ||y||^2 / 2 of the pool scores, the
 // rounding-error norms (rounded up as in the row statistics) and the group maxima.
 template <Elt E>
+__device__ __forceinline__ void ball_center_one(const BallArgs& a, int p, int lane);
+
+template <Elt E>
 __global__ void __launch_bounds__(256) ball_center_kernel(BallArgs a) {
   const int lane = threadIdx.x & 31;
-  const int p = blockIdx.x * 8 + (threadIdx.x >> 5);
   const int G = a.gid[node_count(a)];
-  if (G == 0 || p >= min(a.goff[G], a.cap_rows)) return;
+  if (G == 0) return;
+  const int P = min(a.goff[G], a.cap_rows);
+  for (int p = blockIdx.x * 8 + (threadIdx.x >> 5); p < P; p += gridDim.x * 8) ball_center_one<E>(a, p, lane);
+}
+
+template <Elt E>
+__device__ __forceinline__ void ball_center_one(const BallArgs& a, int p, int lane) {
   const int g = a.ggrp[p];
   if (g < 0 || a.gfail[g] || a.rsize[g] == 0) return;
   const int j = a.gmap[p];
@@ -397,7 +442,86 @@ __global__ void __launch_bounds__(256) ball_center_kernel(BallArgs a) {
   atomicMax(reinterpret_cast<unsigned long long*>(&sc->amax), dbits_b((double)an));
 }
 
+// ---------------------------------------------------------------- cluster order of the rows
+// Propagation gathers each row's neighbour rows; it hits in L2 when the rows in flight share
+// their neighbours, i.e. when rows are walked cluster by cluster. Clusters here are the
+// components of the graph linking each row to its first kOrderLinks neighbours at a similar local
+// scale (the k-th distances within kScaleRatio of each other, so that a row whose neighbours lie
+// in other clusters does not chain clusters together). A component whose rows fit in half of
+// L2 is walked as one run (key = its root); the rows of a larger one (which no order keeps in
+// L2, and whose single run would only serialise unrelated gathers) keep their previous key.
+// Rows are counting-sorted by key.
+constexpr int kOrderLinks = 4;
+
+__global__ void order_init_kernel(int* parent, int* cnt, int* fill, int n) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    parent[i] = i;
+    cnt[i] = 0;
+    fill[i] = 0;
+  }
+}
+
+__global__ void order_link_kernel(const int32_t* nbr, const float* d2, int n, int k, int* parent, int* err) {
+  const int links = min(k, kOrderLinks);
+  for (long t = (long)blockIdx.x * blockDim.x + threadIdx.x; t < (long)n * links; t += (long)gridDim.x * blockDim.x) {
+    const int i = (int)(t / links), s = (int)(t % links);
+    const int j = nbr[(size_t)i * k + s];
+    if (j < 0) continue;
+    const float di = d2[(size_t)i * k + k - 1], dj = d2[(size_t)j * k + k - 1];
+    if (di <= kScaleRatio * dj && dj <= kScaleRatio * di && !uf_unite(parent, i, j)) atomicOr(err, 1);
+  }
+}
+
+__global__ void order_count_kernel(int* parent, int n, int* root, int* cnt) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    const int r = uf_find(parent, i);
+    root[i] = r;
+    atomicAdd(cnt + r, 1);
+  }
+}
+
+// key[i] = root[i] for rows of components of at most max_run rows, else prev_key[i]; counted.
+__global__ void order_key2_kernel(const int* root, const int* csize, const int* prev_key, int n, int max_run,
+                                  int* key, int* cnt) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    const int r = root[i];
+    const int kk = csize[r] <= max_run ? r : prev_key[i];
+    key[i] = kk;
+    atomicAdd(cnt + kk, 1);
+  }
+}
+
+__global__ void order_scatter_kernel2(const int* root, const int* off, int n, int* fill, int* order) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    const int r = root[i];
+    order[off[r] + atomicAdd(fill + r, 1)] = i;
+  }
+}
+
 }  // namespace
+
+cudaError_t launch_cluster_order(const int32_t* nbr, const float* d2, int n, int d, int k, const int* prev_key,
+                                 int* parent, int* root, int* csize, int* cnt, int* off, int* fill, int* order,
+                                 int* err, cudaStream_t st) {
+  if (n < 1 || k < 1) return cudaSuccess;
+  int dev = 0, l2 = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  e = cudaDeviceGetAttribute(&l2, cudaDevAttrL2CacheSize, dev);
+  if (e != cudaSuccess) return e;
+  const int max_run = (int)std::max<long>(1, (long)l2 / 2 / ((long)d * 4));
+  const int nb = std::min((n + 255) / 256, 152 * 8);
+  order_init_kernel<<<nb, 256, 0, st>>>(parent, csize, fill, n);
+  e = cudaMemsetAsync(cnt, 0, sizeof(int) * (n + 1), st);
+  if (e != cudaSuccess) return e;
+  order_link_kernel<<<nb, 256, 0, st>>>(nbr, d2, n, k, parent, err);
+  order_count_kernel<<<nb, 256, 0, st>>>(parent, n, root, csize);
+  order_key2_kernel<<<nb, 256, 0, st>>>(root, csize, prev_key, n, max_run, root, cnt);
+  e = launch_scan(cnt, off, n, st);
+  if (e != cudaSuccess) return e;
+  order_scatter_kernel2<<<nb, 256, 0, st>>>(root, off, n, fill, order);
+  return cudaGetLastError();
+}
 
 size_t carve_ball(Carve& c, int n, int d, int kinds, int kp, Elt elt, int cap_rows, BallArgs* out, int nb) {
   // n: nodes (the A rows, plus the nb gallery rows of a search against a gallery)
@@ -406,6 +530,8 @@ size_t carve_ball(Carve& c, int n, int d, int kinds, int kp, Elt elt, int cap_ro
   t.pend = c.take<int>(n);
   t.acnt = c.take<int>(n);
   t.rad = c.take<float>(n);
+  t.rdense = c.take<int>(n);
+  t.seen = c.take<int>(n);
   t.active = c.take<int>(n + 1);
   t.gid = c.take<int>(n + 1);
   t.pos_of_row = c.take<int>(n);
@@ -446,7 +572,7 @@ size_t carve_ball(Carve& c, int n, int d, int kinds, int kp, Elt elt, int cap_ro
   if (out) {
     BallArgs& a = *out;
 #define GCR_BALL_TAKE(f) a.f = t.f
-    GCR_BALL_TAKE(parent); GCR_BALL_TAKE(pend); GCR_BALL_TAKE(acnt); GCR_BALL_TAKE(rad); GCR_BALL_TAKE(active);
+    GCR_BALL_TAKE(parent); GCR_BALL_TAKE(pend); GCR_BALL_TAKE(acnt); GCR_BALL_TAKE(rad); GCR_BALL_TAKE(rdense); GCR_BALL_TAKE(seen); GCR_BALL_TAKE(active);
     GCR_BALL_TAKE(gid); GCR_BALL_TAKE(pos_of_row); GCR_BALL_TAKE(root_of_row); GCR_BALL_TAKE(groot);
     GCR_BALL_TAKE(ga); GCR_BALL_TAKE(gkind); GCR_BALL_TAKE(gthr); GCR_BALL_TAKE(gthr_fill); GCR_BALL_TAKE(gsize);
     GCR_BALL_TAKE(rsize); GCR_BALL_TAKE(goff); GCR_BALL_TAKE(boff); GCR_BALL_TAKE(blim); GCR_BALL_TAKE(gscale); GCR_BALL_TAKE(gfill); GCR_BALL_TAKE(afill); GCR_BALL_TAKE(bfill);
@@ -465,12 +591,13 @@ cudaError_t launch_ball_prepare(const BallArgs& a, cudaStream_t st) {
   const int nn = a.two ? a.na + a.nb : a.na;
   if (a.na < 1 || a.unc_cap < 1) return cudaSuccess;
   const int nb = (nn + 255) / 256;
-  const int wb = (a.unc_cap + 7) / 8;
+  const int wb = std::min((a.unc_cap + 7) / 8, 152 * 8);   // grid-stride loops over the pending pairs
   ball_init_kernel<<<nb, 256, 0, st>>>(a);
-  ball_mark_kernel<<<(a.unc_cap + 255) / 256, 256, 0, st>>>(a);
+  ball_mark_kernel<<<std::min((a.unc_cap + 255) / 256, 152 * 4), 256, 0, st>>>(a);
   if (a.two) ball_scale_kernel<<<wb, 256, 0, st>>>(a);
   ball_link_kernel<<<wb, 256, 0, st>>>(a);
   ball_root_kernel<<<wb, 256, 0, st>>>(a);
+  ball_elig_kernel<<<std::min(nb, 152 * 8), 256, 0, st>>>(a);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   e = launch_scan(a.active, a.gid, nn, st);  // group ids; gid[nn] = number of groups
@@ -495,13 +622,13 @@ cudaError_t launch_ball_prepare(const BallArgs& a, cudaStream_t st) {
   if (e != cudaSuccess) return e;
   e = cudaMemsetAsync(a.ggrp, 0xff, sizeof(int) * a.cap_rows, st);
   if (e != cudaSuccess) return e;
-  ball_place_kernel<<<(a.cap_rows + 255) / 256, 256, 0, st>>>(a);
-  if (a.two) ball_place_rows_kernel<<<(a.unc_cap + 255) / 256, 256, 0, st>>>(a);
+  ball_place_kernel<<<std::min((a.cap_rows + 255) / 256, 152 * 8), 256, 0, st>>>(a);
+  if (a.two) ball_place_rows_kernel<<<std::min((a.unc_cap + 255) / 256, 152 * 4), 256, 0, st>>>(a);
   ball_items_count_kernel<<<nb, 256, 0, st>>>(a);
   e = launch_scan(a.icnt, a.ioff, nn, st);
   if (e != cudaSuccess) return e;
   ball_items_kernel<<<nb, 256, 0, st>>>(a);
-  const unsigned cb = (unsigned)((a.cap_rows + 7) / 8);
+  const unsigned cb = (unsigned)std::min((a.cap_rows + 7) / 8, 152 * 16);
   if (a.elt == Elt::TF32) ball_center_kernel<Elt::TF32><<<cb, 256, 0, st>>>(a);
   else ball_center_kernel<Elt::BF16><<<cb, 256, 0, st>>>(a);
   return cudaGetLastError();

@@ -104,13 +104,16 @@ struct RefineArgs {
   int* unc_kind;
   float* unc_thr;
   float* unc_dk;            // per queued pair (may be NULL): an upper bound on its exact k-th
-                            // squared distance
+                            // squared distance, negated when the pair's band is predicted to
+                            // overflow the band capacity
   float* dk_all;            // [kinds][n] (may be NULL): the same bound for every (row, graph)
   int skip_saturated;       // 1: pairs whose pool is saturated with near-ties are not queued
-  int* bq_count;            // ball refinement: pairs handed on to the band rescan
-  int* bq_row;
-  int* bq_kind;
+  int* bq_count;            // ball refinement: pairs handed on to the band rescan, in the
+  int* bq_row;              // pending queue's order (bq_flag per pending pair, bq_pos its
+  int* bq_kind;             // scan: cap + 1 entries)
   float* bq_thr;
+  int* bq_flag;
+  int* bq_pos;
   unsigned long long* stats;
   // band rescan results
   const int* band_cnt;
@@ -186,6 +189,7 @@ struct BallArgs {
   const int* unc_row;
   const int* unc_kind;
   const float* unc_dk;      // per pair: an upper bound on its exact k-th squared distance
+                            // (negated: the pair's band is predicted to overflow)
   const float* dk_all;      // [kinds][na]: that bound for every (row, graph) (two = 0)
   int unc_cap;
   void* cent;               // scratch: cent_rows rounded rows (the centres' operand copies)
@@ -193,6 +197,8 @@ struct BallArgs {
   int* err;                 // set when a union-find link gives up
   // workspace (carve_ball)
   int *parent, *pend, *acnt, *active, *gid, *pos_of_row, *root_of_row;
+  int* rdense;              // per root: a pair of the group was predicted to overflow the band
+  int* seen;                // per root: the root of some pending pair
   float* rad;
   float* gscale;            // per B row (two = 1): its local scale
   int *groot, *ga, *gkind, *gsize, *rsize, *goff, *boff, *blim, *gfill, *afill, *bfill, *gfail, *icnt, *ioff;
@@ -217,6 +223,14 @@ struct BallArgs {
 // n: nodes (the A rows, plus the nb B rows when two = 1); cap_rows: gathered positions.
 size_t carve_ball(Carve& c, int n, int d, int kinds, int kp, Elt elt, int cap_rows, BallArgs* out, int nb = 0);
 cudaError_t launch_ball_prepare(const BallArgs& a, cudaStream_t st);
+// Cluster order of the rows for the propagation: order[0..n) lists the rows component by
+// component of the graph of each row's first few neighbours at a similar scale (nbr, d2: n x k
+// lists by ascending distance), for components whose rows (d floats each) fit in half of L2;
+// the rows of larger components are ordered by prev_key. Scratch: parent, root, csize, fill (n),
+// cnt, off (n + 1).
+cudaError_t launch_cluster_order(const int32_t* nbr, const float* d2, int n, int d, int k, const int* prev_key,
+                                 int* parent, int* root, int* csize, int* cnt, int* off, int* fill, int* order,
+                                 int* err, cudaStream_t st);
 
 // ---- graph.cu
 struct GraphArgs {

@@ -15,6 +15,8 @@
 //      exact FP64 ties go to the smaller index.
 #include <cuda_bf16.h>
 
+#include <algorithm>
+
 #include "common.cuh"
 #include "kernels.h"
 
@@ -411,7 +413,8 @@ __global__ void __launch_bounds__(256) refine_pool_kernel(RefineArgs a) {
     const float mid = pool_at(KP / 2);
     const double dens = (KP / 2) / fmax((double)mid - (double)tau, 1e-30);
     const double below = fmax(0.0, 2.0 * delta + 0.5 * (sc.nmax - sc.nmin) - ((double)s_k - (double)tau));
-    const bool saturated = a.skip_saturated && full && KP + dens * below > 512.0;
+    const bool dense = full && KP + dens * below > 512.0;
+    const bool saturated = a.skip_saturated && dense;
     if (!cert && lane == 0) {
       if (a.stats) atomicAdd(&a.stats[GCR_STAT_UNCERTIFIED], 1ull);
       if (saturated) {
@@ -421,7 +424,8 @@ __global__ void __launch_bounds__(256) refine_pool_kernel(RefineArgs a) {
         a.unc_row[u] = row;
         a.unc_kind[u] = kind;
         a.unc_thr[u] = __double2float_rd(sig_k - eps + 0.5 * sc.nmin - delta);
-        if (a.unc_dk) a.unc_dk[u] = dk;
+        // negative (never -0): the pair's band is predicted to overflow
+        if (a.unc_dk) a.unc_dk[u] = dense ? -fmaxf(dk, 1e-30f) : dk;
       }
     }
   }
@@ -533,21 +537,25 @@ __global__ void __launch_bounds__(256, 3) refine_band_kernel(RefineArgs a) {
 // neighbour lies in the ball, so the pool's refined top k is then N_i. Otherwise, and for pairs
 // outside the searched groups, the pair goes on to the band queue with its original threshold.
 template <int VPL, int P>
+__device__ void refine_ball_one(const RefineArgs& a, const BallArgs& b, int u, int lane);
+
+template <int VPL, int P>
 __global__ void __launch_bounds__(256) refine_ball_kernel(RefineArgs a, BallArgs b) {
-  constexpr int KP = 32 * P;
   const int lane = threadIdx.x & 31;
-  const int u = blockIdx.x * 8 + (threadIdx.x >> 5);
-  if (u >= min(*a.unc_count, b.unc_cap)) return;
+  const int U = min(*a.unc_count, b.unc_cap);
+  for (int u = blockIdx.x * 8 + (threadIdx.x >> 5); u < U; u += gridDim.x * 8) refine_ball_one<VPL, P>(a, b, u, lane);
+}
+
+template <int VPL, int P>
+__device__ void refine_ball_one(const RefineArgs& a, const BallArgs& b, int u, int lane) {
+  constexpr int KP = 32 * P;
   const int i = a.unc_row[u], kind = a.unc_kind[u];
   const int p = b.pos_of_row[i];
   const int g = p >= 0 ? b.ggrp[p] : -1;
+  // pairs handed on to the band rescan are flagged; a stable compaction keeps the pending
+  // queue's (cluster-local) order for the rescan, whose candidate gathers then hit in L2
   auto hand_on = [&]() {
-    if (lane == 0) {
-      const int v = atomicAdd(a.bq_count, 1);
-      a.bq_row[v] = i;
-      a.bq_kind[v] = kind;
-      a.bq_thr[v] = a.unc_thr[u];
-    }
+    if (lane == 0) a.bq_flag[u] = 1;
   };
   if (g < 0 || b.gfail[g]) { hand_on(); return; }
   const float* pv = b.gpool_v + ((size_t)kind * b.cap_rows + p) * KP;
@@ -828,7 +836,7 @@ cudaError_t launch_band_p(const RefineArgs& a, cudaStream_t st) {
 
 template <int P>
 cudaError_t launch_ball_vpl(const RefineArgs& a, const BallArgs& b, cudaStream_t st) {
-  dim3 grid((unsigned)((b.unc_cap + 7) / 8));
+  dim3 grid((unsigned)std::min((b.unc_cap + 7) / 8, 152 * 8));  // warps stride over the pending pairs
   const int vpl = (a.d + 127) / 128;
   if (vpl <= 1) refine_ball_kernel<1, P><<<grid, 256, 0, st>>>(a, b);
   else if (vpl <= 2) refine_ball_kernel<2, P><<<grid, 256, 0, st>>>(a, b);
@@ -840,11 +848,30 @@ cudaError_t launch_ball_vpl(const RefineArgs& a, const BallArgs& b, cudaStream_t
   return cudaGetLastError();
 }
 
+__global__ void hand_on_kernel(RefineArgs a, int cap) {
+  const int U = min(*a.unc_count, cap);
+  for (int u = blockIdx.x * blockDim.x + threadIdx.x; u < U; u += gridDim.x * blockDim.x) {
+    if (!a.bq_flag[u]) continue;
+    const int v = a.bq_pos[u];
+    a.bq_row[v] = a.unc_row[u];
+    a.bq_kind[v] = a.unc_kind[u];
+    a.bq_thr[v] = a.unc_thr[u];
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) *a.bq_count = a.bq_pos[cap];
+}
+
 cudaError_t launch_refine_ball(const RefineArgs& a, const BallArgs& b, cudaStream_t st) {
-  if (a.kp == 32) return launch_ball_vpl<1>(a, b, st);
-  if (a.kp == 64) return launch_ball_vpl<2>(a, b, st);
-  if (a.kp == 128) return launch_ball_vpl<4>(a, b, st);
-  return cudaErrorInvalidValue;
+  cudaError_t e = cudaMemsetAsync(a.bq_flag, 0, sizeof(int) * b.unc_cap, st);
+  if (e != cudaSuccess) return e;
+  if (a.kp == 32) e = launch_ball_vpl<1>(a, b, st);
+  else if (a.kp == 64) e = launch_ball_vpl<2>(a, b, st);
+  else if (a.kp == 128) e = launch_ball_vpl<4>(a, b, st);
+  else return cudaErrorInvalidValue;
+  if (e != cudaSuccess) return e;
+  e = launch_scan(a.bq_flag, a.bq_pos, b.unc_cap, st);
+  if (e != cudaSuccess) return e;
+  hand_on_kernel<<<std::min((b.unc_cap + 255) / 256, 152 * 4), 256, 0, st>>>(a, b.unc_cap);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_refine_band(const RefineArgs& a, cudaStream_t st) {

@@ -18,6 +18,7 @@
 // shared abort flag that every role polls, waits (bounded) for its in-flight MMAs, frees TMEM
 // and returns; the timeout is counted in a device word that gcr_sync reports.
 #include <algorithm>
+#include <cmath>
 #include <cuda.h>
 #include <cuda_bf16.h>
 
@@ -212,6 +213,8 @@ struct UmmaArgs {
   const int4* items;
   const int* n_items;
   const float* col_bias;
+  int vote;        // POOL: pick the kernel that skips groups of four scores below every row's
+                   // threshold by a vote (GPOOL always does)
 };
 
 struct __align__(8) Bars {
@@ -268,7 +271,7 @@ struct Tiles {
 // MODE is a template parameter (not only a field of UmmaArgs) so that each mode's epilogue is
 // compiled alone: no per-value mode branches, and the POOL kernels need 88-90 registers instead
 // of 116-118 (similarity GEMM on crosscam 2.72 -> 2.65 ms per TF32 launch, 2.75 -> 2.48 BF16).
-template <int MODE, int KP, bool CROSS>
+template <int MODE, int KP, bool CROSS, bool VOTE = false>
 __global__ void __launch_bounds__(320, 1)
 umma_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
             const __grid_constant__ CUtensorMap tmA2, const __grid_constant__ CUtensorMap tmB2, UmmaArgs a) {
@@ -488,17 +491,33 @@ umma_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
             const float hb = (cb + lane < cend) ? a.col_bias[cb + lane] : 0.f;
             float2* myq = qs + qrow * kQCap;
 #pragma unroll
-            for (int g = 0; g < 8; ++g) {
-              pool_make_room<KP>(4, lane, me, g_row0 + quad * 32, kind * BM + quad * 32, qs, pv, pi);
+            for (int c = 0; c < 32; ++c) v[c] -= __shfl_sync(GCR_FULL, hb, c);  // biased scores
+            const int r0w = g_row0 + quad * 32;  // first row of this warp (rows are not 32-aligned)
+            if (cb + 32 > cend || (a.self_excl && cb < r0w + 32 && cb + 32 > r0w)) {
 #pragma unroll
-              for (int c = 0; c < 4; ++c) {
-                const int cc = g * 4 + c;
-                const int j = cb + cc;
-                const int cj = __shfl_sync(GCR_FULL, ccam, cc);
-                const float hj = __shfl_sync(GCR_FULL, hb, cc);
-                bool ok = j < cend && !(a.self_excl && j == my_row);
-                if (CROSS && kind == 1) ok = ok && cj != my_cam;
-                pool_push(me, v[cc] - hj, j, ok, myq, sw);
+              for (int c = 0; c < 32; ++c)
+                if (cb + c >= cend || (a.self_excl && cb + c == my_row)) v[c] = -CUDART_INF_F;
+            }
+            // four values at a time, as in the POOL mode
+#pragma unroll
+            for (int g = 0; g < 8; ++g) {
+              const float m4 = fmaxf(fmaxf(v[4 * g], v[4 * g + 1]), fmaxf(v[4 * g + 2], v[4 * g + 3]));
+              if (!VOTE || __any_sync(GCR_FULL, m4 > me.tau)) {
+                pool_make_room<KP>(4, lane, me, r0w, kind * BM + quad * 32, qs, pv, pi);
+#pragma unroll
+                for (int c = 0; c < 4; ++c) {
+                  const int cc = g * 4 + c;
+                  const int cj = (CROSS && kind == 1) ? __shfl_sync(GCR_FULL, ccam, cc) : 0;
+                  const bool eligible = !(CROSS && kind == 1) || cj != my_cam;
+                  if (VOTE) {
+                    if (eligible && v[cc] > me.tau) {
+                      myq[me.qcnt ^ sw] = make_float2(v[cc], __int_as_float(cb + cc));
+                      ++me.qcnt;
+                    }
+                  } else {
+                    pool_push(me, v[cc], cb + cc, eligible, myq, sw);  // branch-free append
+                  }
+                }
               }
             }
           }
@@ -507,20 +526,52 @@ umma_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
             int ccam = 0;
             if (CROSS && kind == 1) ccam = (cb + lane < a.n) ? a.cam[cb + lane] : -1;
             float2* myq = qs + qrow * kQCap;
+            const int r0w = blockIdx.x * BM + quad * 32;  // first row of this warp
+            if (VOTE) {
+              // Where few scores pass (a long sweep for the pool size, or admission floors),
+              // most groups of four fall below every row's threshold: one vote over the warp
+              // skips them. The chunk on the warp's diagonal (each row meets itself) and the
+              // ragged last chunk first get their excluded columns set to -inf. The queues get
+              // room every 4 values; votes and shuffles run on every lane.
+              if (cb + 32 > a.n || (a.self_excl && cb == r0w)) {
 #pragma unroll
-            // queues are checked every 4 values, so they fill to 28 of 32 slots before a merge
-            // (every 8: 24; measured 2.82 -> 2.73 ms per TF32 launch, every 2 is slower again)
-            for (int g = 0; g < 8; ++g) {
-              pool_make_room<KP>(4, lane, me, blockIdx.x * BM + quad * 32, kind * BM + quad * 32, qs, pv, pi);
+                for (int c = 0; c < 32; ++c)
+                  if (cb + c >= a.n || (a.self_excl && cb + c == my_row)) v[c] = -CUDART_INF_F;
+              }
 #pragma unroll
-              for (int c = 0; c < 4; ++c) {
-                const int cc = g * 4 + c;
-                const int j = cb + cc;
-                // the shuffle runs on every lane (a full-mask shuffle must not sit behind a branch)
-                const int cj = __shfl_sync(GCR_FULL, ccam, cc);
-                bool ok = j < a.n && !(a.self_excl && j == my_row);
-                if (CROSS && kind == 1) ok = ok && cj != my_cam;
-                pool_push(me, v[cc], j, ok, myq, sw);
+              for (int g = 0; g < 8; ++g) {
+                const float m4 = fmaxf(fmaxf(v[4 * g], v[4 * g + 1]), fmaxf(v[4 * g + 2], v[4 * g + 3]));
+                if (__any_sync(GCR_FULL, m4 > me.tau)) {
+                  pool_make_room<KP>(4, lane, me, r0w, kind * BM + quad * 32, qs, pv, pi);
+#pragma unroll
+                  for (int c = 0; c < 4; ++c) {
+                    const int cc = g * 4 + c;
+                    // every lane of the warp (kind is the warp's) takes the camera of column cc
+                    const int cj = (CROSS && kind == 1) ? __shfl_sync(GCR_FULL, ccam, cc) : 0;
+                    if ((!(CROSS && kind == 1) || cj != my_cam) && v[cc] > me.tau) {
+                      myq[me.qcnt ^ sw] = make_float2(v[cc], __int_as_float(cb + cc));
+                      ++me.qcnt;
+                    }
+                  }
+                }
+              }
+            } else {
+              // Where many scores pass, every value goes through the branch-free append; the
+              // queues are checked every 4 values, so they fill to 28 of 32 slots before a merge
+              // (every 8: 24; measured 2.82 -> 2.73 ms per TF32 launch, every 2 is slower again)
+#pragma unroll
+              for (int g = 0; g < 8; ++g) {
+                pool_make_room<KP>(4, lane, me, r0w, kind * BM + quad * 32, qs, pv, pi);
+#pragma unroll
+                for (int c = 0; c < 4; ++c) {
+                  const int cc = g * 4 + c;
+                  const int j = cb + cc;
+                  // the shuffle runs on every lane (a full-mask shuffle must not sit behind a branch)
+                  const int cj = __shfl_sync(GCR_FULL, ccam, cc);
+                  bool ok = j < a.n && !(a.self_excl && j == my_row);
+                  if (CROSS && kind == 1) ok = ok && cj != my_cam;
+                  pool_push(me, v[cc], j, ok, myq, sw);
+                }
               }
             }
           }
@@ -648,10 +699,10 @@ size_t smem_bytes(int mode) {
   return s;
 }
 
-template <int MODE, int KP, bool CROSS>
+template <int MODE, int KP, bool CROSS, bool VOTE = false>
 cudaError_t launch(const CUtensorMap& ta, const CUtensorMap& tb, const UmmaArgs& a, dim3 grid, cudaStream_t st,
                    const CUtensorMap* ta2 = nullptr, const CUtensorMap* tb2 = nullptr) {
-  auto fn = umma_kernel<MODE, KP, CROSS>;
+  auto fn = umma_kernel<MODE, KP, CROSS, VOTE>;
   const size_t smem = smem_bytes(a.mode);
   cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
@@ -698,7 +749,18 @@ cudaError_t launch_umma_pool(const void* Ab, int na, const void* Bb, int nb, int
   a.pool_v = pool_v;
   a.pool_i = pool_i;
   a.seed = seed;
+  // expected share of a split's scores that enter a row's pool, in random order: about
+  // kp (1 + ln(columns / kp)) / columns; a vote pays where that is small (or with floors)
+  const double cols = (double)std::min(nb, tps * BN);
+  const double admit = cols > kp ? kp * (1.0 + std::log(cols / kp)) / cols : 1.0;
+  a.vote = (seed != nullptr || admit < 0.006) ? 1 : 0;
   dim3 grid((na + BM - 1) / BM, splits);
+  if (a.vote) {
+    if (kp == 32) return cross ? launch<POOL, 32, true, true>(ta, tb, a, grid, st) : launch<POOL, 32, false, true>(ta, tb, a, grid, st);
+    if (kp == 64) return cross ? launch<POOL, 64, true, true>(ta, tb, a, grid, st) : launch<POOL, 64, false, true>(ta, tb, a, grid, st);
+    if (kp == 128) return cross ? launch<POOL, 128, true, true>(ta, tb, a, grid, st) : launch<POOL, 128, false, true>(ta, tb, a, grid, st);
+    return cudaErrorInvalidValue;
+  }
   if (kp == 32) return cross ? launch<POOL, 32, true>(ta, tb, a, grid, st) : launch<POOL, 32, false>(ta, tb, a, grid, st);
   if (kp == 64) return cross ? launch<POOL, 64, true>(ta, tb, a, grid, st) : launch<POOL, 64, false>(ta, tb, a, grid, st);
   if (kp == 128) return cross ? launch<POOL, 128, true>(ta, tb, a, grid, st) : launch<POOL, 128, false>(ta, tb, a, grid, st);
@@ -727,11 +789,12 @@ cudaError_t launch_umma_gpool(const void* Y, int rows, int d, Elt elt, const int
   a.items = items;
   a.n_items = n_items;
   a.col_bias = col_bias;
+  a.vote = 1;
   // persistent: one CTA per SM (the POOL shared memory allows one), items strided over the grid
   dim3 grid((unsigned)std::max(1, std::min(max_items, 152)));
-  if (kp == 32) return cross ? launch<GPOOL, 32, true>(ta, tb, a, grid, st) : launch<GPOOL, 32, false>(ta, tb, a, grid, st);
-  if (kp == 64) return cross ? launch<GPOOL, 64, true>(ta, tb, a, grid, st) : launch<GPOOL, 64, false>(ta, tb, a, grid, st);
-  if (kp == 128) return cross ? launch<GPOOL, 128, true>(ta, tb, a, grid, st) : launch<GPOOL, 128, false>(ta, tb, a, grid, st);
+  if (kp == 32) return cross ? launch<GPOOL, 32, true, true>(ta, tb, a, grid, st) : launch<GPOOL, 32, false, true>(ta, tb, a, grid, st);
+  if (kp == 64) return cross ? launch<GPOOL, 64, true, true>(ta, tb, a, grid, st) : launch<GPOOL, 64, false, true>(ta, tb, a, grid, st);
+  if (kp == 128) return cross ? launch<GPOOL, 128, true, true>(ta, tb, a, grid, st) : launch<GPOOL, 128, false, true>(ta, tb, a, grid, st);
   return cudaErrorInvalidValue;
 }
 

@@ -141,6 +141,36 @@ def test_serving_loop_continuous_batching(gcr):
         np.testing.assert_allclose(d.cpu().numpy(), r.dist, atol=1e-6, rtol=0)
 
 
+def test_serving_loop_memory_budget_binds(gcr):
+    """A memory budget below what the slots could hold at once (4 slots, room for one full batch
+    and a little more): requests whose batch would exceed it wait in the queue, are admitted as
+    in-flight batches complete and free their workspace, the admitted footprint never exceeds the
+    budget, and every result equals a direct call on the request's queries alone."""
+    from paper_2306_08792_gb300.serving import Gallery, Server, make_requests, _bucket
+    w = workloads.serving(seed=5, n_gallery=20000, d=256, n_clusters=1000, n_requests=48, rate=2000.0,
+                          max_batch=64)
+    p = gcr.default_params(k=20, T=2, topk_out=100, precision="tf32")
+    G = Gallery(torch.from_numpy(w.gallery).cuda(), p)
+    probe = Server(G, n_slots=1, max_batch=64)
+    full = probe.ws_of(64)
+    budget = full + probe.ws_of(8)
+    del probe
+    srv = Server(G, n_slots=4, max_batch=64, budget_bytes=budget)
+    assert srv.budget == budget < 4 * full
+    srv.warmup(sizes=(1, 2, 4, 8, 16, 32, 64))
+    reqs = make_requests(w, 48, realtime=False)     # all waiting at once: the budget decides
+    res = srv.run(reqs, realtime=False)
+    assert res["requests"] == 48
+    assert res["memory_waits"] > 0, res
+    assert 0 < res["max_in_flight_bytes"] <= budget, res
+    for r in reqs:
+        assert r.done > 0 and srv.ws_of(_bucket(r.queries.shape[0])) <= budget
+    for r in reqs[::4]:
+        i, d = G.query(torch.from_numpy(r.queries).cuda())
+        assert np.array_equal(i.cpu().numpy(), r.idx)
+        np.testing.assert_allclose(d.cpu().numpy(), r.dist, atol=1e-6, rtol=0)
+
+
 def test_serve_rejects_cross_camera_and_bad_topk(gcr):
     from paper_2306_08792_gb300 import _lib
     import ctypes
