@@ -105,7 +105,11 @@ enum {
   GCR_STAT_BALL = 8,          /* uncertified pairs certified by the ball search: the exact
                                  search, in coordinates centred on a shared ball, of every
                                  sample that can be among their k nearest                 */
-  GCR_STATS_LEN = 9
+  GCR_STAT_BALL_PAIRS = 9,    /* uncertified pairs that took part in the ball search (it
+                                 runs when a pair is predicted dense or 1,024 take part)  */
+  GCR_STAT_BALL_GROUPS = 10,  /* balls searched                                            */
+  GCR_STAT_BALL_ROWS = 11,    /* rows gathered into the searched balls                     */
+  GCR_STATS_LEN = 12
 };
 
 /* The graph produced by gcr_build_graph and consumed by gcr_propagate. All arrays are

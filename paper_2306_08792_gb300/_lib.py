@@ -15,8 +15,8 @@ STAGE_NAMES = ["normalize", "prep", "sim_gemm", "refine", "band", "graph", "prop
                "gcrv", "ball"]
 GCR_STAGES = 12
 STAT_NAMES = ["rows", "uncertified", "band_failed", "fp64_rows", "fp64_dots", "clamped", "rescored", "saturated",
-              "ball"]
-GCR_STATS_LEN = 9
+              "ball", "ball_pairs", "ball_groups", "ball_rows"]
+GCR_STATS_LEN = 12
 
 
 class Params(ctypes.Structure):

@@ -278,7 +278,7 @@ int knn_impl(const float* X, int64_t n64_, int32_t d, const int32_t* cam, const 
       b.enrmA = b.enrmB = w.enrm; b.anrmA = b.anrmB = w.anrm; b.scB = w.sc; b.cam = camp;
       b.pool_i = w.pool_i; b.pool_v = w.pool_v; b.unc_count = w.unc_count; b.unc_row = w.unc_row;
       b.unc_kind = w.unc_kind; b.unc_dk = w.unc_dk; b.dk_all = w.dk_all; b.unc_cap = kinds * n;
-      b.cent = w.band_a; b.cent_rows = w.band_rows; b.err = w.err;
+      b.cent = w.band_a; b.cent_rows = w.band_rows; b.err = w.err; b.stats = stats;
       GCR_CUDA_TRY(launch_ball_prepare(b, st));
       GCR_CUDA_TRY(launch_umma_gpool(b.Yr, b.cap_rows, d, elt, b.gcam, kinds == 2, 1, r.kp, b.items, b.ioff + n,
                                      b.max_items, b.hy, b.gpool_v, b.gpool_i, st));
@@ -304,8 +304,8 @@ int knn_impl(const float* X, int64_t n64_, int32_t d, const int32_t* cam, const 
     if (g->row_order) {
       StageScope so_(GCR_STAGE_GRAPH, st, 5);
       // scratch: the graph build's buffers (free until it runs); w.okey holds the pools' keys
-      GCR_CUDA_TRY(launch_cluster_order(g->nbr, g->nbr_d2, n, d, p->k, w.okey, w.fill, w.long_list, w.op_cnt,
-                                        w.ocnt, w.ooff, w.ofill, g->row_order, w.err, st));
+      GCR_CUDA_TRY(launch_cluster_order(g->nbr, g->nbr_d2, w.n64, n, d, p->k, w.okey, w.fill, w.long_list,
+                                        w.op_cnt, w.ocnt, w.ooff, w.ofill, g->row_order, w.err, st));
     }
   }
   return GCR_OK;
@@ -767,7 +767,7 @@ int serve_knn(const float* xq, int b, int d, const gcr_params* p, int k, int kp,
     bl.enrmA = w.enrm; bl.anrmA = w.anrm; bl.enrmB = gs.enrm; bl.anrmB = gs.anrm; bl.scB = gs.sc; bl.cam = nullptr;
     bl.pool_i = w.pool_i; bl.pool_v = w.pool_v; bl.unc_count = w.unc_count; bl.unc_row = w.unc_row;
     bl.unc_kind = w.unc_kind; bl.unc_dk = w.unc_dk; bl.dk_all = nullptr; bl.unc_cap = b; bl.cent = w.band_a;
-    bl.cent_rows = b; bl.err = w.err;
+    bl.cent_rows = b; bl.err = w.err; bl.stats = stats;
     GCR_CUDA_TRY(cudaMemsetAsync(w.err, 0, sizeof(int) * 4, st));
     GCR_CUDA_TRY(launch_ball_prepare(bl, st));
     GCR_CUDA_TRY(launch_umma_gpool(bl.Yr, bl.cap_rows, d, elt, nullptr, false, 0, kp, bl.items, bl.ioff + b + ng,

@@ -14,6 +14,9 @@
 //     distance bound (same graph) is within a factor kScaleRatio of i's: rows of one contracted
 //     cluster share a local scale, while a row whose k-th neighbour lies in another cluster
 //     (a cluster smaller than k) has a far larger one and does not chain clusters together;
+//     Only pairs that can be in a searched ball take part (ball_participates: a dense pair, or
+//     one whose k-th distance bound is at most a quarter of its squared norm), and the search
+//     runs only when some pair is dense or kMinBallPairs take part;
 //  2. group g gets the centre c_g = x_{r_g}, r_g its smallest member, and the radius
 //     R_g = max over its pairs of ||x_i - c_g|| + sqrt(Dbar), Dbar an upper bound on the pair's
 //     exact k-th squared distance (from its refined pool): by the triangle inequality every
@@ -43,6 +46,14 @@ constexpr float kScaleRatio = 8.f;  // largest ratio of the k-th distance bounds
 // A group of fewer pending rows than this, none of them predicted to overflow the band, is left
 // to the threshold rescan: its ball sweep and 128-row GEMM tiles cost more than their rows' sweeps.
 constexpr int kMinGroupRows = 8;
+// With no pair predicted to overflow the band and fewer taking part than this, the whole ball
+// search is skipped (its fixed cost, a few sweeps and GEMM tiles, exceeds the rescan of so few
+// pairs); every pending pair then goes to the threshold rescan, which certifies them exactly.
+constexpr int kMinBallPairs = 1024;
+
+__device__ __forceinline__ bool ball_go(const BallArgs& a) {
+  return *a.ndense > 0 || *a.npart >= kMinBallPairs;
+}
 
 // Union-find over row indices. Every parent pointer goes to a smaller or equal index, so a find
 // ends after at most x steps. Parents are read and written through L2 (ld/st.cg): the atomics
@@ -94,12 +105,22 @@ __global__ void ball_init_kernel(BallArgs a) {
     a.root_of_row[v] = -1;
   }
   if (a.two && v < a.nb) a.gscale[v] = CUDART_INF_F;
+  if (v == 0) {
+    *a.npart = 0;
+    *a.ndense = 0;
+  }
 }
 
 __global__ void ball_mark_kernel(BallArgs a) {
   const int U = min(*a.unc_count, a.unc_cap);
-  for (int u = blockIdx.x * blockDim.x + threadIdx.x; u < U; u += gridDim.x * blockDim.x)
-    atomicOr(a.pend + a.unc_row[u], 1 << a.unc_kind[u]);
+  for (int u = blockIdx.x * blockDim.x + threadIdx.x; u < U; u += gridDim.x * blockDim.x) {
+    const int i = a.unc_row[u];
+    if (ball_participates(a.unc_dk[u], a.n64A[i])) {
+      atomicOr(a.pend + i, 1 << a.unc_kind[u]);
+      atomicAdd(a.npart, 1);
+      if (a.unc_dk[u] < 0.f) atomicAdd(a.ndense, 1);
+    }
+  }
 }
 
 // Approximate squared distance of pending row i to its pool entry s (against a gallery).
@@ -111,11 +132,13 @@ __device__ __forceinline__ float pool_d2(const BallArgs& a, int i, int kind, int
 // Against a gallery, a gallery row has no kNN list of its own: its local scale is the smallest
 // approximate squared distance at which a pending row lists it among its first k candidates.
 __global__ void ball_scale_kernel(BallArgs a) {
+  if (!ball_go(a)) return;
   const int lane = threadIdx.x & 31;
   const int U = min(*a.unc_count, a.unc_cap);
   const int nw = gridDim.x * (blockDim.x >> 5);
   for (int u = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); u < U; u += nw) {
     const int i = a.unc_row[u], kind = a.unc_kind[u];
+    if (!ball_participates(a.unc_dk[u], a.n64A[i])) continue;
     const int* pi = a.pool_i + ((size_t)kind * a.na + i) * a.kp;
     for (int s = lane; s < a.k; s += 32) {
       const int j = pi[s];
@@ -129,11 +152,13 @@ __global__ void ball_scale_kernel(BallArgs a) {
 // scale (within kScaleRatio): among the A rows, the two k-th distance bounds; against a gallery,
 // i's distance to j and j's scale.
 __global__ void ball_link_kernel(BallArgs a) {
+  if (!ball_go(a)) return;
   const int lane = threadIdx.x & 31;
   const int U = min(*a.unc_count, a.unc_cap);
   const int nw = gridDim.x * (blockDim.x >> 5);
   for (int u = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); u < U; u += nw) {
     const int i = a.unc_row[u], kind = a.unc_kind[u];
+    if (!ball_participates(a.unc_dk[u], a.n64A[i])) continue;
     const int* pi = a.pool_i + ((size_t)kind * a.na + i) * a.kp;
     const float di = a.two ? 0.f : a.dk_all[(size_t)kind * a.na + i];
     for (int s = lane; s < a.k; s += 32) {
@@ -154,11 +179,13 @@ __global__ void ball_link_kernel(BallArgs a) {
 // One warp per pending pair: the pair's root, its contribution to the group radius
 // (||x_i - c|| + sqrt(Dbar), rounded up) and, once per row, the group's pending-row count.
 __global__ void ball_root_kernel(BallArgs a) {
+  if (!ball_go(a)) return;
   const int lane = threadIdx.x & 31;
   const int U = min(*a.unc_count, a.unc_cap);
   const int nw = gridDim.x * (blockDim.x >> 5);
   for (int u = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); u < U; u += nw) {
     const int i = a.unc_row[u], kind = a.unc_kind[u];
+    if (!ball_participates(a.unc_dk[u], a.n64A[i])) continue;  // the same value on every lane
     int root = 0;
     if (lane == 0) root = uf_find(a.parent, i);
     root = __shfl_sync(GCR_FULL, root, 0);
@@ -191,11 +218,14 @@ __global__ void ball_root_kernel(BallArgs a) {
 // the rounding bound by (R / ||c||)^2, so a wider ball gains too little over the rescan); the
 // others' pairs go to the threshold rescan.
 __global__ void ball_elig_kernel(BallArgs a) {
+  const bool go = ball_go(a);
+  if (go && blockIdx.x == 0 && threadIdx.x == 0 && a.stats)
+    atomicAdd(a.stats + GCR_STAT_BALL_PAIRS, (unsigned long long)*a.npart);
   for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < node_count(a); v += gridDim.x * blockDim.x) {
     const double nc = (a.two && v >= a.na) ? a.n64B[v - a.na] : a.n64A[v];
     const double R = (double)a.rad[v];
     const bool contracted = R * R <= 0.25 * nc;
-    a.active[v] = (a.seen[v] && (a.rdense[v] || (a.acnt[v] >= kMinGroupRows && contracted))) ? 1 : 0;
+    a.active[v] = (go && a.seen[v] && (a.rdense[v] || (a.acnt[v] >= kMinGroupRows && contracted))) ? 1 : 0;
   }
 }
 
@@ -332,9 +362,10 @@ __global__ void ball_place_rows_kernel(BallArgs a) {
   const int U = min(*a.unc_count, a.unc_cap);
   for (int u = blockIdx.x * blockDim.x + threadIdx.x; u < U; u += gridDim.x * blockDim.x) {
     const int i = a.unc_row[u], kind = a.unc_kind[u];
+    if (!ball_participates(a.unc_dk[u], a.n64A[i])) continue;
     if ((a.pend[i] & ((1 << kind) - 1)) != 0) continue;  // once per row
     const int root = a.root_of_row[i];
-    if (!a.active[root]) continue;                        // a group left to the rescan
+    if (root < 0 || !a.active[root]) continue;            // no group, or one left to the rescan
     const int g = a.gid[root];
     if (a.rsize[g] == 0) continue;
     const int s = atomicAdd(a.afill + g, 1);
@@ -358,6 +389,10 @@ __global__ void ball_items_count_kernel(BallArgs a) {
     if (!a.gfail[g]) c = (a.ga[g] + 127) / 128;
   }
   a.icnt[g] = c;
+  if (c > 0 && a.stats) {
+    atomicAdd(a.stats + GCR_STAT_BALL_GROUPS, 1ull);
+    atomicAdd(a.stats + GCR_STAT_BALL_ROWS, (unsigned long long)a.rsize[g]);
+  }
   if (g < G) {  // neutral per-group maxima for the centring pass
     a.gsc[g].nmin = 1e300;
     a.gsc[g].nmax = 0.0;
@@ -447,10 +482,11 @@ __device__ __forceinline__ void ball_center_one(const BallArgs& a, int p, int la
 // their neighbours, i.e. when rows are walked cluster by cluster. Clusters here are the
 // components of the graph linking each row to its first kOrderLinks neighbours at a similar local
 // scale (the k-th distances within kScaleRatio of each other, so that a row whose neighbours lie
-// in other clusters does not chain clusters together). A component whose rows fit in half of
-// L2 is walked as one run (key = its root); the rows of a larger one (which no order keeps in
-// L2, and whose single run would only serialise unrelated gathers) keep their previous key.
-// Rows are counting-sorted by key.
+// in other clusters does not chain clusters together), among contracted rows (k-th distance at
+// most a quarter of the squared norm). A component of two or more rows that fit in half of L2
+// is walked as one run (key = its root); the rows of a larger one (which no order keeps in L2,
+// and whose single run would only serialise unrelated gathers) and the rows left alone keep
+// their previous key. Rows are counting-sorted by key.
 constexpr int kOrderLinks = 4;
 
 __global__ void order_init_kernel(int* parent, int* cnt, int* fill, int n) {
@@ -461,13 +497,16 @@ __global__ void order_init_kernel(int* parent, int* cnt, int* fill, int n) {
   }
 }
 
-__global__ void order_link_kernel(const int32_t* nbr, const float* d2, int n, int k, int* parent, int* err) {
+__global__ void order_link_kernel(const int32_t* nbr, const float* d2, const double* n64, int n, int k, int* parent,
+                                  int* err) {
   const int links = min(k, kOrderLinks);
   for (long t = (long)blockIdx.x * blockDim.x + threadIdx.x; t < (long)n * links; t += (long)gridDim.x * blockDim.x) {
     const int i = (int)(t / links), s = (int)(t % links);
+    const float di = d2[(size_t)i * k + k - 1];
+    if (!((double)di <= 0.25 * n64[i])) continue;  // not contracted: the row keeps its key
     const int j = nbr[(size_t)i * k + s];
     if (j < 0) continue;
-    const float di = d2[(size_t)i * k + k - 1], dj = d2[(size_t)j * k + k - 1];
+    const float dj = d2[(size_t)j * k + k - 1];
     if (di <= kScaleRatio * dj && dj <= kScaleRatio * di && !uf_unite(parent, i, j)) atomicOr(err, 1);
   }
 }
@@ -480,12 +519,12 @@ __global__ void order_count_kernel(int* parent, int n, int* root, int* cnt) {
   }
 }
 
-// key[i] = root[i] for rows of components of at most max_run rows, else prev_key[i]; counted.
+// key[i] = root[i] for rows of components of 2 to max_run rows, else prev_key[i]; counted.
 __global__ void order_key2_kernel(const int* root, const int* csize, const int* prev_key, int n, int max_run,
                                   int* key, int* cnt) {
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
     const int r = root[i];
-    const int kk = csize[r] <= max_run ? r : prev_key[i];
+    const int kk = (csize[r] > 1 && csize[r] <= max_run) ? r : prev_key[i];
     key[i] = kk;
     atomicAdd(cnt + kk, 1);
   }
@@ -500,9 +539,9 @@ __global__ void order_scatter_kernel2(const int* root, const int* off, int n, in
 
 }  // namespace
 
-cudaError_t launch_cluster_order(const int32_t* nbr, const float* d2, int n, int d, int k, const int* prev_key,
-                                 int* parent, int* root, int* csize, int* cnt, int* off, int* fill, int* order,
-                                 int* err, cudaStream_t st) {
+cudaError_t launch_cluster_order(const int32_t* nbr, const float* d2, const double* n64, int n, int d, int k,
+                                 const int* prev_key, int* parent, int* root, int* csize, int* cnt, int* off,
+                                 int* fill, int* order, int* err, cudaStream_t st) {
   if (n < 1 || k < 1) return cudaSuccess;
   int dev = 0, l2 = 0;
   cudaError_t e = cudaGetDevice(&dev);
@@ -514,7 +553,7 @@ cudaError_t launch_cluster_order(const int32_t* nbr, const float* d2, int n, int
   order_init_kernel<<<nb, 256, 0, st>>>(parent, csize, fill, n);
   e = cudaMemsetAsync(cnt, 0, sizeof(int) * (n + 1), st);
   if (e != cudaSuccess) return e;
-  order_link_kernel<<<nb, 256, 0, st>>>(nbr, d2, n, k, parent, err);
+  order_link_kernel<<<nb, 256, 0, st>>>(nbr, d2, n64, n, k, parent, err);
   order_count_kernel<<<nb, 256, 0, st>>>(parent, n, root, csize);
   order_key2_kernel<<<nb, 256, 0, st>>>(root, csize, prev_key, n, max_run, root, cnt);
   e = launch_scan(cnt, off, n, st);
@@ -547,6 +586,8 @@ size_t carve_ball(Carve& c, int n, int d, int kinds, int kp, Elt elt, int cap_ro
   t.boff = c.take<int>(n);
   t.blim = c.take<int>(n);
   t.gscale = c.take<float>(nb > 0 ? nb : 1);
+  t.npart = c.take<int>(1);
+  t.ndense = c.take<int>(1);
   t.gfill = c.take<int>(n);
   t.afill = c.take<int>(n);
   t.bfill = c.take<int>(n);
@@ -575,7 +616,8 @@ size_t carve_ball(Carve& c, int n, int d, int kinds, int kp, Elt elt, int cap_ro
     GCR_BALL_TAKE(parent); GCR_BALL_TAKE(pend); GCR_BALL_TAKE(acnt); GCR_BALL_TAKE(rad); GCR_BALL_TAKE(rdense); GCR_BALL_TAKE(seen); GCR_BALL_TAKE(active);
     GCR_BALL_TAKE(gid); GCR_BALL_TAKE(pos_of_row); GCR_BALL_TAKE(root_of_row); GCR_BALL_TAKE(groot);
     GCR_BALL_TAKE(ga); GCR_BALL_TAKE(gkind); GCR_BALL_TAKE(gthr); GCR_BALL_TAKE(gthr_fill); GCR_BALL_TAKE(gsize);
-    GCR_BALL_TAKE(rsize); GCR_BALL_TAKE(goff); GCR_BALL_TAKE(boff); GCR_BALL_TAKE(blim); GCR_BALL_TAKE(gscale); GCR_BALL_TAKE(gfill); GCR_BALL_TAKE(afill); GCR_BALL_TAKE(bfill);
+    GCR_BALL_TAKE(rsize); GCR_BALL_TAKE(goff); GCR_BALL_TAKE(boff); GCR_BALL_TAKE(blim); GCR_BALL_TAKE(gscale);
+    GCR_BALL_TAKE(npart); GCR_BALL_TAKE(ndense); GCR_BALL_TAKE(gfill); GCR_BALL_TAKE(afill); GCR_BALL_TAKE(bfill);
     GCR_BALL_TAKE(gfail); GCR_BALL_TAKE(icnt); GCR_BALL_TAKE(ioff); GCR_BALL_TAKE(gsc); GCR_BALL_TAKE(max_items);
     GCR_BALL_TAKE(items); GCR_BALL_TAKE(ball_j); GCR_BALL_TAKE(gmap); GCR_BALL_TAKE(ggrp); GCR_BALL_TAKE(n64y);
     GCR_BALL_TAKE(hy); GCR_BALL_TAKE(enrm_y); GCR_BALL_TAKE(anrm_y); GCR_BALL_TAKE(gcam); GCR_BALL_TAKE(Y);
@@ -628,7 +670,7 @@ cudaError_t launch_ball_prepare(const BallArgs& a, cudaStream_t st) {
   e = launch_scan(a.icnt, a.ioff, nn, st);
   if (e != cudaSuccess) return e;
   ball_items_kernel<<<nb, 256, 0, st>>>(a);
-  const unsigned cb = (unsigned)std::min((a.cap_rows + 7) / 8, 152 * 16);
+  const unsigned cb = (unsigned)std::min((a.cap_rows + 7) / 8, 152 * 4);
   if (a.elt == Elt::TF32) ball_center_kernel<Elt::TF32><<<cb, 256, 0, st>>>(a);
   else ball_center_kernel<Elt::BF16><<<cb, 256, 0, st>>>(a);
   return cudaGetLastError();

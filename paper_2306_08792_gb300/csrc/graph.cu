@@ -37,20 +37,33 @@ __global__ void weights_kernel(int n, int k, float gamma, const int32_t* __restr
 }
 
 // Exclusive scan of in[0, n) into out[0, n] (out[n] = total), one block of 1024 threads,
-// tiles of 4096 elements with a running carry.
-__global__ void scan_kernel(const int* __restrict__ in, int* __restrict__ out, int n) {
+// tiles of 8,192 elements with a running carry: each tile is read with coalesced loads (all 8
+// per thread in flight) into shared memory, each thread then takes 8 consecutive elements from
+// there (padded against bank conflicts), scans them, and the block combines the threads' sums.
+constexpr int kScanPer = 8;
+constexpr int kScanTile = 1024 * kScanPer;
+__device__ __forceinline__ int scan_pad(int i) { return i + (i >> 5); }
+__global__ void __launch_bounds__(1024) scan_kernel(const int* __restrict__ in, int* __restrict__ out, int n) {
+  __shared__ int tile[kScanTile + kScanTile / 32];
   __shared__ int wsum[32];
   __shared__ int carry_s;
   const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
   if (tid == 0) carry_s = 0;
-  __syncthreads();
-  for (int base = 0; base < n; base += 4096) {
-    int v[4];
+  for (int base = 0; base < n; base += kScanTile) {
+    int ld[kScanPer];
+#pragma unroll
+    for (int e = 0; e < kScanPer; ++e) {
+      const int idx = base + e * 1024 + tid;
+      ld[e] = idx < n ? in[idx] : 0;
+    }
+#pragma unroll
+    for (int e = 0; e < kScanPer; ++e) tile[scan_pad(e * 1024 + tid)] = ld[e];
+    __syncthreads();
+    int v[kScanPer];
     int loc = 0;
 #pragma unroll
-    for (int e = 0; e < 4; ++e) {
-      const int idx = base + tid * 4 + e;
-      v[e] = idx < n ? in[idx] : 0;
+    for (int e = 0; e < kScanPer; ++e) {
+      v[e] = tile[scan_pad(tid * kScanPer + e)];
       loc += v[e];
     }
     int incl = loc;
@@ -71,15 +84,18 @@ __global__ void scan_kernel(const int* __restrict__ in, int* __restrict__ out, i
       wsum[lane] = s;
     }
     __syncthreads();
-    const int carry = carry_s;
-    int run = carry + (w > 0 ? wsum[w - 1] : 0) + incl - loc;
+    int run = carry_s + (w > 0 ? wsum[w - 1] : 0) + incl - loc;
 #pragma unroll
-    for (int e = 0; e < 4; ++e) {
-      const int idx = base + tid * 4 + e;
-      if (idx < n) out[idx] = run;
+    for (int e = 0; e < kScanPer; ++e) {
+      tile[scan_pad(tid * kScanPer + e)] = run;
       run += v[e];
     }
     __syncthreads();
+#pragma unroll
+    for (int e = 0; e < kScanPer; ++e) {
+      const int idx = base + e * 1024 + tid;
+      if (idx < n) out[idx] = tile[scan_pad(e * 1024 + tid)];
+    }
     if (tid == 1023) carry_s = run;
     __syncthreads();
   }

@@ -195,12 +195,15 @@ struct BallArgs {
   void* cent;               // scratch: cent_rows rounded rows (the centres' operand copies)
   int cent_rows;            // >= the number of groups (at most one per pending row)
   int* err;                 // set when a union-find link gives up
+  unsigned long long* stats;  // GCR_STAT_BALL_PAIRS / _GROUPS / _ROWS counters (may be NULL)
   // workspace (carve_ball)
   int *parent, *pend, *acnt, *active, *gid, *pos_of_row, *root_of_row;
   int* rdense;              // per root: a pair of the group was predicted to overflow the band
   int* seen;                // per root: the root of some pending pair
   float* rad;
   float* gscale;            // per B row (two = 1): its local scale
+  int* npart;               // pending pairs taking part, and those predicted dense
+  int* ndense;
   int *groot, *ga, *gkind, *gsize, *rsize, *goff, *boff, *blim, *gfill, *afill, *bfill, *gfail, *icnt, *ioff;
   float *gthr, *gthr_fill;
   RowScalars* gsc;          // per group: maxima over its positions
@@ -220,17 +223,25 @@ struct BallArgs {
   int* gpool_i;
   int cap_rows;
 };
+// Whether a pending pair enters the ball search: its band is predicted to overflow (dk < 0), or
+// its k-th distance bound is at most a quarter of its squared norm (dk <= n_i / 4). A ball holds
+// the pair's k-th neighbour, so R^2 >= dk and a pair above that bound could only be in a ball
+// too wide to be searched; such a pair goes to the threshold rescan, even when its row is
+// placed in a ball for another graph (the ball was sized without it).
+__device__ __forceinline__ bool ball_participates(float dk, double n_i) {
+  return dk < 0.f || (double)dk <= 0.25 * n_i;
+}
 // n: nodes (the A rows, plus the nb B rows when two = 1); cap_rows: gathered positions.
 size_t carve_ball(Carve& c, int n, int d, int kinds, int kp, Elt elt, int cap_rows, BallArgs* out, int nb = 0);
 cudaError_t launch_ball_prepare(const BallArgs& a, cudaStream_t st);
 // Cluster order of the rows for the propagation: order[0..n) lists the rows component by
 // component of the graph of each row's first few neighbours at a similar scale (nbr, d2: n x k
-// lists by ascending distance), for components whose rows (d floats each) fit in half of L2;
-// the rows of larger components are ordered by prev_key. Scratch: parent, root, csize, fill (n),
+// lists by ascending distance; n64 the rows' squared norms), for components of contracted rows
+// that fit in half of L2 (d floats a row); the other rows are ordered by prev_key. Scratch: parent, root, csize, fill (n),
 // cnt, off (n + 1).
-cudaError_t launch_cluster_order(const int32_t* nbr, const float* d2, int n, int d, int k, const int* prev_key,
-                                 int* parent, int* root, int* csize, int* cnt, int* off, int* fill, int* order,
-                                 int* err, cudaStream_t st);
+cudaError_t launch_cluster_order(const int32_t* nbr, const float* d2, const double* n64, int n, int d, int k,
+                                 const int* prev_key, int* parent, int* root, int* csize, int* cnt, int* off,
+                                 int* fill, int* order, int* err, cudaStream_t st);
 
 // ---- graph.cu
 struct GraphArgs {

@@ -557,7 +557,7 @@ __device__ void refine_ball_one(const RefineArgs& a, const BallArgs& b, int u, i
   auto hand_on = [&]() {
     if (lane == 0) a.bq_flag[u] = 1;
   };
-  if (g < 0 || b.gfail[g]) { hand_on(); return; }
+  if (g < 0 || b.gfail[g] || !ball_participates(a.unc_dk[u], a.n64[i])) { hand_on(); return; }
   const float* pv = b.gpool_v + ((size_t)kind * b.cap_rows + p) * KP;
   const int* pi = b.gpool_i + ((size_t)kind * b.cap_rows + p) * KP;
   WList<P> L;
@@ -836,7 +836,8 @@ cudaError_t launch_band_p(const RefineArgs& a, cudaStream_t st) {
 
 template <int P>
 cudaError_t launch_ball_vpl(const RefineArgs& a, const BallArgs& b, cudaStream_t st) {
-  dim3 grid((unsigned)std::min((b.unc_cap + 7) / 8, 152 * 8));  // warps stride over the pending pairs
+  // one block per SM (the kernel's registers allow no more); warps stride over the pending pairs
+  dim3 grid((unsigned)std::min((b.unc_cap + 7) / 8, 152));
   const int vpl = (a.d + 127) / 128;
   if (vpl <= 1) refine_ball_kernel<1, P><<<grid, 256, 0, st>>>(a, b);
   else if (vpl <= 2) refine_ball_kernel<2, P><<<grid, 256, 0, st>>>(a, b);

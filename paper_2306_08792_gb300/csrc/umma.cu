@@ -301,6 +301,7 @@ umma_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
     const int U = min(*a.count, a.cap);
     const int tiles = (U + BM - 1) / BM;
     tl.count = max(0, (tiles - (int)blockIdx.y + (int)gridDim.y - 1) / (int)gridDim.y);
+    if (tl.count == 0) return;  // no rows for this CTA: leave before any barrier or TMEM use
   } else if (MODE == GRAM) {
     // G_s is symmetric: tiles wholly below the diagonal (every column < every row) are mirrored
     tl.count = ((int)blockIdx.x + 1) * BN <= (int)blockIdx.y * BM ? 0 : 1;
