@@ -763,6 +763,78 @@ def serving_vs_oracle(oracle, np, st):
             "max_order_violation": float(np.max(np.maximum(0.0, dq[:, :-1] - dq[:, 1:])))}
 
 
+# ------------------------------------------------------------------ reduced-precision bounds
+# Rounding of a row to each candidate GEMM operand type, from the types' definitions: TF32 and
+# BF16 keep 10 and 7 explicit mantissa bits (round to nearest even); e4m3 keeps 3, with an
+# exponent range that a per-row scale max|x| / 448 maps the row into (subnormals below 2^-6).
+def _round_mantissa(np, x, bits, min_exp=None):
+    ax = np.abs(x)
+    e = np.floor(np.log2(np.where(ax > 0, ax, 1.0)))
+    if min_exp is not None:
+        e = np.maximum(e, min_exp)
+    step = np.exp2(e - bits)
+    return np.round(x / step) * step
+
+
+def rounded_rows(np, X, kind):
+    if kind == "tf32":
+        return _round_mantissa(np, X, 10)
+    if kind == "bf16":
+        return _round_mantissa(np, X, 7)
+    scale = np.max(np.abs(X), axis=1, keepdims=True) / 448.0
+    scale = np.where(scale > 0, scale, 1.0)
+    return _round_mantissa(np, X / scale, 3, min_exp=-6) * scale
+
+
+def certification_rates(np, oracle, X32, rows, k, kinds=("fp8_e4m3", "bf16", "tf32"), pool_mult=4):
+    """For sampled rows: can a pool of pool_mult * k candidates, searched with a GEMM on operands
+    of each type, certify the k nearest? Every score left out of such a pool is at most its last
+    approximate score, so within delta of the (pool+1)-th exact score; the k-th must clear that by
+    2 delta: s_(k) - s_(pool+1) > 2 delta_i, delta_i = ||x^_i|| max||e_j|| + ||e_i|| max||x_j|| +
+    gamma_(d+32) ||x^_i|| max||x^_j|| (x^ the rounded row, e = x^ - x, FP32 accumulation)."""
+    X = X32.astype(np.float64)
+    n, d = X.shape
+    kp = pool_mult * k
+    S = X[rows] @ X.T
+    S[np.arange(len(rows)), rows] = -np.inf
+    top = -np.sort(-S, axis=1)[:, :kp + 1]
+    gap = top[:, k - 1] - top[:, kp]
+    gacc = (d + 32) * 2.0 ** -23
+    out = {"rows": int(len(rows)), "pool": kp, "median_gap_k_to_pool": float(np.median(gap))}
+    for kind in kinds:
+        Xr = rounded_rows(np, X, kind)
+        E = Xr - X
+        en = np.linalg.norm(E, axis=1)
+        an = np.linalg.norm(Xr, axis=1)
+        bn = np.linalg.norm(X, axis=1)
+        delta = an[rows] * en.max() + en[rows] * bn.max() + gacc * an[rows] * an.max()
+        out[kind] = {"certified_share": float(np.mean(gap > 2.0 * delta)), "median_delta": float(np.median(delta))}
+    return out
+
+
+def oracle_full_times(oracle, np, workloads):
+    """The FP64 oracle timed over whole workloads: the plain one (500 + 2,000 rows, d = 256) and
+    the video one (GCRV, Algorithm 2: profiles then GCR with both graphs, full ranking)."""
+    out = {}
+    w = workloads.plain()
+    t0 = time.perf_counter()
+    Xo = oracle.gcr(w.X, w.k, w.gamma, w.T)
+    oracle.rerank(Xo[:w.n_query], Xo[w.n_query:])
+    dt = time.perf_counter() - t0
+    out["plain"] = {"seconds": dt, "queries_per_s": w.n_query / dt,
+                    "workload": "500 queries + 2,000 gallery, d=256, k=20, T=2, full ranking"}
+    v = workloads.video()
+    t0 = time.perf_counter()
+    Xv = oracle.gcrv(v.frames, v.trk_off, v.trk_cam, v.lam, v.k, v.gamma, v.T, alpha=v.alpha)
+    oracle.rerank(Xv[:v.n_query], Xv[v.n_query:])
+    dt = time.perf_counter() - t0
+    out["video"] = {"seconds": dt, "queries_per_s": v.n_query / dt,
+                    "workload": "1,980 + 11,310 tracklets (675,977 frames, d=2048), Eq. 17 profiles, k=20, T=2, "
+                                "cross-camera, full ranking"}
+    out["cores"] = os.cpu_count()
+    return out
+
+
 def max_over_ranks(value: float, dist, device=None) -> float:
     """Largest value over all ranks (the slowest replica sets the job's time)."""
     if dist is None:
@@ -955,6 +1027,22 @@ def run_ours(a):
             if isinstance(sv, dict) and "_staged" in sv:
                 sv["vs_oracle"] = serving_vs_oracle(oracle, np, sv["_staged"])
         line["vs_oracle"]["wall_s_all_workloads"] = time.perf_counter() - t0
+        # whether reduced-precision GEMM operands (FP8 e4m3 with a per-row scale, BF16, TF32)
+        # could certify the kNN of each layer from a pool of 4k candidates
+        t0 = time.perf_counter()
+        rng = np.random.default_rng(7)
+        study = {"crosscam": [], "zipf": []}
+        for L in cross_staged["layers"]:
+            r = np.sort(rng.choice(L["X"].shape[0], 1000, replace=False))
+            study["crosscam"].append(certification_rates(np, oracle, L["X"], r, w.k))
+        if "_staged" in z:
+            for L in z["_staged"]["layers"]:
+                r = np.sort(rng.choice(L["X"].shape[0], 1000, replace=False))
+                study["zipf"].append(certification_rates(np, oracle, L["X"], r, z["_cfg"]["k"]))
+        study["wall_s"] = time.perf_counter() - t0
+        line["precision_study"] = study
+        # the oracle over whole workloads (small plain and video)
+        line["cpu_baseline"]["full_runs"] = oracle_full_times(oracle, np, workloads)
     for obj in [line.get("zipf", {}), line.get("video", {})] + list(line.get("serving", {}).values()):
         if isinstance(obj, dict):
             obj.pop("_staged", None)

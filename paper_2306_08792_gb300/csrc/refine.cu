@@ -148,34 +148,28 @@ __device__ __forceinline__ void sort32_d(double& s, int& i, double& v, int lane)
   }
 }
 
-// The row's own features, lane slice: elements v*128 + lane*4 .. +3.
-template <int VPL>
-__device__ __forceinline__ void load_row(const float* __restrict__ X, int d, int row, int lane, float4 (&xi)[VPL]) {
-  const float* base = X + (size_t)row * d;
-#pragma unroll
-  for (int v = 0; v < VPL; ++v) {
-    const int off = v * 128 + lane * 4;
-    xi[v] = off < d ? *reinterpret_cast<const float4*>(base + off) : make_float4(0.f, 0.f, 0.f, 0.f);
-  }
-}
+// The row's own features x_i are not held in registers (at d = 2048 that would be 64 per lane
+// and cap the resident warps of these latency-bound kernels): every dot product reads the lane's
+// slice (elements v*128 + lane*4 .. +3) again, from L1 after the first time.
 
 // FP32 dots of x_i with up to 4 rows (j < 0: skipped); sequential per-lane chain then butterfly.
 template <int VPL>
-__device__ __forceinline__ void dot4_f32(const float* __restrict__ X, int d, const float4 (&xi)[VPL],
+__device__ __forceinline__ void dot4_f32(const float* __restrict__ X, int d, const float* __restrict__ xrow,
                                          const int (&j)[4], int lane, float (&out)[4]) {
   float acc[4] = {0.f, 0.f, 0.f, 0.f};
 #pragma unroll
   for (int v = 0; v < VPL; ++v) {
     const int off = v * 128 + lane * 4;
     if (off < d) {
+      const float4 xv = *reinterpret_cast<const float4*>(xrow + off);
 #pragma unroll
       for (int t = 0; t < 4; ++t) {
         if (j[t] >= 0) {
           const float4 y = *reinterpret_cast<const float4*>(X + (size_t)j[t] * d + off);
-          acc[t] = fmaf(xi[v].x, y.x, acc[t]);
-          acc[t] = fmaf(xi[v].y, y.y, acc[t]);
-          acc[t] = fmaf(xi[v].z, y.z, acc[t]);
-          acc[t] = fmaf(xi[v].w, y.w, acc[t]);
+          acc[t] = fmaf(xv.x, y.x, acc[t]);
+          acc[t] = fmaf(xv.y, y.y, acc[t]);
+          acc[t] = fmaf(xv.z, y.z, acc[t]);
+          acc[t] = fmaf(xv.w, y.w, acc[t]);
         }
       }
     }
@@ -185,18 +179,19 @@ __device__ __forceinline__ void dot4_f32(const float* __restrict__ X, int d, con
 }
 
 template <int VPL>
-__device__ __forceinline__ double dot_f64(const float* __restrict__ X, int d, const float4 (&xi)[VPL],
+__device__ __forceinline__ double dot_f64(const float* __restrict__ X, int d, const float* __restrict__ xrow,
                                           int j, int lane) {
   double acc = 0.0;
 #pragma unroll
   for (int v = 0; v < VPL; ++v) {
     const int off = v * 128 + lane * 4;
     if (off < d) {
+      const float4 xv = *reinterpret_cast<const float4*>(xrow + off);
       const float4 y = *reinterpret_cast<const float4*>(X + (size_t)j * d + off);
-      acc = fma((double)xi[v].x, (double)y.x, acc);
-      acc = fma((double)xi[v].y, (double)y.y, acc);
-      acc = fma((double)xi[v].z, (double)y.z, acc);
-      acc = fma((double)xi[v].w, (double)y.w, acc);
+      acc = fma((double)xv.x, (double)y.x, acc);
+      acc = fma((double)xv.y, (double)y.y, acc);
+      acc = fma((double)xv.z, (double)y.z, acc);
+      acc = fma((double)xv.w, (double)y.w, acc);
     }
   }
   return warp_sum_d(acc);
@@ -204,7 +199,7 @@ __device__ __forceinline__ double dot_f64(const float* __restrict__ X, int d, co
 
 // Re-scores entries [0, r) of L in FP32 (entry e's index is L.id), setting sig and val.
 template <int VPL, int P>
-__device__ __forceinline__ void rescore(const RefineArgs& a, const float4 (&xi)[VPL], WList<P>& L, int r, int lane) {
+__device__ __forceinline__ void rescore(const RefineArgs& a, const float* __restrict__ xi, WList<P>& L, int r, int lane) {
   for (int e0 = 0; e0 < r; e0 += 4) {
     int j[4];
 #pragma unroll
@@ -237,7 +232,7 @@ __device__ __forceinline__ void rescore(const RefineArgs& a, const float4 (&xi)[
 // the output index of a candidate (the ball search lists gathered positions), also the key of
 // exact FP64 ties.
 template <int VPL, int P>
-__device__ void finalize(const RefineArgs& a, const float4 (&xi)[VPL], WList<P>& L, int r, int kk,
+__device__ void finalize(const RefineArgs& a, const float* __restrict__ xi, WList<P>& L, int r, int kk,
                          double eps, int frow, int orow, int kind, int lane, const int* idmap = nullptr) {
   int32_t* onbr = a.nbr[kind] + (size_t)orow * a.k;
   float* od2 = a.d2[kind] + (size_t)orow * a.k;
@@ -339,7 +334,7 @@ __device__ __forceinline__ void bounds(const RefineArgs& a, int row, int vpl, do
 
 // One warp per (row, kind).
 template <int VPL, int P>
-__global__ void __launch_bounds__(256) refine_pool_kernel(RefineArgs a) {
+__global__ void __launch_bounds__(256, 4) refine_pool_kernel(RefineArgs a) {
   constexpr int KP = 32 * P;
   const int lane = threadIdx.x & 31;
   const long wid = (long)blockIdx.x * 8 + (threadIdx.x >> 5);
@@ -393,8 +388,7 @@ __global__ void __launch_bounds__(256) refine_pool_kernel(RefineArgs a) {
   int r = 0;
 #pragma unroll
   for (int p = 0; p < P; ++p) r += __popc(__ballot_sync(GCR_FULL, L.id[p] >= 0 && (double)pval[p] >= thr));
-  float4 xi[VPL];
-  load_row<VPL>(a.X, a.d, row, lane, xi);
+  const float* xi = a.X + (size_t)row * a.d;
   rescore<VPL, P>(a, xi, L, r, lane);
   if (lane == 0 && a.stats) atomicAdd(&a.stats[GCR_STAT_RESCORED], (unsigned long long)r);
   wl_sort<P>(L, lane);
@@ -480,8 +474,7 @@ __global__ void __launch_bounds__(256, 3) refine_band_kernel(RefineArgs a) {
     double delta, eps;
     RowScalars sc;
     bounds<P>(a, row, VPL, delta, eps, sc);
-    float4 xi[VPL];
-    load_row<VPL>(a.X, a.d, row, lane, xi);
+    const float* xi = a.X + (size_t)row * a.d;
     WList<P> L;
 #pragma unroll
     for (int p = 0; p < P; ++p) { L.sig[p] = -CUDART_INF; L.id[p] = 0x7fffffff; L.val[p] = 0.0; }
@@ -611,8 +604,7 @@ __device__ void refine_ball_one(const RefineArgs& a, const BallArgs& b, int u, i
   c.XB = b.Y;
   c.n64 = b.n64y;
   c.n64B = b.n64y;
-  float4 xi[VPL];
-  load_row<VPL>(b.Y, a.d, p, lane, xi);
+  const float* xi = b.Y + (size_t)p * a.d;
   rescore<VPL, P>(c, xi, L, r, lane);
   if (lane == 0 && a.stats) atomicAdd(&a.stats[GCR_STAT_RESCORED], (unsigned long long)r);
   wl_sort<P>(L, lane);

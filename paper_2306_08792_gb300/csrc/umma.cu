@@ -480,11 +480,20 @@ umma_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
       }
       const int cend = MODE == GPOOL ? g_cend : a.n;  // end of this tile's valid columns
       const int ncol = min(BN, cend - c0);
+      // cross-camera pools: the column cameras of chunk ch + 1 are loaded while chunk ch is
+      // processed, so one load latency per tile is exposed instead of one per chunk
+      int cam_next = 0;
+      if (MODE == POOL && CROSS && kind == 1) cam_next = (c0 + lane < a.n) ? a.cam[c0 + lane] : -1;
       for (int ch = 0; ch < BN / 32; ++ch) {
         if (ch * 32 >= ncol) break;
         float v[32];
         tmem_ld32(tmem + lane_addr + buf * BN + ch * 32, v);
         const int cb = c0 + ch * 32;
+        int cam_cur = 0;
+        if (MODE == POOL && CROSS && kind == 1) {
+          cam_cur = cam_next;
+          if ((ch + 1) * 32 < ncol) cam_next = (cb + 32 + lane < a.n) ? a.cam[cb + 32 + lane] : -1;
+        }
         if (MODE == GPOOL) {
           if (kind == 0 || CROSS) {
             int ccam = 0;
@@ -525,7 +534,7 @@ umma_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
         } else if (MODE == POOL) {
           if (kind == 0 || CROSS) {
             int ccam = 0;
-            if (CROSS && kind == 1) ccam = (cb + lane < a.n) ? a.cam[cb + lane] : -1;
+            if (CROSS && kind == 1) ccam = cam_cur;
             float2* myq = qs + qrow * kQCap;
             const int r0w = blockIdx.x * BM + quad * 32;  // first row of this warp
             if (VOTE) {
