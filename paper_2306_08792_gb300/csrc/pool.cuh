@@ -146,4 +146,118 @@ __device__ __forceinline__ void pool_flush(int lane, bool valid, PoolOwner& me, 
   }
 }
 
+// ---------------------------------------------------------------- lane-parallel heap pools
+// For 32-entry pools on the tensor-core path. Each row's pool is a heap of (score, index) pairs
+// in shared memory ordered by better(): the root is the worst entry kept, so once the heap holds
+// KP entries the admission threshold is the root's score (the same threshold as a sorted list's
+// last entry). Heaps and queues are slot-major, [slot][128 rows] of float2, so the lanes of a
+// warp (consecutive rows) always touch different bank pairs whatever slot each one is at. A lane
+// appends the scores that pass to its row's queue; when any lane's queue could overflow, every
+// lane drains its own queue into its own heap, so one pass serves the warp's 32 rows (the sorted
+// lists instead take one warp-wide merge per row, each waiting on a list in L2). At the end a
+// heapsort leaves each pool sorted best first, as the sorted lists are.
+constexpr int kHeapQ = 8;                  // queue slots per row
+constexpr uint32_t kHeapSlot = 128 * 8;    // bytes between consecutive slots of one row
+
+__device__ __forceinline__ bool worse(float a, int ai, float b, int bi) { return a < b || (a == b && ai > bi); }
+
+__device__ __forceinline__ float2 heap_ld(uint32_t addr) {
+  float2 r;
+  asm volatile("ld.shared.v2.f32 {%0, %1}, [%2];" : "=f"(r.x), "=f"(r.y) : "r"(addr) : "memory");
+  return r;
+}
+__device__ __forceinline__ void heap_st(uint32_t addr, float2 v) {
+  asm volatile("st.shared.v2.f32 [%0], {%1, %2};" ::"r"(addr), "f"(v.x), "f"(v.y) : "memory");
+}
+
+struct HeapState {
+  float tau;
+  int len;
+};
+
+// Drains qcnt queued entries (queue slot 0 at qaddr) into the heap at haddr holding len entries.
+// An entry that no longer beats the root (the threshold rose since it was queued) is dropped.
+// Returns the new threshold (tau unchanged when nothing was queued) and length.
+template <int KP>
+__device__ __noinline__ HeapState heap_drain(uint32_t haddr, uint32_t qaddr, int qcnt, int len, float tau,
+                                             float floor) {
+  for (int i = 0; i < qcnt; ++i) {
+    const float2 e = heap_ld(qaddr + i * kHeapSlot);
+    const int ei = __float_as_int(e.y);
+    if (len < KP) {  // not full yet: sift up from the first free slot
+      int pos = len++;
+      while (pos > 0) {
+        const int par = (pos - 1) >> 1;
+        const float2 p = heap_ld(haddr + par * kHeapSlot);
+        if (!worse(e.x, ei, p.x, __float_as_int(p.y))) break;
+        heap_st(haddr + pos * kHeapSlot, p);
+        pos = par;
+      }
+      heap_st(haddr + pos * kHeapSlot, e);
+    } else {  // full: replace the root if better, then sift down
+      const float2 root = heap_ld(haddr);
+      if (!worse(root.x, __float_as_int(root.y), e.x, ei)) continue;
+      int pos = 0;
+      for (;;) {
+        int c = 2 * pos + 1;
+        if (c >= KP) break;
+        float2 cv = heap_ld(haddr + c * kHeapSlot);
+        if (c + 1 < KP) {
+          const float2 c2 = heap_ld(haddr + (c + 1) * kHeapSlot);
+          if (worse(c2.x, __float_as_int(c2.y), cv.x, __float_as_int(cv.y))) {
+            cv = c2;
+            ++c;
+          }
+        }
+        if (!worse(cv.x, __float_as_int(cv.y), e.x, ei)) break;
+        heap_st(haddr + pos * kHeapSlot, cv);
+        pos = c;
+      }
+      heap_st(haddr + pos * kHeapSlot, e);
+    }
+  }
+  if (qcnt > 0) tau = (len == KP) ? fmaxf(heap_ld(haddr).x, floor) : floor;
+  return HeapState{tau, len};
+}
+
+// Heapsort of the len entries at haddr (best first) and the row's KP-entry list written to lv /
+// li, padded with (-inf, -1) past len.
+template <int KP>
+__device__ __noinline__ void heap_emit(uint32_t haddr, int len, float* lv, int* li) {
+  for (int end = len - 1; end > 0; --end) {
+    const float2 root = heap_ld(haddr);
+    const float2 last = heap_ld(haddr + end * kHeapSlot);
+    const int lasti = __float_as_int(last.y);
+    heap_st(haddr + end * kHeapSlot, root);
+    int pos = 0;
+    for (;;) {
+      int c = 2 * pos + 1;
+      if (c >= end) break;
+      float2 cv = heap_ld(haddr + c * kHeapSlot);
+      if (c + 1 < end) {
+        const float2 c2 = heap_ld(haddr + (c + 1) * kHeapSlot);
+        if (worse(c2.x, __float_as_int(c2.y), cv.x, __float_as_int(cv.y))) {
+          cv = c2;
+          ++c;
+        }
+      }
+      if (!worse(cv.x, __float_as_int(cv.y), last.x, lasti)) break;
+      heap_st(haddr + pos * kHeapSlot, cv);
+      pos = c;
+    }
+    heap_st(haddr + pos * kHeapSlot, last);
+  }
+  for (int e = 0; e < KP; ++e) {
+    float v = -CUDART_INF_F;
+    int i = -1;
+    if (e < len) {
+      const float2 x = heap_ld(haddr + e * kHeapSlot);
+      v = x.x;
+      i = __float_as_int(x.y);
+    }
+    lv[e] = v;
+    li[e] = i;
+  }
+}
+
 }  // namespace gcr

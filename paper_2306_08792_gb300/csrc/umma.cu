@@ -215,6 +215,7 @@ struct UmmaArgs {
   const float* col_bias;
   int vote;        // POOL: pick the kernel that skips groups of four scores below every row's
                    // threshold by a vote (GPOOL always does)
+  int warm;        // POOL: admission floors from each row's first column tile (warm_floor)
 };
 
 struct __align__(8) Bars {
@@ -268,6 +269,71 @@ struct Tiles {
   }
 };
 
+constexpr int kWarmIters = 6;  // bisection steps of warm_floor
+
+// Admission floor of one row from the first column tile of its sweep. A pool starts empty, so
+// without a floor every score of that tile would enter the row's queue and the warp would merge
+// it about BN / 28 times before the threshold means anything. Bisection over the tile's eligible
+// scores (held in TMEM, read once per step) finds a value f with at least KP of them above it:
+// the row's KP best scores of the whole sweep all lie above f, so scores at or below f can be
+// dropped from the sweep, and the row's list still ends full with every score left out below its
+// last entry. The counts use the same values and the same eligibility (column < n, not the row
+// itself, another camera for the cross-camera pool) as the appends. -inf when the tile holds
+// KP eligible scores or fewer. All lanes run every step (the TMEM loads are warp-wide).
+template <int KP, bool CAMCHK>
+__device__ __noinline__ float warm_floor(uint32_t taddr, int cb0, int ncol, int n, int self_excl, int my_row,
+                                         const int* __restrict__ cam, int my_cam, int lane) {
+  uint32_t elig[BN / 32];
+  float lo_v = CUDART_INF_F, hi_v = -CUDART_INF_F;
+  int ne = 0;
+#pragma unroll
+  for (int ch = 0; ch < BN / 32; ++ch) {
+    elig[ch] = 0u;
+    if (ch * 32 < ncol) {
+      float v[32];
+      tmem_ld32(taddr + ch * 32, v);
+      const int cb = cb0 + ch * 32;
+      int ccam = 0;
+      if (CAMCHK) ccam = (cb + lane < n) ? cam[cb + lane] : -1;
+#pragma unroll
+      for (int c = 0; c < 32; ++c) {
+        const int cj = CAMCHK ? __shfl_sync(GCR_FULL, ccam, c) : 0;
+        const bool e = cb + c < n && !(self_excl && cb + c == my_row) && (!CAMCHK || cj != my_cam);
+        if (e) {
+          lo_v = fminf(lo_v, v[c]);
+          hi_v = fmaxf(hi_v, v[c]);
+          ++ne;
+          elig[ch] |= 1u << c;
+        }
+      }
+    }
+  }
+  const bool active = ne > KP;
+  float f = -CUDART_INF_F;
+  float a = active ? lo_v : 0.f, b = active ? hi_v : 0.f;
+#pragma unroll 1
+  for (int it = 0; it < kWarmIters; ++it) {
+    const float mid = 0.5f * a + 0.5f * b;
+    int cnt = 0;
+#pragma unroll
+    for (int ch = 0; ch < BN / 32; ++ch) {
+      if (ch * 32 < ncol) {
+        float v[32];
+        tmem_ld32(taddr + ch * 32, v);
+#pragma unroll
+        for (int c = 0; c < 32; ++c) cnt += (((elig[ch] >> c) & 1u) && v[c] > mid) ? 1 : 0;
+      }
+    }
+    if (cnt >= KP) {
+      f = mid;
+      a = mid;
+    } else {
+      b = mid;
+    }
+  }
+  return active ? f : -CUDART_INF_F;
+}
+
 // MODE is a template parameter (not only a field of UmmaArgs) so that each mode's epilogue is
 // compiled alone: no per-value mode branches, and the POOL kernels need 88-90 registers instead
 // of 116-118 (similarity GEMM on crosscam 2.72 -> 2.65 ms per TF32 launch, 2.75 -> 2.48 BF16).
@@ -276,9 +342,15 @@ __global__ void __launch_bounds__(320, 1)
 umma_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
             const __grid_constant__ CUtensorMap tmA2, const __grid_constant__ CUtensorMap tmB2, UmmaArgs a) {
   extern __shared__ __align__(1024) unsigned char dyn_raw[];
-  unsigned char* dyn = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(dyn_raw) + 1023) & ~uintptr_t(1023));
+  // aligned by an offset from the shared array itself, so that every pointer derived from it
+  // stays known as shared memory (queue appends compile to shared stores, not generic ones)
+  unsigned char* dyn = dyn_raw + ((1024u - (smem_u32(dyn_raw) & 1023u)) & 1023u);
   unsigned char* stages = dyn;                                        // NST * STAGE_BYTES
   float2* qs = reinterpret_cast<float2*>(dyn + NST * STAGE_BYTES);   // [2][BM][kQCap] queues
+  // 32-entry pools of the per-value path: lane-parallel heaps ([2][KP][BM] float2, slot-major)
+  // and their queues ([2][kHeapQ][BM]) in place of the sorted lists' queues
+  constexpr bool HEAP = MODE == POOL && KP == 32 && !VOTE;
+  float2* hq = reinterpret_cast<float2*>(dyn + NST * STAGE_BYTES + 2 * KP * BM * sizeof(float2));
   __shared__ Bars bars;
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -426,6 +498,9 @@ umma_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
     int my_kind = 0;
     const int qrow = kind * BM + r;
     const int sw = qrow & 31;
+    const uint32_t haddr = smem_u32(dyn + NST * STAGE_BYTES) + (uint32_t)((kind * KP * BM + r) * sizeof(float2));
+    const uint32_t qaddr = smem_u32(hq) + (uint32_t)((kind * kHeapQ * BM + r) * sizeof(float2));
+    float2* const hqp = hq + kind * kHeapQ * BM + r;  // this row's queue, slot s at hqp[s * BM]
     const size_t pbase = ((size_t)blockIdx.y * (CROSS ? 2 : 1) + kind) * a.a_rows * KP;
     float* pv = a.pool_v ? a.pool_v + pbase : nullptr;
     int* pi = a.pool_i ? a.pool_i + pbase : nullptr;
@@ -480,6 +555,14 @@ umma_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
       }
       const int cend = MODE == GPOOL ? g_cend : a.n;  // end of this tile's valid columns
       const int ncol = min(BN, cend - c0);
+      if (MODE == POOL && t == 0 && a.warm && (kind == 0 || CROSS)) {
+        const uint32_t ta = tmem + lane_addr + buf * BN;
+        const float f = (CROSS && kind == 1)
+                            ? warm_floor<KP, true>(ta, c0, ncol, a.n, a.self_excl, my_row, a.cam, my_cam, lane)
+                            : warm_floor<KP, false>(ta, c0, ncol, a.n, a.self_excl, my_row, a.cam, my_cam, lane);
+        me.floor = fmaxf(me.floor, f);
+        me.tau = fmaxf(me.tau, f);
+      }
       // cross-camera pools: the column cameras of chunk ch + 1 are loaded while chunk ch is
       // processed, so one load latency per tile is exposed instead of one per chunk
       int cam_next = 0;
@@ -565,22 +648,65 @@ umma_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
                   }
                 }
               }
-            } else {
-              // Where many scores pass, every value goes through the branch-free append; the
-              // queues are checked every 4 values, so they fill to 28 of 32 slots before a merge
-              // (every 8: 24; measured 2.82 -> 2.73 ms per TF32 launch, every 2 is slower again)
+            } else if (HEAP) {
+              // Per-value path with heap pools: a score that passes goes to the row's queue
+              // (a predicated shared store); every 4 values, if any lane's queue could not take
+              // 4 more, all lanes drain their queues into their heaps. The excluded columns
+              // (past n, and each row itself on the warp's diagonal chunk) are set to -inf once
+              // per chunk; the global pool's warps compare against a camera no column has.
+              if (cb + 32 > a.n || (a.self_excl && cb == r0w)) {
+#pragma unroll
+                for (int c = 0; c < 32; ++c)
+                  if (cb + c >= a.n || (a.self_excl && cb + c == my_row)) v[c] = -CUDART_INF_F;
+              }
+              const int cmp_cam = (CROSS && kind == 1) ? my_cam : -2;
 #pragma unroll
               for (int g = 0; g < 8; ++g) {
-                pool_make_room<KP>(4, lane, me, r0w, kind * BM + quad * 32, qs, pv, pi);
+                if (__any_sync(GCR_FULL, me.qcnt > kHeapQ - 4)) {
+                  const HeapState hs = heap_drain<KP>(haddr, qaddr, me.qcnt, me.len, me.tau, me.floor);
+                  me.tau = hs.tau;
+                  me.len = hs.len;
+                  me.qcnt = 0;
+                }
 #pragma unroll
                 for (int c = 0; c < 4; ++c) {
                   const int cc = g * 4 + c;
-                  const int j = cb + cc;
-                  // the shuffle runs on every lane (a full-mask shuffle must not sit behind a branch)
-                  const int cj = __shfl_sync(GCR_FULL, ccam, cc);
-                  bool ok = j < a.n && !(a.self_excl && j == my_row);
-                  if (CROSS && kind == 1) ok = ok && cj != my_cam;
-                  pool_push(me, v[cc], j, ok, myq, sw);
+                  const int cj = CROSS ? __shfl_sync(GCR_FULL, ccam, cc) : 0;
+                  if (cj != cmp_cam && v[cc] > me.tau) {
+                    hqp[me.qcnt * BM] = make_float2(v[cc], __int_as_float(cb + cc));
+                    ++me.qcnt;
+                  }
+                }
+              }
+            } else {
+              // Where many scores pass, every value goes through the branch-free append; the
+              // queues are checked every 4 values, so they fill to 28 of 32 slots before a merge
+              // (every 8: 24; measured 2.82 -> 2.73 ms per TF32 launch, every 2 is slower again).
+              // The excluded columns (past n, and each row itself on the warp's diagonal chunk)
+              // are set to -inf once per chunk, so the append tests only the score (and, in the
+              // cross-camera warps, the column's camera).
+              if (cb + 32 > a.n || (a.self_excl && cb == r0w)) {
+#pragma unroll
+                for (int c = 0; c < 32; ++c)
+                  if (cb + c >= a.n || (a.self_excl && cb + c == my_row)) v[c] = -CUDART_INF_F;
+              }
+              if (CROSS && kind == 1) {  // warp-uniform
+#pragma unroll
+                for (int g = 0; g < 8; ++g) {
+                  pool_make_room<KP>(4, lane, me, r0w, kind * BM + quad * 32, qs, pv, pi);
+#pragma unroll
+                  for (int c = 0; c < 4; ++c) {
+                    const int cc = g * 4 + c;
+                    const int cj = __shfl_sync(GCR_FULL, ccam, cc);
+                    pool_push(me, v[cc], cb + cc, cj != my_cam, myq, sw);
+                  }
+                }
+              } else {
+#pragma unroll
+                for (int g = 0; g < 8; ++g) {
+                  pool_make_room<KP>(4, lane, me, r0w, kind * BM + quad * 32, qs, pv, pi);
+#pragma unroll
+                  for (int c = 0; c < 4; ++c) pool_push(me, v[g * 4 + c], cb + g * 4 + c, true, myq, sw);
                 }
               }
             }
@@ -638,8 +764,18 @@ umma_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
       if (g_last && (kind == 0 || CROSS))
         pool_flush<KP>(lane, g_valid, me, g_row0 + quad * 32, kind * BM + quad * 32, qs, pv, pi);
     }
-    if (MODE == POOL && (kind == 0 || CROSS) && !*abort_flag)
-      pool_flush<KP>(lane, my_row < a.a_rows, me, blockIdx.x * BM + quad * 32, kind * BM + quad * 32, qs, pv, pi);
+    if (MODE == POOL && (kind == 0 || CROSS) && !*abort_flag) {
+      if (HEAP) {
+        if (__any_sync(GCR_FULL, me.qcnt > 0)) {
+          const HeapState hs = heap_drain<KP>(haddr, qaddr, me.qcnt, me.len, me.tau, me.floor);
+          me.len = hs.len;
+          me.qcnt = 0;
+        }
+        if (my_row < a.a_rows) heap_emit<KP>(haddr, me.len, pv + (size_t)my_row * KP, pi + (size_t)my_row * KP);
+      } else {
+        pool_flush<KP>(lane, my_row < a.a_rows, me, blockIdx.x * BM + quad * 32, kind * BM + quad * 32, qs, pv, pi);
+      }
+    }
   }
   tc_fence_before();
   __syncthreads();
@@ -703,9 +839,10 @@ cudaError_t make_map(CUtensorMap* m, const void* base, Elt elt, int rows, int d,
   return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
 }
 
-size_t smem_bytes(int mode) {
+size_t smem_bytes(int mode, bool heap = false) {
   size_t s = 1024 + (size_t)NST * STAGE_BYTES;
-  if (mode == POOL || mode == GPOOL) s += 2 * BM * kQCap * (sizeof(float) + sizeof(int));
+  if (heap) s += 2 * (32 + kHeapQ) * BM * sizeof(float2);
+  else if (mode == POOL || mode == GPOOL) s += 2 * BM * kQCap * (sizeof(float) + sizeof(int));
   return s;
 }
 
@@ -713,7 +850,7 @@ template <int MODE, int KP, bool CROSS, bool VOTE = false>
 cudaError_t launch(const CUtensorMap& ta, const CUtensorMap& tb, const UmmaArgs& a, dim3 grid, cudaStream_t st,
                    const CUtensorMap* ta2 = nullptr, const CUtensorMap* tb2 = nullptr) {
   auto fn = umma_kernel<MODE, KP, CROSS, VOTE>;
-  const size_t smem = smem_bytes(a.mode);
+  const size_t smem = smem_bytes(a.mode, MODE == POOL && KP == 32 && !VOTE);
   cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   fn<<<grid, CROSS ? 320 : 192, smem, st>>>(ta, tb, ta2 ? *ta2 : ta, tb2 ? *tb2 : tb, a);
@@ -764,6 +901,7 @@ cudaError_t launch_umma_pool(const void* Ab, int na, const void* Bb, int nb, int
   const double cols = (double)std::min(nb, tps * BN);
   const double admit = cols > kp ? kp * (1.0 + std::log(cols / kp)) / cols : 1.0;
   a.vote = (seed != nullptr || admit < 0.006) ? 1 : 0;
+  a.warm = 1;
   dim3 grid((na + BM - 1) / BM, splits);
   if (a.vote) {
     if (kp == 32) return cross ? launch<POOL, 32, true, true>(ta, tb, a, grid, st) : launch<POOL, 32, false, true>(ta, tb, a, grid, st);
