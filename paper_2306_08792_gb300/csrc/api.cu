@@ -109,6 +109,8 @@ struct BuildWs {
   float* anrm;
   float* pool_v;
   int* pool_i;
+  float* tau_x;        // paired GEMM splits: per-row thresholds of the two column halves
+  int* pair_cnt;
   int* unc_count;
   int* unc_row;
   int* unc_kind;
@@ -163,8 +165,12 @@ size_t carve_build(Carve& c, int64_t n, int32_t d, const gcr_params* p, const Re
   t.xr = bf ? c.take<char>(nn * d * es) : nullptr;
   t.enrm = bf ? c.take<float>(nn) : nullptr;
   t.anrm = bf ? c.take<float>(nn) : nullptr;
-  t.pool_v = c.take<float>((size_t)kinds * nn * r.kp);
-  t.pool_i = c.take<int>((size_t)kinds * nn * r.kp);
+  // 32-entry pools on the tensor-core path: room for the two column halves of paired GEMM splits
+  const bool pairable = bf && r.kp == 32;
+  t.pool_v = c.take<float>((size_t)(pairable ? 2 : 1) * kinds * nn * r.kp);
+  t.pool_i = c.take<int>((size_t)(pairable ? 2 : 1) * kinds * nn * r.kp);
+  t.tau_x = pairable ? c.take<float>((size_t)2 * kinds * nn) : nullptr;
+  t.pair_cnt = pairable ? c.take<int>((size_t)kinds * 4 * 2 * ((nn + 255) / 256)) : nullptr;
   t.unc_count = c.take<int>(4);
   t.unc_row = c.take<int>((size_t)kinds * nn);
   t.unc_kind = c.take<int>((size_t)kinds * nn);
@@ -233,7 +239,7 @@ int knn_impl(const float* X, int64_t n64_, int32_t d, const int32_t* cam, const 
     StageScope sc_(GCR_STAGE_SIM_GEMM, st);
     if (bf) {
       GCR_CUDA_TRY(launch_umma_pool(w.xr, n, w.xr, n, d, elt, camp, p->cross_camera != 0, 1, r.kp, 1, w.pool_v,
-                                    w.pool_i, st));
+                                    w.pool_i, st, nullptr, w.tau_x, w.pair_cnt));
     } else {
       GCR_CUDA_TRY(launch_sgemm_pool(X, n, X, n, d, camp, r.kp, p->cross_camera != 0, 1, 1, w.pool_v, w.pool_i, st));
     }

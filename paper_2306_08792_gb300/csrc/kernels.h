@@ -49,9 +49,14 @@ cudaError_t launch_sgemm_dist(const float* Xq, int nq, const float* Xg, int ng, 
 // seed (may be NULL): per row of A an admission floor; every split keeps only scores above it,
 // so a merged pool may hold fewer than kp entries, and every score left out of it is <= the
 // floor or <= its last entry.
+// tau_x ([2][kinds][na] floats) and pair_cnt ([2 ceil(na / 256)][kinds][4] ints), both may be
+// NULL: for 32-entry pools without a seed and with splits = 1, where one 128-row A block per SM
+// would not fit in half the L2, two CTAs sweep the two column halves of each row block; pool_v
+// and pool_i then need room for two [kind][na][kp] regions, and the pools end in the first.
 cudaError_t launch_umma_pool(const void* Ab, int na, const void* Bb, int nb, int d, Elt elt,
                              const int* cam, bool cross, int self_excl, int kp, int splits, float* pool_v,
-                             int* pool_i, cudaStream_t st, const float* seed = nullptr);
+                             int* pool_i, cudaStream_t st, const float* seed = nullptr, float* tau_x = nullptr,
+                             int* pair_cnt = nullptr);
 // Pools of row blocks of the gathered matrix Y (rows x d, rounded operand) against column ranges
 // of Y: work item w = {first row, rows <= 128, first column, columns} of *n_items (<= max_items);
 // pool entry (s - col_bias[j], j), j a position in Y; column j == row skipped when self_excl;

@@ -260,4 +260,47 @@ __device__ __noinline__ void heap_emit(uint32_t haddr, int len, float* lv, int* 
   }
 }
 
+// Paired column splits: the row's sorted list in this CTA's heap slots (own, best first, len
+// entries; slot e at own[e * 128]) merged with the other half's list (KP entries, best first,
+// padded with (-inf, -1), read through L2) into the KP best, written to (dv, di). The other
+// list is first copied to the scratch slots (same layout), so that dv may be the other list
+// itself. Each entry goes straight to its rank: its index in its own list plus the number of
+// entries of the other list that rank before it (a binary search; better() orders the two
+// lists' entries totally, so the ranks of all entries are distinct).
+template <int KP>
+__device__ __forceinline__ void pair_merge_lists(const float2* own, int len, const float* ov, const int* oi,
+                                                 float2* scratch, float* dv, int* di) {
+  for (int e = 0; e < KP; ++e) scratch[e * 128] = make_float2(__ldcg(ov + e), __int_as_float(__ldcg(oi + e)));
+  for (int i = 0; i < len; ++i) {
+    const float2 x = own[i * 128];
+    const int xi = __float_as_int(x.y);
+    int lo = 0, hi = KP;  // others before x: the first j with other[j] not better than x
+    while (lo < hi) {
+      const int mid = (lo + hi) >> 1;
+      const float2 y = scratch[mid * 128];
+      if (better(y.x, __float_as_int(y.y), x.x, xi)) lo = mid + 1;
+      else hi = mid;
+    }
+    if (i + lo < KP) {
+      dv[i + lo] = x.x;
+      di[i + lo] = xi;
+    }
+  }
+  for (int j = 0; j < KP; ++j) {
+    const float2 y = scratch[j * 128];
+    const int yi = __float_as_int(y.y);
+    int lo = 0, hi = len;  // own entries before y
+    while (lo < hi) {
+      const int mid = (lo + hi) >> 1;
+      const float2 x = own[mid * 128];
+      if (better(x.x, __float_as_int(x.y), y.x, yi)) lo = mid + 1;
+      else hi = mid;
+    }
+    if (j + lo < KP) {
+      dv[j + lo] = y.x;
+      di[j + lo] = yi;
+    }
+  }
+}
+
 }  // namespace gcr

@@ -130,6 +130,30 @@ __device__ __forceinline__ void umma_commit(uint64_t* bar) {
   asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
                : "memory");
 }
+// 2-CTA clusters sharing B tiles: the commit arrives on the barrier at the same offset in every
+// CTA of the mask; the load writes the tile (and completes its bytes on the barrier) at the same
+// offsets in every CTA of the mask.
+__device__ __forceinline__ void umma_commit_mc(uint64_t* bar, uint16_t mask) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64 [%0], %1;"
+               ::"r"(smem_u32(bar)), "h"(mask)
+               : "memory");
+}
+__device__ __forceinline__ void tma_load_2d_mc(void* dst, const CUtensorMap* map, uint64_t* bar, int x, int y,
+                                               uint16_t mask) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes.multicast::cluster"
+      " [%0], [%1, {%3, %4}], [%2], %5;"
+      ::"r"(smem_u32(dst)), "l"(reinterpret_cast<uint64_t>(map)), "r"(smem_u32(bar)), "r"(x), "r"(y), "h"(mask)
+      : "memory");
+}
+__device__ __forceinline__ void cluster_sync_all() {
+  asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+__device__ __forceinline__ uint32_t cluster_rank() {
+  uint32_t r;
+  asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+  return r;
+}
 // Asynchronous TMEM load of 32 columns (one accumulator row per thread) ...
 __device__ __forceinline__ void tmem_ld32_async(uint32_t taddr, uint32_t (&r)[32]) {
   asm volatile(
@@ -216,6 +240,20 @@ struct UmmaArgs {
   int vote;        // POOL: pick the kernel that skips groups of four scores below every row's
                    // threshold by a vote (GPOOL always does)
   int warm;        // POOL: admission floors from each row's first column tile (warm_floor)
+  // POOL with heap pools, paired splits: two CTAs per row block (grid.x = the 2 column splits,
+  // grid.y = row blocks, so both halves of a block run at the same time and the row blocks at
+  // work stay few enough for their A rows to stay in L2). Each writes its rows' thresholds to
+  // tau_x after every tile and raises its own to the other's (a threshold of either half is a
+  // score with KP of the row's scores at or above it); the warp that finishes second merges the
+  // two lists into the first split's pools.
+  int pair;
+  float* tau_x;    // [2][pools][a_rows], NaN-initialised (no threshold yet)
+  int* pair_cnt;   // [row blocks][pools][4], zero-initialised: finished warps per (block, pool, quad)
+  // POOL with heap pools: 2-CTA clusters of consecutive row blocks that take the same column
+  // tiles; each CTA loads its A block and one half of the B tile, and the half goes to both
+  // CTAs by TMA multicast (tmB2: B in 128-row boxes), so a CTA reads two thirds of the bytes
+  // per stage. Each MMA commit frees the stage in both CTAs (empty barriers count 2 arrivals).
+  int mc;
 };
 
 struct __align__(8) Bars {
@@ -255,14 +293,15 @@ struct ItemCursor {
 template <int MODE>
 struct Tiles {
   int count;
+  int rb, split;  // POOL: row block and column split of this CTA
   __device__ int row0(const UmmaArgs& a, int t) const {
-    if (MODE == POOL) return blockIdx.x * BM;
+    if (MODE == POOL) return rb * BM;
     if (MODE == GRAM || MODE == MUL) return blockIdx.y * BM;
     if (MODE == BAND) return (blockIdx.y + t * gridDim.y) * BM;  // row tiles strided over grid.y
     return (((int)blockIdx.x + t * (int)gridDim.x) % a.dist_nrb) * BM;
   }
   __device__ int col0(const UmmaArgs& a, int t) const {
-    if (MODE == POOL) return (blockIdx.y * a.tps + t) * BN;
+    if (MODE == POOL) return (split * a.tps + t) * BN;
     if (MODE == GRAM || MODE == MUL) return blockIdx.x * BN;
     if (MODE == BAND) return blockIdx.x * BN;
     return (((int)blockIdx.x + t * (int)gridDim.x) / a.dist_nrb) * BN;
@@ -362,13 +401,15 @@ umma_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
   const int mul_b0 = MODE == MUL ? max(0, a.mul_rowcam[blockIdx.y]) * a.n : 0;
 
   Tiles<MODE> tl;
+  tl.rb = (MODE == POOL && a.pair) ? (int)blockIdx.y : (int)blockIdx.x;
+  tl.split = (MODE == POOL && a.pair) ? (int)blockIdx.x : (int)blockIdx.y;
   int nitems = 0;
   if (MODE == GPOOL) {
     nitems = *a.n_items;
     if ((int)blockIdx.x >= nitems) return;  // nothing to do: leave before any barrier or TMEM use
     tl.count = 0;
     for (int it = blockIdx.x; it < nitems; it += gridDim.x) tl.count += (a.items[it].w + BN - 1) / BN;
-  } else if (MODE == POOL) tl.count = max(0, min(a.tps, (a.n + BN - 1) / BN - (int)blockIdx.y * a.tps));
+  } else if (MODE == POOL) tl.count = max(0, min(a.tps, (a.n + BN - 1) / BN - tl.split * a.tps));
   else if (MODE == BAND) {
     const int U = min(*a.count, a.cap);
     const int tiles = (U + BM - 1) / BM;
@@ -386,7 +427,7 @@ umma_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
   if (threadIdx.x == 0) {
     for (int s = 0; s < NST; ++s) {
       mbar_init(&bars.full[s], 1);
-      mbar_init(&bars.empty[s], 1);
+      mbar_init(&bars.empty[s], (MODE == POOL && a.mc) ? 2 : 1);
     }
     const int epi_warps = CROSS ? 8 : 4;
     for (int b = 0; b < 2; ++b) {
@@ -405,6 +446,8 @@ umma_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
+  // clusters: every barrier of both CTAs is initialised before either CTA signals the other's
+  if (MODE == POOL && a.mc) cluster_sync_all();
   const uint32_t tmem = bars.tmem_base;
   volatile int* abort_flag = &bars.abort_flag;
 
@@ -436,7 +479,13 @@ umma_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
             tma_load_2d(sa + A_BYTES, pass == 1 ? &tmB2 : &tmB, &bars.full[s], x, mul_b0 + c0);
           } else {
             tma_load_2d(sa, &tmA, &bars.full[s], kb * bk, r0);
-            tma_load_2d(sa + A_BYTES, &tmB, &bars.full[s], kb * bk, c0);
+            if (MODE == POOL && a.mc) {
+              const uint32_t cr = cluster_rank();
+              tma_load_2d_mc(sa + A_BYTES + cr * (B_BYTES / 2), &tmB2, &bars.full[s], kb * bk,
+                             c0 + (int)cr * (BN / 2), (uint16_t)0x3);
+            } else {
+              tma_load_2d(sa + A_BYTES, &tmB, &bars.full[s], kb * bk, c0);
+            }
           }
         }
       }
@@ -475,7 +524,8 @@ umma_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
 #pragma unroll
             for (int k = 0; k < 4; ++k) umma_bf16(dcol, ad + (uint64_t)(2 * k), bd + (uint64_t)(2 * k), (kb | k) != 0);
           }
-          umma_commit(&bars.empty[s]);
+          if (MODE == POOL && a.mc) umma_commit_mc(&bars.empty[s], (uint16_t)0x3);
+          else umma_commit(&bars.empty[s]);
         }
         if (ok) umma_commit(&bars.tfull[buf]);
       }
@@ -501,11 +551,11 @@ umma_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
     const uint32_t haddr = smem_u32(dyn + NST * STAGE_BYTES) + (uint32_t)((kind * KP * BM + r) * sizeof(float2));
     const uint32_t qaddr = smem_u32(hq) + (uint32_t)((kind * kHeapQ * BM + r) * sizeof(float2));
     float2* const hqp = hq + kind * kHeapQ * BM + r;  // this row's queue, slot s at hqp[s * BM]
-    const size_t pbase = ((size_t)blockIdx.y * (CROSS ? 2 : 1) + kind) * a.a_rows * KP;
+    const size_t pbase = ((size_t)tl.split * (CROSS ? 2 : 1) + kind) * a.a_rows * KP;
     float* pv = a.pool_v ? a.pool_v + pbase : nullptr;
     int* pi = a.pool_i ? a.pool_i + pbase : nullptr;
     if (MODE == POOL) {
-      my_row = blockIdx.x * BM + r;
+      my_row = tl.rb * BM + r;
       const bool valid = my_row < a.a_rows;
       pool_init(me, valid, (valid && a.seed) ? a.seed[my_row] : -CUDART_INF_F);
       if (CROSS && valid) my_cam = a.cam[my_row];
@@ -514,9 +564,14 @@ umma_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
     if (MODE == GPOOL) cur.start(a, nitems);
     bool g_valid = false;        // GPOOL: this thread's row belongs to the current item
     int g_row0 = 0, g_cend = 0;  // GPOOL: first row of the item, end of its columns
+    // paired splits: this row's threshold in the other half's sweep (read before the wait)
+    const bool pair_row = HEAP && a.pair && (kind == 0 || CROSS) && my_row < a.a_rows;
+    const size_t tx_mine = ((size_t)tl.split * (CROSS ? 2 : 1) + kind) * a.a_rows + (pair_row ? my_row : 0);
+    const size_t tx_other = ((size_t)(tl.split ^ 1) * (CROSS ? 2 : 1) + kind) * a.a_rows + (pair_row ? my_row : 0);
     for (int t = 0; t < tl.count; ++t) {
       const int buf = t & 1;
       const uint32_t use = t >> 1;
+      const float tau_other = pair_row ? __ldcg(a.tau_x + tx_other) : CUDART_NAN_F;
       if (!mbar_wait(&bars.tfull[buf], use & 1, abort_flag)) break;
       tc_fence_after();
       const int r0 = MODE == GPOOL ? cur.w.x : tl.row0(a, t);
@@ -562,6 +617,10 @@ umma_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
                             : warm_floor<KP, false>(ta, c0, ncol, a.n, a.self_excl, my_row, a.cam, my_cam, lane);
         me.floor = fmaxf(me.floor, f);
         me.tau = fmaxf(me.tau, f);
+      }
+      if (pair_row) {  // fmaxf ignores the NaN of a threshold not yet written
+        me.floor = fmaxf(me.floor, tau_other);
+        me.tau = fmaxf(me.tau, tau_other);
       }
       // cross-camera pools: the column cameras of chunk ch + 1 are loaded while chunk ch is
       // processed, so one load latency per tile is exposed instead of one per chunk
@@ -619,7 +678,7 @@ umma_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
             int ccam = 0;
             if (CROSS && kind == 1) ccam = cam_cur;
             float2* myq = qs + qrow * kQCap;
-            const int r0w = blockIdx.x * BM + quad * 32;  // first row of this warp
+            const int r0w = tl.rb * BM + quad * 32;  // first row of this warp
             if (VOTE) {
               // Where few scores pass (a long sweep for the pool size, or admission floors),
               // most groups of four fall below every row's threshold: one vote over the warp
@@ -761,6 +820,7 @@ umma_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
       tc_fence_before();
       __syncwarp();
       if (lane == 0) mbar_arrive(&bars.tempty[buf]);
+      if (pair_row) __stcg(a.tau_x + tx_mine, me.tau);
       if (g_last && (kind == 0 || CROSS))
         pool_flush<KP>(lane, g_valid, me, g_row0 + quad * 32, kind * BM + quad * 32, qs, pv, pi);
     }
@@ -772,13 +832,35 @@ umma_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
           me.qcnt = 0;
         }
         if (my_row < a.a_rows) heap_emit<KP>(haddr, me.len, pv + (size_t)my_row * KP, pi + (size_t)my_row * KP);
+        if (a.pair) {
+          // the list is written: make it visible, count this warp, and merge if it is second
+          // (the stage buffers are idle by now and hold the other half's lists)
+          __threadfence();
+          __syncwarp();
+          int prev = 0;
+          if (lane == 0) prev = atomicAdd(a.pair_cnt + ((size_t)tl.rb * (CROSS ? 2 : 1) + kind) * 4 + quad, 1);
+          prev = __shfl_sync(GCR_FULL, prev, 0);
+          if (prev == 1) {
+            __threadfence();
+            const size_t ro = ((size_t)(tl.split ^ 1) * (CROSS ? 2 : 1) + kind) * a.a_rows * KP;  // the other half
+            const size_t r0s = (size_t)kind * a.a_rows * KP;                                   // split 0's pools
+            const float2* own = reinterpret_cast<const float2*>(dyn + NST * STAGE_BYTES) + kind * KP * BM + r;
+            float2* scratch = reinterpret_cast<float2*>(stages) + kind * KP * BM + r;
+            if (my_row < a.a_rows)
+              pair_merge_lists<KP>(own, me.len, a.pool_v + ro + (size_t)my_row * KP, a.pool_i + ro + (size_t)my_row * KP,
+                                   scratch, a.pool_v + r0s + (size_t)my_row * KP, a.pool_i + r0s + (size_t)my_row * KP);
+          }
+        }
       } else {
-        pool_flush<KP>(lane, my_row < a.a_rows, me, blockIdx.x * BM + quad * 32, kind * BM + quad * 32, qs, pv, pi);
+        pool_flush<KP>(lane, my_row < a.a_rows, me, tl.rb * BM + quad * 32, kind * BM + quad * 32, qs, pv, pi);
       }
     }
   }
   tc_fence_before();
   __syncthreads();
+  // clusters: neither CTA leaves while the other may still signal its barriers (its MMAs have
+  // drained by now) or write its stages
+  if (MODE == POOL && a.mc) cluster_sync_all();
   if (warp == 1) {
     __syncwarp();
     tc_fence_after();
@@ -848,13 +930,28 @@ size_t smem_bytes(int mode, bool heap = false) {
 
 template <int MODE, int KP, bool CROSS, bool VOTE = false>
 cudaError_t launch(const CUtensorMap& ta, const CUtensorMap& tb, const UmmaArgs& a, dim3 grid, cudaStream_t st,
-                   const CUtensorMap* ta2 = nullptr, const CUtensorMap* tb2 = nullptr) {
+                   const CUtensorMap* ta2 = nullptr, const CUtensorMap* tb2 = nullptr, dim3 cluster = dim3(1, 1, 1)) {
   auto fn = umma_kernel<MODE, KP, CROSS, VOTE>;
   const size_t smem = smem_bytes(a.mode, MODE == POOL && KP == 32 && !VOTE);
   cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  fn<<<grid, CROSS ? 320 : 192, smem, st>>>(ta, tb, ta2 ? *ta2 : ta, tb2 ? *tb2 : tb, a);
-  return cudaGetLastError();
+  if (cluster.x * cluster.y * cluster.z == 1) {
+    fn<<<grid, CROSS ? 320 : 192, smem, st>>>(ta, tb, ta2 ? *ta2 : ta, tb2 ? *tb2 : tb, a);
+    return cudaGetLastError();
+  }
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = dim3(CROSS ? 320 : 192, 1, 1);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeClusterDimension;
+  at[0].val.clusterDim.x = cluster.x;
+  at[0].val.clusterDim.y = cluster.y;
+  at[0].val.clusterDim.z = cluster.z;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, fn, ta, tb, ta2 ? *ta2 : ta, tb2 ? *tb2 : tb, a);
 }
 
 }  // namespace
@@ -873,13 +970,31 @@ int umma_read_and_clear_timeouts() {
 
 cudaError_t launch_umma_pool(const void* Ab, int na, const void* Bb, int nb, int d, Elt elt,
                              const int* cam, bool cross, int self_excl, int kp, int splits, float* pool_v,
-                             int* pool_i, cudaStream_t st, const float* seed) {
+                             int* pool_i, cudaStream_t st, const float* seed, float* tau_x, int* pair_cnt) {
   CUtensorMap ta, tb;
   cudaError_t e = make_map(&ta, Ab, elt, na, d, BM);
   if (e != cudaSuccess) return e;
   e = make_map(&tb, Bb, elt, nb, d, BN);
   if (e != cudaSuccess) return e;
   const int ntiles = (nb + BN - 1) / BN;
+  const int rblocks = (na + BM - 1) / BM;
+  // Paired splits (heap pools only) where the A blocks of one CTA per SM would not fit in half
+  // the L2: each CTA re-reads its A block for every column tile, and 151 blocks of 128 x 2048
+  // TF32 rows (151 MB) would otherwise come from DRAM every time.
+  int l2 = 0, nsm = 0, dev = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&l2, cudaDevAttrL2CacheSize, dev);
+  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  const double live_a = (double)std::min(rblocks, std::max(nsm, 1)) * BM * d * (double)elt_bytes(elt);
+  // expected share of a split's scores that enter a row's pool, in random order: about
+  // kp (1 + ln(columns / kp)) / columns; a vote pays where that is small (or with floors)
+  auto admit_share = [&](int tiles_per_split) {
+    const double cols = (double)std::min(nb, tiles_per_split * BN);
+    return cols > kp ? kp * (1.0 + std::log(cols / kp)) / cols : 1.0;
+  };
+  const bool pair = kp == 32 && !seed && tau_x && pair_cnt && splits <= 1 && ntiles >= 2 && l2 > 0 &&
+                    live_a > 0.5 * l2 && admit_share((ntiles + 1) / 2) >= 0.006;
+  if (pair) splits = 2;
   if (splits < 1) splits = 1;
   if (splits > ntiles) splits = ntiles;
   const int tps = (ntiles + splits - 1) / splits;
@@ -896,13 +1011,37 @@ cudaError_t launch_umma_pool(const void* Ab, int na, const void* Bb, int nb, int
   a.pool_v = pool_v;
   a.pool_i = pool_i;
   a.seed = seed;
-  // expected share of a split's scores that enter a row's pool, in random order: about
-  // kp (1 + ln(columns / kp)) / columns; a vote pays where that is small (or with floors)
-  const double cols = (double)std::min(nb, tps * BN);
-  const double admit = cols > kp ? kp * (1.0 + std::log(cols / kp)) / cols : 1.0;
-  a.vote = (seed != nullptr || admit < 0.006) ? 1 : 0;
+  a.vote = (seed != nullptr || admit_share(tps) < 0.006) ? 1 : 0;
   a.warm = 1;
-  dim3 grid((na + BM - 1) / BM, splits);
+  dim3 grid(rblocks, splits);
+  // heap pools: 2-CTA clusters over row blocks (an even count: a last block past na has no
+  // rows and only loads its half of the shared B tiles)
+  const bool heap = kp == 32 && !a.vote;
+  const int rb_grid = heap ? (rblocks + 1) & ~1 : rblocks;
+  CUtensorMap tb_half;
+  dim3 cluster(1, 1, 1);
+  if (heap) {
+    e = make_map(&tb_half, Bb, elt, nb, d, BN / 2);
+    if (e != cudaSuccess) return e;
+    a.mc = 1;
+    grid = dim3(rb_grid, splits);
+    cluster = dim3(2, 1, 1);
+  }
+  if (pair) {  // no vote: the admission share was checked for these splits
+    const int pools = cross ? 2 : 1;
+    cudaError_t e2 = cudaMemsetAsync(tau_x, 0xFF, sizeof(float) * 2 * pools * (size_t)na, st);  // NaN
+    if (e2 == cudaSuccess) e2 = cudaMemsetAsync(pair_cnt, 0, sizeof(int) * (size_t)rb_grid * pools * 4, st);
+    if (e2 != cudaSuccess) return e2;
+    a.pair = 1;
+    a.tau_x = tau_x;
+    a.pair_cnt = pair_cnt;
+    grid = dim3(2, rb_grid);
+    cluster = dim3(1, 2, 1);
+  }
+  if (heap) {
+    return cross ? launch<POOL, 32, true>(ta, tb, a, grid, st, nullptr, &tb_half, cluster)
+                 : launch<POOL, 32, false>(ta, tb, a, grid, st, nullptr, &tb_half, cluster);
+  }
   if (a.vote) {
     if (kp == 32) return cross ? launch<POOL, 32, true, true>(ta, tb, a, grid, st) : launch<POOL, 32, false, true>(ta, tb, a, grid, st);
     if (kp == 64) return cross ? launch<POOL, 64, true, true>(ta, tb, a, grid, st) : launch<POOL, 64, false, true>(ta, tb, a, grid, st);

@@ -86,6 +86,24 @@ def test_knn_cross_camera(gcr, precision, pool):
     assert np.all(w.cam[nc] != w.cam[:, None])
 
 
+def test_knn_paired_splits_all_rows(gcr):
+    """TF32 with 32-entry pools at a size where one 128-row block of d = 2048 per SM would not fit
+    in half the L2 (8,900 rows: 70 row blocks, 73 MB), so two CTAs sweep the two column halves of
+    each block (35 column tiles: 18 + 17, a ragged last tile and a ragged last row block) and
+    merge their pools; every row's global and cross-camera kNN sets against the FP64 oracle."""
+    w = workloads.crosscam(seed=21, n_query=900, n_gallery=8000, d=2048, n_clusters=350)
+    X0 = gcr.gcr_normalize(_dev(w.X))
+    cam = _dev(w.cam, torch.int32)
+    p = gcr.default_params(k=w.k, cross_camera=1, alpha=0.7, precision="tf32")
+    G = gcr.gcr_build_graph(X0, p, cam)
+    torch.cuda.synchronize()
+    X64 = X0.double().cpu().numpy()
+    r = parity.compare_knn(X64, np.arange(w.n), G.nbr.cpu().numpy(), w.k)
+    rc = parity.compare_knn(X64, np.arange(w.n), G.nbr_cr.cpu().numpy(), w.k, w.cam, cross=True)
+    assert r["mismatched"] == 0 and rc["mismatched"] == 0, (r, rc)
+    assert G.stats_dict()["band_failed"] == 0
+
+
 EDGE = [("fp32", 1, 8, 5), ("fp32", 5, 12, 10), ("fp32", 130, 68, 7), ("fp32", 300, 256, 0),
         ("fp32", 257, 36, 31), ("bf16", 1, 8, 5), ("bf16", 5, 16, 10), ("bf16", 130, 72, 7),
         ("bf16", 300, 256, 0), ("bf16", 257, 40, 31), ("bf16", 600, 200, 63), ("tf32", 1, 8, 5),
