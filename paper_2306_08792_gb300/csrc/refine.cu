@@ -153,26 +153,42 @@ __device__ __forceinline__ void sort32_d(double& s, int& i, double& v, int lane)
 // slice (elements v*128 + lane*4 .. +3) again, from L1 after the first time.
 
 // FP32 dots of x_i with up to 4 rows (j < 0: skipped); sequential per-lane chain then butterfly.
+// The four rows' next 128-column slices are loaded while the current ones are multiplied, so a
+// lane keeps eight 16-byte loads of rows j in flight (the rescoring is bound by the latency of
+// these L2 gathers, not by their bandwidth).
 template <int VPL>
 __device__ __forceinline__ void dot4_f32(const float* __restrict__ X, int d, const float* __restrict__ xrow,
                                          const int (&j)[4], int lane, float (&out)[4]) {
   float acc[4] = {0.f, 0.f, 0.f, 0.f};
+  const float* rp[4];
+#pragma unroll
+  for (int t = 0; t < 4; ++t) rp[t] = X + (size_t)(j[t] >= 0 ? j[t] : 0) * d + lane * 4;
+  const float4 zero = make_float4(0.f, 0.f, 0.f, 0.f);
+  float4 cur[4];
+#pragma unroll
+  for (int t = 0; t < 4; ++t) cur[t] = (j[t] >= 0 && lane * 4 < d) ? *reinterpret_cast<const float4*>(rp[t]) : zero;
 #pragma unroll
   for (int v = 0; v < VPL; ++v) {
     const int off = v * 128 + lane * 4;
+    float4 nxt[4];
+#pragma unroll
+    for (int t = 0; t < 4; ++t)
+      nxt[t] = (v + 1 < VPL && j[t] >= 0 && off + 128 < d) ? *reinterpret_cast<const float4*>(rp[t] + (v + 1) * 128)
+                                                            : zero;
     if (off < d) {
       const float4 xv = *reinterpret_cast<const float4*>(xrow + off);
 #pragma unroll
       for (int t = 0; t < 4; ++t) {
         if (j[t] >= 0) {
-          const float4 y = *reinterpret_cast<const float4*>(X + (size_t)j[t] * d + off);
-          acc[t] = fmaf(xv.x, y.x, acc[t]);
-          acc[t] = fmaf(xv.y, y.y, acc[t]);
-          acc[t] = fmaf(xv.z, y.z, acc[t]);
-          acc[t] = fmaf(xv.w, y.w, acc[t]);
+          acc[t] = fmaf(xv.x, cur[t].x, acc[t]);
+          acc[t] = fmaf(xv.y, cur[t].y, acc[t]);
+          acc[t] = fmaf(xv.z, cur[t].z, acc[t]);
+          acc[t] = fmaf(xv.w, cur[t].w, acc[t]);
         }
       }
     }
+#pragma unroll
+    for (int t = 0; t < 4; ++t) cur[t] = nxt[t];
   }
 #pragma unroll
   for (int t = 0; t < 4; ++t) out[t] = warp_sum(acc[t]);
