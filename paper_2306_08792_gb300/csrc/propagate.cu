@@ -44,6 +44,31 @@ __global__ void __launch_bounds__(256) propagate_kernel(const int* __restrict__ 
       const float wt = e < L ? val[beg + e] : 0.f;
       const int m = min(32, L - e0);
       int t = 0;
+      // four entries at a time: their slices are all loaded before any is multiplied, so a lane
+      // keeps 4 * VW gathers in flight (the layer is bound by the latency of these gathers);
+      // each output element still adds the entries in the operator's order
+      for (; t + 4 <= m; t += 4) {
+        float4 xa[4][VW];
+        float wa[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const int cu = __shfl_sync(GCR_FULL, c, t + u);
+          wa[u] = __shfl_sync(GCR_FULL, wt, t + u);
+          const float* ru = X_in + (size_t)cu * d;
+#pragma unroll
+          for (int v = 0; v < VW; ++v) {
+            const int off = base + v * 128;
+            xa[u][v] = off < d ? *reinterpret_cast<const float4*>(ru + off) : make_float4(0.f, 0.f, 0.f, 0.f);
+          }
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+#pragma unroll
+          for (int v = 0; v < VW; ++v) {
+            acc[v].x = fmaf(wa[u], xa[u][v].x, acc[v].x); acc[v].y = fmaf(wa[u], xa[u][v].y, acc[v].y);
+            acc[v].z = fmaf(wa[u], xa[u][v].z, acc[v].z); acc[v].w = fmaf(wa[u], xa[u][v].w, acc[v].w);
+          }
+      }
       for (; t + 2 <= m; t += 2) {
         const int c0 = __shfl_sync(GCR_FULL, c, t), c1 = __shfl_sync(GCR_FULL, c, t + 1);
         const float w0 = __shfl_sync(GCR_FULL, wt, t), w1 = __shfl_sync(GCR_FULL, wt, t + 1);

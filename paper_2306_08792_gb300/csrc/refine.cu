@@ -155,7 +155,8 @@ __device__ __forceinline__ void sort32_d(double& s, int& i, double& v, int lane)
 // FP32 dots of x_i with up to 4 rows (j < 0: skipped); sequential per-lane chain then butterfly.
 // The four rows' next 128-column slices are loaded while the current ones are multiplied, so a
 // lane keeps eight 16-byte loads of rows j in flight (the rescoring is bound by the latency of
-// these L2 gathers, not by their bandwidth).
+// these L2 gathers, not by their bandwidth). The rows are read through L2 only, so that they do
+// not evict x_i, which every dot product reads from L1.
 template <int VPL>
 __device__ __forceinline__ void dot4_f32(const float* __restrict__ X, int d, const float* __restrict__ xrow,
                                          const int (&j)[4], int lane, float (&out)[4]) {
@@ -166,14 +167,14 @@ __device__ __forceinline__ void dot4_f32(const float* __restrict__ X, int d, con
   const float4 zero = make_float4(0.f, 0.f, 0.f, 0.f);
   float4 cur[4];
 #pragma unroll
-  for (int t = 0; t < 4; ++t) cur[t] = (j[t] >= 0 && lane * 4 < d) ? *reinterpret_cast<const float4*>(rp[t]) : zero;
+  for (int t = 0; t < 4; ++t) cur[t] = (j[t] >= 0 && lane * 4 < d) ? __ldcg(reinterpret_cast<const float4*>(rp[t])) : zero;
 #pragma unroll
   for (int v = 0; v < VPL; ++v) {
     const int off = v * 128 + lane * 4;
     float4 nxt[4];
 #pragma unroll
     for (int t = 0; t < 4; ++t)
-      nxt[t] = (v + 1 < VPL && j[t] >= 0 && off + 128 < d) ? *reinterpret_cast<const float4*>(rp[t] + (v + 1) * 128)
+      nxt[t] = (v + 1 < VPL && j[t] >= 0 && off + 128 < d) ? __ldcg(reinterpret_cast<const float4*>(rp[t] + (v + 1) * 128))
                                                             : zero;
     if (off < d) {
       const float4 xv = *reinterpret_cast<const float4*>(xrow + off);
