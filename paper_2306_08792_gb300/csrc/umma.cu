@@ -35,7 +35,8 @@ namespace {
 constexpr int BM = 128;            // rows of A per tile (UMMA M)
 constexpr int BN = 256;            // rows of B per tile (UMMA N)
 constexpr int BKB = 128;           // K bytes per stage (one swizzle row): 64 BF16 / 32 TF32
-constexpr int NST = 3;             // pipeline stages
+constexpr int NST = 3;             // pipeline stages of the modes with pool queues (POOL, GPOOL)
+constexpr int NST_MAX = 4;         // the others (no queues in shared memory)
 constexpr int A_BYTES = BM * BKB;
 constexpr int B_BYTES = BN * BKB;
 constexpr int STAGE_BYTES = A_BYTES + B_BYTES;
@@ -257,8 +258,8 @@ struct UmmaArgs {
 };
 
 struct __align__(8) Bars {
-  uint64_t full[NST];
-  uint64_t empty[NST];
+  uint64_t full[NST_MAX];
+  uint64_t empty[NST_MAX];
   uint64_t tfull[2];
   uint64_t tempty[2];
   uint64_t drain;
@@ -384,12 +385,13 @@ umma_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
   // aligned by an offset from the shared array itself, so that every pointer derived from it
   // stays known as shared memory (queue appends compile to shared stores, not generic ones)
   unsigned char* dyn = dyn_raw + ((1024u - (smem_u32(dyn_raw) & 1023u)) & 1023u);
-  unsigned char* stages = dyn;                                        // NST * STAGE_BYTES
-  float2* qs = reinterpret_cast<float2*>(dyn + NST * STAGE_BYTES);   // [2][BM][kQCap] queues
+  constexpr int NS = (MODE == POOL || MODE == GPOOL) ? NST : NST_MAX;  // ring stages
+  unsigned char* stages = dyn;                                        // NS * STAGE_BYTES
+  float2* qs = reinterpret_cast<float2*>(dyn + NS * STAGE_BYTES);    // [2][BM][kQCap] queues
   // 32-entry pools of the per-value path: lane-parallel heaps ([2][KP][BM] float2, slot-major)
   // and their queues ([2][kHeapQ][BM]) in place of the sorted lists' queues
   constexpr bool HEAP = MODE == POOL && KP == 32 && !VOTE;
-  float2* hq = reinterpret_cast<float2*>(dyn + NST * STAGE_BYTES + 2 * KP * BM * sizeof(float2));
+  float2* hq = reinterpret_cast<float2*>(dyn + NS * STAGE_BYTES + 2 * KP * BM * sizeof(float2));
   __shared__ Bars bars;
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -425,7 +427,7 @@ umma_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
   }
 
   if (threadIdx.x == 0) {
-    for (int s = 0; s < NST; ++s) {
+    for (int s = 0; s < NS; ++s) {
       mbar_init(&bars.full[s], 1);
       mbar_init(&bars.empty[s], (MODE == POOL && a.mc) ? 2 : 1);
     }
@@ -462,8 +464,8 @@ umma_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
         const int c0 = MODE == GPOOL ? cur.w.z + cur.ct * BN : tl.col0(a, t);
         if (MODE == GPOOL) cur.advance(a, nitems);
         for (int kb = 0; kb < kb_count; ++kb, ++it) {
-          const int s = it % NST;
-          const uint32_t round = it / NST;
+          const int s = it % NS;
+          const uint32_t round = it / NS;
           if (!mbar_wait(&bars.empty[s], (round & 1) ^ 1, abort_flag)) break;
           unsigned char* sa = stages + s * STAGE_BYTES;
           mbar_arrive_expect_tx(&bars.full[s], STAGE_BYTES);
@@ -491,10 +493,10 @@ umma_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
       }
       // in-flight loads land before the CTA can exit: wait for the last armed stages
       if (*abort_flag) {
-        for (int back = 1; back <= NST && back <= it; ++back) {
+        for (int back = 1; back <= NS && back <= it; ++back) {
           const int j = it - back;
           const unsigned long long t0 = globaltimer();
-          while (!mbar_try_wait(&bars.full[j % NST], (j / NST) & 1) && globaltimer() - t0 < kTimeoutNs) {
+          while (!mbar_try_wait(&bars.full[j % NS], (j / NS) & 1) && globaltimer() - t0 < kTimeoutNs) {
           }
         }
       }
@@ -511,8 +513,8 @@ umma_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
         tc_fence_after();
         const uint32_t dcol = tmem + buf * BN;
         for (int kb = 0; kb < kb_count; ++kb, ++it) {
-          const int s = it % NST;
-          if (!mbar_wait(&bars.full[s], (it / NST) & 1, abort_flag)) { ok = false; break; }
+          const int s = it % NS;
+          if (!mbar_wait(&bars.full[s], (it / NS) & 1, abort_flag)) { ok = false; break; }
           tc_fence_after();
           const uint32_t sa = smem_u32(stages + s * STAGE_BYTES);
           const uint64_t ad = smem_desc(sa), bd = smem_desc(sa + A_BYTES);
@@ -548,7 +550,7 @@ umma_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
     int my_kind = 0;
     const int qrow = kind * BM + r;
     const int sw = qrow & 31;
-    const uint32_t haddr = smem_u32(dyn + NST * STAGE_BYTES) + (uint32_t)((kind * KP * BM + r) * sizeof(float2));
+    const uint32_t haddr = smem_u32(dyn + NS * STAGE_BYTES) + (uint32_t)((kind * KP * BM + r) * sizeof(float2));
     const uint32_t qaddr = smem_u32(hq) + (uint32_t)((kind * kHeapQ * BM + r) * sizeof(float2));
     float2* const hqp = hq + kind * kHeapQ * BM + r;  // this row's queue, slot s at hqp[s * BM]
     const size_t pbase = ((size_t)tl.split * (CROSS ? 2 : 1) + kind) * a.a_rows * KP;
@@ -844,7 +846,7 @@ umma_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
             __threadfence();
             const size_t ro = ((size_t)(tl.split ^ 1) * (CROSS ? 2 : 1) + kind) * a.a_rows * KP;  // the other half
             const size_t r0s = (size_t)kind * a.a_rows * KP;                                   // split 0's pools
-            const float2* own = reinterpret_cast<const float2*>(dyn + NST * STAGE_BYTES) + kind * KP * BM + r;
+            const float2* own = reinterpret_cast<const float2*>(dyn + NS * STAGE_BYTES) + kind * KP * BM + r;
             float2* scratch = reinterpret_cast<float2*>(stages) + kind * KP * BM + r;
             if (my_row < a.a_rows)
               pair_merge_lists<KP>(own, me.len, a.pool_v + ro + (size_t)my_row * KP, a.pool_i + ro + (size_t)my_row * KP,
@@ -922,9 +924,10 @@ cudaError_t make_map(CUtensorMap* m, const void* base, Elt elt, int rows, int d,
 }
 
 size_t smem_bytes(int mode, bool heap = false) {
+  if (mode != POOL && mode != GPOOL) return 1024 + (size_t)NST_MAX * STAGE_BYTES;
   size_t s = 1024 + (size_t)NST * STAGE_BYTES;
   if (heap) s += 2 * (32 + kHeapQ) * BM * sizeof(float2);
-  else if (mode == POOL || mode == GPOOL) s += 2 * BM * kQCap * (sizeof(float) + sizeof(int));
+  else s += 2 * BM * kQCap * (sizeof(float) + sizeof(int));
   return s;
 }
 
