@@ -140,6 +140,8 @@ struct BuildWs {
   double* inv;
   int* long_list;
   int* long_count;
+  int* scan_tmp2;      // the second graph's transpose scratch (built on a second stream)
+  int* long_list2;
   unsigned long long* stats;
   int* err;
   int* okey;
@@ -203,6 +205,8 @@ size_t carve_build(Carve& c, int64_t n, int32_t d, const gcr_params* p, const Re
   t.inv = c.take<double>((size_t)2 * kinds * nn);
   t.long_list = c.take<int>(nn);
   t.long_count = c.take<int>(4);
+  t.scan_tmp2 = c.take<int>(nn + 1);
+  t.long_list2 = c.take<int>(nn);
   t.stats = c.take<unsigned long long>(GCR_STATS_LEN);
   t.err = c.take<int>(4);
   t.okey = c.take<int>(nn);
@@ -342,6 +346,7 @@ int build_graph_impl(const float* X, int64_t n64_, int32_t d, const int32_t* cam
   ga.op_rowptr = g->op_rowptr; ga.op_len = g->op_len; ga.op_col = g->op_col; ga.op_val = g->op_val;
   ga.raw_col = w.raw_col; ga.raw_val = w.raw_val; ga.op_cnt = w.op_cnt; ga.scan_tmp = w.scan_tmp;
   ga.inv = w.inv; ga.long_list = w.long_list; ga.long_count = w.long_count;
+  ga.scan_tmp2 = w.scan_tmp2; ga.long_list2 = w.long_list2;
   {
     StageScope sc_(GCR_STAGE_GRAPH, st, 7 * kinds + 3);
     GCR_CUDA_TRY(launch_build_operator(ga, st));

@@ -11,6 +11,8 @@
 // row, so every sum (degrees, operator rows) runs in a fixed order: results are
 // bit-reproducible run to run. Operator rows are sorted by column with duplicate columns
 // (mutual neighbours, overlapping graphs) merged into one entry.
+#include <mutex>
+
 #include "common.cuh"
 #include "kernels.h"
 
@@ -480,32 +482,83 @@ cudaError_t launch_scan(const int* in, int* out, int n, cudaStream_t st) {
   return cudaGetLastError();
 }
 
+namespace {
+
+// The transposes of the two graphs are independent until the operator is assembled: the
+// cross-camera graph's is built on a second stream (forked from and joined back into the
+// caller's stream by events, so the pattern also holds under stream capture). One side stream
+// per device; the mutex keeps a call's fork, side work and join together, since an event wait
+// binds to the event's last record at the time it is enqueued.
+constexpr int kMaxGraphDevices = 64;
+struct SideStream {
+  cudaStream_t s = nullptr;
+  cudaEvent_t fork = nullptr, join = nullptr;
+};
+SideStream g_side[kMaxGraphDevices];
+std::mutex g_side_mu;
+
+cudaError_t transpose_graph(const GraphArgs& g, int q, int* raw_col, float* raw_val, int* scan_tmp, int* long_list,
+                            int* long_count, cudaStream_t st) {
+  const int n = g.n, k = g.k;
+  cudaError_t e = cudaMemsetAsync(g.cnt[q], 0, sizeof(int) * (n + 1), st);
+  if (e != cudaSuccess) return e;
+  e = cudaMemsetAsync(g.fill[q], 0, sizeof(int) * n, st);
+  if (e != cudaSuccess) return e;
+  weights_kernel<<<(n + 255) / 256, 256, 0, st>>>(n, k, g.gamma, g.nbr[q], g.d2[q], g.w[q], g.deg_r[q], g.cnt[q]);
+  // exclusive scan of the in-degree counts: transposed row pointers (into scan_tmp, copied back)
+  scan_kernel<<<1, 1024, 0, st>>>(g.cnt[q], scan_tmp, n);
+  e = cudaMemcpyAsync(g.cnt[q], scan_tmp, sizeof(int) * (n + 1), cudaMemcpyDeviceToDevice, st);
+  if (e != cudaSuccess) return e;
+  if ((long)n * k > 0) {
+    // unsorted transpose into raw buffers, then sorted into t_src / t_w
+    scatter_kernel<<<(unsigned)(((long)n * k + 255) / 256), 256, 0, st>>>(n, k, g.nbr[q], g.w[q], g.cnt[q],
+                                                                         g.fill[q], raw_col, raw_val);
+  }
+  tsort_kernel<<<(n + 7) / 8, 256, 0, st>>>(n, g.cnt[q], raw_col, raw_val, g.t_src[q], g.t_w[q], g.deg_c[q]);
+  e = cudaMemsetAsync(long_count, 0, sizeof(int), st);
+  if (e != cudaSuccess) return e;
+  long_list_kernel<<<(n + 255) / 256, 256, 0, st>>>(n, g.cnt[q], long_list, long_count);
+  int nbits = 0;
+  while (nbits < 31 && ((long)1 << nbits) < (long)n) ++nbits;
+  tsort_long_kernel<8><<<2 * 152, 256, 0, st>>>(g.cnt[q], raw_col, raw_val, g.t_src[q], g.t_w[q], g.deg_c[q],
+                                                long_list, long_count, nbits);
+  return cudaGetLastError();
+}
+
+}  // namespace
+
 cudaError_t launch_build_operator(const GraphArgs& g, cudaStream_t st) {
   const int n = g.n, k = g.k;
   cudaError_t e;
-  for (int q = 0; q < g.kinds; ++q) {
-    e = cudaMemsetAsync(g.cnt[q], 0, sizeof(int) * (n + 1), st);
+  if (g.kinds == 1) {
+    e = transpose_graph(g, 0, g.op_col, g.op_val, g.scan_tmp, g.long_list, g.long_count, st);
     if (e != cudaSuccess) return e;
-    e = cudaMemsetAsync(g.fill[q], 0, sizeof(int) * n, st);
+  } else {
+    // graph 0 on the caller's stream with the operator's buffers as scratch; graph 1 on the side
+    // stream with the raw buffers (unused until the operator is filled) and its own scan
+    // temporary and hub list
+    int dev = 0;
+    e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
-    weights_kernel<<<(n + 255) / 256, 256, 0, st>>>(n, k, g.gamma, g.nbr[q], g.d2[q], g.w[q], g.deg_r[q], g.cnt[q]);
-    // exclusive scan of the in-degree counts: transposed row pointers (into scan_tmp, copied back)
-    scan_kernel<<<1, 1024, 0, st>>>(g.cnt[q], g.scan_tmp, n);
-    e = cudaMemcpyAsync(g.cnt[q], g.scan_tmp, sizeof(int) * (n + 1), cudaMemcpyDeviceToDevice, st);
-    if (e != cudaSuccess) return e;
-    if ((long)n * k > 0) {
-      // unsorted transpose into the operator's raw buffers, then sorted into t_src / t_w
-      scatter_kernel<<<(unsigned)(((long)n * k + 255) / 256), 256, 0, st>>>(
-          n, k, g.nbr[q], g.w[q], g.cnt[q], g.fill[q], g.op_col, g.op_val);
+    if (dev < 0 || dev >= kMaxGraphDevices) return cudaErrorInvalidDevice;
+    std::lock_guard<std::mutex> lock(g_side_mu);
+    SideStream& ss = g_side[dev];
+    if (!ss.s) {
+      e = cudaStreamCreateWithFlags(&ss.s, cudaStreamNonBlocking);
+      if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ss.fork, cudaEventDisableTiming);
+      if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ss.join, cudaEventDisableTiming);
+      if (e != cudaSuccess) return e;
     }
-    tsort_kernel<<<(n + 7) / 8, 256, 0, st>>>(n, g.cnt[q], g.op_col, g.op_val, g.t_src[q], g.t_w[q], g.deg_c[q]);
-    e = cudaMemsetAsync(g.long_count, 0, sizeof(int), st);
+    e = cudaEventRecord(ss.fork, st);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(ss.s, ss.fork, 0);
     if (e != cudaSuccess) return e;
-    long_list_kernel<<<(n + 255) / 256, 256, 0, st>>>(n, g.cnt[q], g.long_list, g.long_count);
-    int nbits = 0;
-    while (nbits < 31 && ((long)1 << nbits) < (long)n) ++nbits;
-    tsort_long_kernel<8><<<2 * 152, 256, 0, st>>>(g.cnt[q], g.op_col, g.op_val, g.t_src[q], g.t_w[q], g.deg_c[q],
-                                                  g.long_list, g.long_count, nbits);
+    e = transpose_graph(g, 1, g.raw_col, g.raw_val, g.scan_tmp2, g.long_list2, g.long_count + 1, ss.s);
+    if (e != cudaSuccess) return e;
+    e = transpose_graph(g, 0, g.op_col, g.op_val, g.scan_tmp, g.long_list, g.long_count, st);
+    if (e != cudaSuccess) return e;
+    e = cudaEventRecord(ss.join, ss.s);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(st, ss.join, 0);
+    if (e != cudaSuccess) return e;
   }
   e = cudaGetLastError();
   if (e != cudaSuccess) return e;

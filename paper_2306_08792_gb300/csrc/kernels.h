@@ -271,7 +271,9 @@ struct GraphArgs {
   int* scan_tmp;            // [n+1] scratch
   double* inv;              // [2*kinds][n] scratch: inverse square roots of the degrees
   int* long_list;           // [n] scratch: transposed rows of a hub's length
-  int* long_count;          // [1] scratch
+  int* long_count;          // [2] scratch
+  int* scan_tmp2;           // [n+1], [n]: the second graph's scan temporary and hub list (its
+  int* long_list2;          //   transpose is built on a second stream)
 };
 cudaError_t launch_build_operator(const GraphArgs& g, cudaStream_t st);
 cudaError_t launch_scan(const int* in, int* out, int n, cudaStream_t st);
