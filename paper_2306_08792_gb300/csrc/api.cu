@@ -309,17 +309,20 @@ int knn_impl(const float* X, int64_t n64_, int32_t d, const int32_t* cam, const 
                                      rb.unc_thr, kBandCap, w.band_cnt, w.band_v, w.band_i, st));
     }
     GCR_CUDA_TRY(launch_refine_band(rb, st));
-    // the propagation walks the rows cluster by cluster of the final lists (its gathers then hit
-    // in L2); the refinement above used the candidate pools' order
-    if (g->row_order) {
-      StageScope so_(GCR_STAGE_GRAPH, st, 5);
-      // scratch: the graph build's buffers (free until it runs); w.okey holds the pools' keys
-      GCR_CUDA_TRY(launch_cluster_order(g->nbr, g->nbr_d2, w.n64, n, d, p->k, w.okey, w.fill, w.long_list,
-                                        w.op_cnt, w.ocnt, w.ooff, w.ofill, g->row_order, w.err, st));
-    }
   }
   return GCR_OK;
 }
+
+// The propagation's row order (clusters of the final lists, so that its gathers hit in L2) is
+// computed on a side stream while the operator is built: one stream and two events per device,
+// the mutex keeping a call's fork, order and join together.
+struct OrderStream {
+  cudaStream_t s = nullptr;
+  cudaEvent_t fork = nullptr, join = nullptr;
+};
+constexpr int kMaxOrderDevices = 64;
+OrderStream g_order_side[kMaxOrderDevices];
+std::mutex g_order_mu;
 
 int build_graph_impl(const float* X, int64_t n64_, int32_t d, const int32_t* cam, const gcr_params* p,
                      const Resolved& r, gcr_graph* g, const BuildWs& w, cudaStream_t st) {
@@ -347,9 +350,34 @@ int build_graph_impl(const float* X, int64_t n64_, int32_t d, const int32_t* cam
   ga.raw_col = w.raw_col; ga.raw_val = w.raw_val; ga.op_cnt = w.op_cnt; ga.scan_tmp = w.scan_tmp;
   ga.inv = w.inv; ga.long_list = w.long_list; ga.long_count = w.long_count;
   ga.scan_tmp2 = w.scan_tmp2; ga.long_list2 = w.long_list2;
+  const bool want_order = g->row_order != nullptr && p->k > 0;
+  std::unique_lock<std::mutex> olock;
+  OrderStream* os = nullptr;
+  if (want_order) {
+    int dev = 0;
+    GCR_CUDA_TRY(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= kMaxOrderDevices) return GCR_E_UNSUPPORTED;
+    olock = std::unique_lock<std::mutex>(g_order_mu);
+    os = &g_order_side[dev];
+    if (!os->s) {
+      GCR_CUDA_TRY(cudaStreamCreateWithFlags(&os->s, cudaStreamNonBlocking));
+      GCR_CUDA_TRY(cudaEventCreateWithFlags(&os->fork, cudaEventDisableTiming));
+      GCR_CUDA_TRY(cudaEventCreateWithFlags(&os->join, cudaEventDisableTiming));
+    }
+  }
   {
-    StageScope sc_(GCR_STAGE_GRAPH, st, 7 * kinds + 3);
+    StageScope sc_(GCR_STAGE_GRAPH, st, 7 * kinds + 3 + (want_order ? 5 : 0));
+    if (want_order) {
+      GCR_CUDA_TRY(cudaEventRecord(os->fork, st));
+      GCR_CUDA_TRY(cudaStreamWaitEvent(os->s, os->fork, 0));
+      // scratch: the search's pending-pair queues, free once the search is done; w.okey holds
+      // the pools' keys (the order of the rows outside any cluster)
+      GCR_CUDA_TRY(launch_cluster_order(g->nbr, g->nbr_d2, w.n64, n, d, p->k, w.okey, w.unc_row, w.unc_kind,
+                                        w.bq_row, w.ocnt, w.ooff, w.ofill, g->row_order, w.err, os->s));
+      GCR_CUDA_TRY(cudaEventRecord(os->join, os->s));
+    }
     GCR_CUDA_TRY(launch_build_operator(ga, st));
+    if (want_order) GCR_CUDA_TRY(cudaStreamWaitEvent(st, os->join, 0));
   }
   return GCR_OK;
 }
