@@ -177,7 +177,8 @@ int gcr_normalize(const float* X_in, float* X_out, int64_t n, int32_t d, gcr_str
  * Part of the work (the cross-camera graph's transpose, the propagation's row order) runs
  * on helper streams that the call forks from `stream` and joins back into it by events
  * (one set per device, created on the first such call and kept): `stream` still orders
- * the whole call, and the call can be captured in a CUDA graph.
+ * the whole call, and once a first call on the device has created them, later calls can
+ * be captured in a CUDA graph (the fork and join become graph dependencies).
  * cam: device int32[n], required when cross_camera = 1, else may be NULL.
  * Errors: GCR_E_INVALID (n < 1, k out of range, gamma <= 0, alpha outside [0,1],
  * pool <= k, missing arrays), GCR_E_UNSUPPORTED (d % 4, d % 8 with BF16 or TF32,
