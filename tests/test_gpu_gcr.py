@@ -104,6 +104,43 @@ def test_knn_paired_splits_all_rows(gcr):
     assert G.stats_dict()["band_failed"] == 0
 
 
+@pytest.mark.parametrize("precision", ["fp32", "tf32"])
+def test_build_graph_captured_in_cuda_graph(gcr, precision):
+    """gcr_build_graph forks helper streams (the cross-camera graph's transpose, the row order)
+    from the caller's stream and joins them back: after a first call has created them, a call
+    can be captured in a CUDA graph, and a replay gives the direct call's graph."""
+    import ctypes
+    from paper_2306_08792_gb300 import _lib
+    w = workloads.crosscam(seed=9, n_query=200, n_gallery=1300, d=128, n_clusters=70)
+    X0 = gcr.gcr_normalize(_dev(w.X))
+    cam = _dev(w.cam, torch.int32)
+    p = gcr.default_params(k=w.k, cross_camera=1, alpha=0.7, precision=precision)
+    ref = gcr.gcr_build_graph(X0, p, cam)
+    torch.cuda.synchronize()
+    need = _lib.load().gcr_build_graph_workspace_size(w.n, X0.shape[1], ctypes.byref(p))
+    ws = torch.empty(need, dtype=torch.uint8, device="cuda")
+    g = gcr.alloc_graph(w.n, p, X0.device)
+    gcr.gcr_build_graph(X0, p, cam, graph=g, ws=ws)
+    torch.cuda.synchronize()
+    cg = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(cg):
+        gcr.gcr_build_graph(X0, p, cam, graph=g, ws=ws)
+    for t in (g.nbr, g.nbr_cr, g.op_rowptr, g.op_len, g.row_order):
+        t.fill_(-7)
+    cg.replay()
+    torch.cuda.synchronize()
+    for name in ("nbr", "nbr_d2", "nbr_cr", "nbr_cr_d2", "deg_r", "deg_c", "op_rowptr", "op_len"):
+        assert torch.equal(getattr(g, name), getattr(ref, name)), name
+    # the row order only schedules the propagation: any permutation of the rows is valid
+    assert np.array_equal(np.sort(g.row_order.cpu().numpy()), np.arange(w.n))
+    rp, ln = ref.op_rowptr.cpu().numpy(), ref.op_len.cpu().numpy()
+    col_r, val_r = ref.op_col.cpu().numpy(), ref.op_val.cpu().numpy()
+    col_g, val_g = g.op_col.cpu().numpy(), g.op_val.cpu().numpy()
+    for i in range(w.n):
+        s0, s1 = rp[i], rp[i] + ln[i]
+        assert np.array_equal(col_g[s0:s1], col_r[s0:s1]) and np.array_equal(val_g[s0:s1], val_r[s0:s1]), i
+
+
 EDGE = [("fp32", 1, 8, 5), ("fp32", 5, 12, 10), ("fp32", 130, 68, 7), ("fp32", 300, 256, 0),
         ("fp32", 257, 36, 31), ("bf16", 1, 8, 5), ("bf16", 5, 16, 10), ("bf16", 130, 72, 7),
         ("bf16", 300, 256, 0), ("bf16", 257, 40, 31), ("bf16", 600, 200, 63), ("tf32", 1, 8, 5),
