@@ -14,6 +14,7 @@ import textwrap
 import warnings
 
 import numpy as np
+import pytest
 
 
 def plant(monkeypatch, module, fname, old, new):
@@ -63,17 +64,21 @@ def pin_cases(test_module):
     return out
 
 
-def failing_pins(cases):
+def failing_pins(cases, skipped=None):
     """(label, exception type) of every pin case that fails.
 
     A pin that raises (an assertion, or an error such as an index out of range) counts as
-    failing; the unmutated oracle passes every pin, so the mutant is what made it fail.
+    failing; the unmutated oracle passes every pin, so the mutant is what made it fail. A pin
+    that skips itself (an optional package missing) is listed in ``skipped`` if given.
     """
     failed = []
     with _quiet():
         for label, fn, kw in cases:
             try:
                 fn(**kw)
+            except pytest.skip.Exception:
+                if skipped is not None:
+                    skipped.append(label)
             except Exception as e:  # noqa: BLE001 - any failure of a pin counts
                 failed.append((label, type(e).__name__))
     return failed

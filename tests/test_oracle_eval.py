@@ -72,3 +72,14 @@ def test_perfect_ranking_scores_one():
     idx = np.array([np.argsort(g_label != q, kind="stable") for q in q_label])
     ap, first = oracle.evaluate(idx, q_label, g_label)
     assert np.all(ap == 1.0) and np.all(first == 0)
+
+
+def test_rank_k_and_map_by_hand():
+    """Rank-k counts the queries whose first hit lies before position k; queries without
+    relevant items (AP NaN) are left out of both figures."""
+    ap = np.array([1.0, 0.5, float("nan"), 0.25, 0.0])
+    first = np.array([0, 4, -1, 5, -1])
+    s = oracle.summarise(ap, first, ranks=(1, 5, 6))
+    assert s["queries"] == 4
+    assert s["mAP"] == pytest.approx((1.0 + 0.5 + 0.25 + 0.0) / 4, abs=1e-15)
+    assert (s["rank1"], s["rank5"], s["rank6"]) == (0.25, 0.5, 0.75)
