@@ -712,9 +712,13 @@ umma_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
             } else if (HEAP) {
               // Per-value path with heap pools: a score that passes goes to the row's queue
               // (a predicated shared store); every 4 values, if any lane's queue could not take
-              // 4 more, all lanes drain their queues into their heaps. The excluded columns
-              // (past n, and each row itself on the warp's diagonal chunk) are set to -inf once
-              // per chunk; the global pool's warps compare against a camera no column has.
+              // 4 more, all lanes drain their queues into their heaps. A group of four that no
+              // row of the warp admits (its max at or below every lane's threshold; thresholds
+              // only rise, so none of it could enter later) is skipped after one vote: with
+              // first-tile floors and the paired halves' exchanged thresholds that is most
+              // groups past the first tiles. The excluded columns (past n, and each row itself
+              // on the warp's diagonal chunk) are set to -inf once per chunk; the global pool's
+              // warps compare against a camera no column has.
               if (cb + 32 > a.n || (a.self_excl && cb == r0w)) {
 #pragma unroll
                 for (int c = 0; c < 32; ++c)
@@ -723,6 +727,8 @@ umma_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
               const int cmp_cam = (CROSS && kind == 1) ? my_cam : -2;
 #pragma unroll
               for (int g = 0; g < 8; ++g) {
+                const float m4 = fmaxf(fmaxf(v[4 * g], v[4 * g + 1]), fmaxf(v[4 * g + 2], v[4 * g + 3]));
+                if (!__any_sync(GCR_FULL, m4 > me.tau)) continue;
                 if (__any_sync(GCR_FULL, me.qcnt > kHeapQ - 4)) {
                   const HeapState hs = heap_drain<KP>(haddr, qaddr, me.qcnt, me.len, me.tau, me.floor);
                   me.tau = hs.tau;
