@@ -54,6 +54,22 @@ def test_knn_matches_bruteforce(seed, n, d, k):
             assert abs(d2[i, s] - bf.sqd(X[i], X[j])) < 1e-12
 
 
+def test_knn_rows_in_blocks_match_bruteforce():
+    """Rows searched in blocks (here 4 rows per block, a ragged last block) and a row subset
+    in an arbitrary order give each row's own N_i."""
+    X, cam = _rand(20, 11, 3, cams=3)
+    rows = np.array([10, 3, 0, 7, 7, 5, 1, 9, 2])
+    ref = bf.knn_lists(X.tolist(), 3)
+    ref_cr = bf.knn_lists(X.tolist(), 3, cam.tolist(), cross=True)
+    idx, d2 = oracle.knn_rows(X, rows, 3, block=4)
+    idx_cr, _ = oracle.knn_rows(X, rows, 3, cam, cross_camera=True, block=4)
+    for t, i in enumerate(rows):
+        assert [int(j) for j in idx[t] if j >= 0] == ref[i]
+        assert [int(j) for j in idx_cr[t] if j >= 0] == ref_cr[i]
+        for s, j in enumerate(ref[i]):
+            assert abs(d2[t, s] - bf.sqd(X[i], X[j])) < 1e-12
+
+
 def test_knn_ties_go_to_smaller_index():
     # integer lattice: many exactly equal distances
     X = np.array([[0, 0], [1, 0], [0, 1], [-1, 0], [0, -1], [1, 1], [2, 0]], dtype=np.float64)

@@ -27,6 +27,8 @@ GCR = [
     # N_i: i excluded, nearest first, ties to the smaller index, other cameras only (Eq. 8)
     (gcr_o, "knn_rows", "D[np.arange(r.shape[0]), r] = np.inf", "pass"),
     (gcr_o, "knn_rows", "cam[r][:, None] == cam[None, :]", "cam[r][:, None] != cam[None, :]"),
+    (gcr_o, "knn_rows", "idx[s + t, :sel.shape[0]] = sel", "idx[t, :sel.shape[0]] = sel"),
+    (gcr_o, "knn_rows", "D[np.arange(r.shape[0]), r] = np.inf", "D[np.arange(r.shape[0]), np.arange(r.shape[0])] = np.inf"),
     (gcr_o, "_select_row", "cand = np.nonzero(drow <= vk)[0]", "cand = np.nonzero(drow <= vk)[0][::-1]"),
     (gcr_o, "_select_row", 'order = np.argsort(drow[cand], kind="stable")',
      'order = np.argsort(-drow[cand], kind="stable")'),
